@@ -1,0 +1,129 @@
+"""Pins of the oracle's time stepping against the paper's theorems and exact solutions."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.stepper import Simulation, ricker
+
+
+def _run_energy(sim, steps):
+    out = [sim.energy()]
+    jumps = []
+    for _ in range(steps):
+        sim.step(1)
+        out.append(sim.energy())
+        if sim.scheme == "stdg":
+            jumps.append(sim.jump_dissipation())
+    return np.array(out), np.array(jumps)
+
+
+def _random_state(sim, seed):
+    rng = np.random.default_rng(seed)
+    sim.set_state(rng.normal(size=sim.v_tr.shape), rng.normal(size=sim.sig_tr.shape))
+
+
+@pytest.mark.parametrize("dim,p,periodic,hetero", [(2, 2, True, False), (2, 3, False, True), (3, 2, True, False),
+                                                  (3, 1, False, True)])
+def test_crank_nicolson_preserves_energy(dim, p, periodic, hetero):
+    # Theorem 5 (Eq. SP3F): exact energy preservation, also with free-surface faces
+    if dim == 2:
+        xyz, ev, per = synth.tri_grid(4, 4, 1.0, 1.0, periodic=periodic, jitter=0.2, seed=7)
+    else:
+        xyz, ev, per = synth.tet_kuhn(3 if periodic else 2, 1.0, periodic=periodic, jitter=0.1, seed=7)
+    n = ev.shape[0]
+    rng = np.random.default_rng(2)
+    lam, mu, rho = (rng.uniform(1, 3, n), rng.uniform(.5, 1.5, n), rng.uniform(.7, 1.4, n)) if hetero else \
+        (np.full(n, 2.0), np.full(n, 1.0), np.full(n, 1.0))
+    sim = Simulation(xyz, ev, per, lam, mu, rho, p, 0, "cn", 0.37)
+    _random_state(sim, 3)
+    e, _ = _run_energy(sim, 4)
+    assert np.abs(e / e[0] - 1).max() < 1e-12
+
+
+@pytest.mark.parametrize("dim,p,pg,periodic", [(2, 1, 1, True), (2, 2, 2, False), (2, 3, 1, True), (3, 1, 1, False),
+                                               (3, 2, 2, True)])
+def test_space_time_energy_loss_equals_time_jumps(dim, p, pg, periodic):
+    # Theorem 4, eq. stsum4: E^{n+1} - E^n + (time-jump terms at t^n) = 0, jumps >= 0
+    if dim == 2:
+        xyz, ev, per = synth.tri_grid(4, 4, 1.0, 1.0, periodic=periodic, jitter=0.2, seed=8)
+    else:
+        xyz, ev, per = synth.tet_kuhn(3 if periodic else 2, 1.0, periodic=periodic, jitter=0.1, seed=8)
+    n = ev.shape[0]
+    rng = np.random.default_rng(4)
+    sim = Simulation(xyz, ev, per, rng.uniform(1, 3, n), rng.uniform(.5, 1.5, n), rng.uniform(.7, 1.4, n),
+                     p, pg, "stdg", 0.21)
+    _random_state(sim, 5)
+    e, jumps = _run_energy(sim, 3)
+    assert (jumps >= 0).all()
+    assert (np.diff(e) <= 1e-14 * e[0]).all()
+    np.testing.assert_allclose(e[:-1] - e[1:], jumps, rtol=1e-9, atol=1e-13 * e[0])
+
+
+def _plane_wave_error(n, p, pg, scheme, periods=1.0, cfl=0.25):
+    w = synth.c1_periodic_pwave(n=n, p=p)
+    cp = 2.0
+    dt = cfl / n / cp
+    steps = int(round(periods / cp / dt))
+    dt = periods / cp / steps
+    sim = Simulation(w.xyz, w.elem_vert, w.period, w.lam, w.mu, w.rho, p, pg, scheme, dt)
+    sim.set_plane_wave(0, np.array([1.0, 0.0]), None, 1e-2)
+    v0, s0 = sim.v_tr.copy(), sim.sig_tr.copy()
+    sim.step(steps)
+    # one full period later the exact solution equals the initial one (Sec. 6.2)
+    return np.linalg.norm(sim.v_tr - v0) / np.linalg.norm(v0)
+
+
+@pytest.mark.parametrize("p,pg,scheme,order", [(1, 1, "stdg", 2.0), (2, 2, "stdg", 3.0), (2, 0, "cn", 2.0)])
+def test_plane_wave_convergence_order(p, pg, scheme, order):
+    # Table tab:NT1: order p+1 for p = p_gamma; Crank-Nicolson is second order in time
+    e1 = _plane_wave_error(6, p, pg, scheme)
+    e2 = _plane_wave_error(12, p, pg, scheme)
+    rate = np.log2(e1 / e2)
+    assert rate > order - 0.35, (e1, e2, rate)
+    assert e2 < 5e-2
+
+
+def test_ricker_closed_form():
+    f0, td, a1 = 10.0, 0.116, 1.0
+    t = np.linspace(0, 0.3, 31)
+    ref = 0.5 * a1 * (1 - 2 * (np.pi * f0 * (t - td)) ** 2) * np.exp(-(np.pi * f0 * (t - td)) ** 2)
+    np.testing.assert_allclose(ricker(t, f0, td, a1), ref, atol=1e-15)
+    assert abs(ricker(td, f0, td, a1) - 0.5 * a1) < 1e-15
+
+
+def test_source_linearity_and_superposition():
+    w = synth.scaled("c2", ny=6, steps=4)
+    base = Simulation.from_workload(w)
+    src = dict(xs=w.shots_xs[0], direction=w.shots_dir[0], f0=w.f0, t_delay=0.02, a1=1.0)
+
+    def run(ic, a1):
+        s = Simulation.from_workload(w)
+        if ic:
+            _random_state(s, 11)
+        if a1 != 0.0:
+            s.set_source(**{**src, "a1": a1})
+        s.step(4)
+        return s.v_tr.copy(), s.sig_tr.copy()
+
+    v_ic, s_ic = run(True, 0.0)
+    v_src, s_src = run(False, 1.0)
+    v_both, s_both = run(True, 1.0)
+    v_two, _ = run(False, 2.0)
+    np.testing.assert_allclose(v_both, v_ic + v_src, atol=1e-12 * np.abs(v_both).max())
+    np.testing.assert_allclose(s_both, s_ic + s_src, atol=1e-12 * np.abs(s_both).max())
+    np.testing.assert_allclose(v_two, 2 * v_src, atol=1e-13 * np.abs(v_two).max())
+    assert np.abs(v_src).max() > 0
+    del base
+
+
+def test_receiver_at_node_reads_nodal_value():
+    w = synth.c1_periodic_pwave(n=5, p=2)
+    sim = Simulation.from_workload(w)
+    _random_state(sim, 1)
+    # centroid of element 7: evaluate the polynomial directly from the nodal values
+    x = sim.mesh.X[7].mean(axis=0)
+    sim.set_receivers(x[None])
+    val = sim.receiver_values()[0]
+    xi = np.linalg.solve(sim.mesh.J[7], x - sim.mesh.X[7, 0])
+    phi = sim.disc.ref.values(xi[None])[0]
+    np.testing.assert_allclose(val, sim.v_tr[7] @ phi, rtol=1e-13)
