@@ -1,0 +1,158 @@
+/*
+ * stdg.h -- C ABI of the GB300 (sm_103a) library for the staggered space-time
+ * discontinuous Galerkin scheme for velocity-stress linear elasticity of
+ * Tavelli & Dumbser, arXiv:1802.04516.
+ *
+ * The library owns all device memory it allocates.  Every pointer argument is a
+ * HOST pointer unless its name ends in _dev (a device pointer the caller owns).
+ * Host buffers are read or written synchronously: when a call returns, the
+ * caller may reuse or free them.  All work is issued on the stream given to
+ * stdg_create (NULL = the legacy default stream).
+ *
+ * Error behaviour: every int-returning call returns STDG_OK (0) or a negative
+ * STDG_E* code; a human-readable message is then available from
+ * stdg_last_error().  A failed call leaves the context usable unless the code is
+ * STDG_ECUDA (a CUDA error: the context should be destroyed).
+ *
+ * Layouts (row-major, contiguous):
+ *   velocity, one slab      [elem][component d][time node N_gamma][space node N_phi]
+ *   velocity trace          [elem][component d][space node N_phi]
+ *   stress trace            [face][component s][dual mode N_psi]
+ *   stress components       2D: xx, yy, xy      3D: xx, yy, zz, xy, yz, xz
+ *   space nodes             equispaced Lagrange nodes of the reference simplex,
+ *                           z outer, then y, x fastest
+ *   dual modes              Taylor monomials ((x - x_j)/h_j)^a, |a| <= p, graded-
+ *                           lexicographic (degree ascending, then x-exponent
+ *                           descending, then y-exponent descending)
+ *   time nodes              Gauss-Legendre points of [0,1], ascending
+ *   faces                   ascending lexicographic order of the sorted global
+ *                           vertex-id tuple; l(j) = smaller, r(j) = larger element
+ * Multi-shot data is shot-major: [shot][...] with the per-shot layout above.
+ */
+#ifndef STDG_H
+#define STDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STDG_OK        0
+#define STDG_EINVAL   (-1)  /* bad argument, NaN or Inf in an input                */
+#define STDG_EMESH    (-2)  /* inverted element, non-manifold or self-adjacent face */
+#define STDG_ENOMEM   (-3)  /* device allocation failed                             */
+#define STDG_ECUDA    (-4)  /* CUDA runtime error                                   */
+#define STDG_ENOTCONV (-5)  /* Krylov hit max_iters; the state is still advanced    */
+#define STDG_ESTATE   (-6)  /* call out of order (e.g. step before set_mesh)        */
+
+enum stdg_scheme { STDG_SCHEME_CN = 0, STDG_SCHEME_STDG = 1 };
+enum stdg_precision { STDG_FP64 = 0, STDG_MIXED_FP32 = 1 };
+
+typedef struct stdg_ctx stdg_ctx;
+
+typedef struct {
+    int p;              /* spatial degree, 1..4 in 2D, 1..3 in 3D                      */
+    int p_gamma;        /* time degree, 0..3; must be 0 for Crank-Nicolson             */
+    int scheme;         /* stdg_scheme                                                   */
+    int precision;      /* stdg_precision                                                */
+    double rel_tol;     /* Krylov stop: ||b - A x||_2 <= rel_tol ||b||_2                 */
+    int max_iters;      /* cap on operator applications per solve                       */
+    int gmres_restart;  /* GMRES(m) restart length                                      */
+    double inner_tol;   /* relative tolerance of the FP32 inner solve (mixed precision)  */
+    int use_graph;      /* 1: one CUDA graph per step with device-side loops; 0: host loop */
+} stdg_options;
+
+typedef struct {
+    int iters_total;        /* operator applications summed over the steps            */
+    int iters_max;          /* largest per-step count                                 */
+    int refinements;        /* FP64 refinement sweeps (mixed precision)               */
+    double final_rel_res;   /* ||b - A x|| / ||b|| of the last step (FP64)            */
+    int status;             /* STDG_OK or STDG_ENOTCONV                               */
+} stdg_stats;
+
+/* Context.  `cuda_stream` is a cudaStream_t (may be NULL). */
+int  stdg_create(stdg_ctx** out, int dim, const stdg_options* opt, void* cuda_stream);
+void stdg_destroy(stdg_ctx* ctx);
+const char* stdg_last_error(const stdg_ctx* ctx);
+
+/* Mesh of simplices (Sec. 3): n_vert x dim coordinates, n_elem x (dim+1) vertex ids
+ * (0-based, positively oriented after unwrapping).  `period` (dim entries, 0 = not
+ * periodic) or NULL.  On a periodic axis vertices are identified, not duplicated.
+ * Every boundary face is a free surface (sigma . n = 0).  Builds faces, l(j)/r(j),
+ * normals, dual cells R_j and, on the device, the blocks D_{i,j} (Eq. MD_3) and the
+ * inverse dual mass matrices M_j^{-1} (Eq. MD_2).  Returns STDG_EMESH for an
+ * inverted element, a face shared by more than two elements or an element that is
+ * its own neighbour. */
+int stdg_set_mesh(stdg_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_elem,
+                  const int32_t* elem_vert, const double* period);
+
+/* Per-element Lame parameters and density (Eq. 5, Eq. NM1): rho_i constant per
+ * element; E_j constant per dual cell, the sub-cell-measure-weighted mean of its
+ * two elements.  All > 0 (lambda > -2mu/dim is not accepted: lambda must be >= 0). */
+int stdg_set_material(stdg_ctx* ctx, const double* lambda, const double* mu, const double* rho);
+
+/* Number of shots (right-hand sides).  Resets states to zero.  Default 1. */
+int stdg_set_shots(stdg_ctx* ctx, int n_shots);
+
+/* Carried state of one shot: the t^{n,-} traces (Eq. NM13). */
+int stdg_set_state(stdg_ctx* ctx, int shot, const double* v_tr, const double* sig_tr);
+int stdg_get_state(stdg_ctx* ctx, int shot, double* v_tr, double* sig_tr);
+
+/* Projects the exact plane wave of Eq. NT2.1/NT2.2 (unit normal n/|n|, wave vector
+ * 2 pi n, amplitude amp; kind 0 = P, 1 = S with polarisation pol, NULL in 2D =
+ * (-n_y, n_x)) at time t onto the bases, for one shot.  Homogeneous media only
+ * (element 0's material is used). */
+int stdg_set_plane_wave(stdg_ctx* ctx, int shot, int kind, const double* n, const double* pol,
+                        double amp, double t);
+
+/* Point sources (Sec. 6.3): shot k has force direction dir[k] at xs[k] and the Ricker
+ * time function S(t) = a1 (0.5 + a2 tau^2) exp(a2 tau^2), tau = t - t_delay,
+ * a2 = -(pi f0)^2.  Sets n_shots (resets states). */
+int stdg_set_sources(stdg_ctx* ctx, int n_shots, const double* xs, const double* dir,
+                     double f0, double t_delay, double a1);
+
+/* Receivers: velocity v_h(x_r, t^{n+1,-}) is recorded after every step. */
+int stdg_set_receivers(stdg_ctx* ctx, int n_rec, const double* xr);
+
+/* Advances every shot by n_steps slabs of size dt (Eq. velocity.sys + NM26, or the
+ * Crank-Nicolson Eqs. velocity.sys.cn + NM26.cn).  `out` may be NULL.  Returns
+ * STDG_ENOTCONV if some solve hit max_iters (the state is still advanced). */
+int stdg_step(stdg_ctx* ctx, double dt, int n_steps, stdg_stats* out);
+
+/* Simulation time of the carried state. */
+int stdg_get_time(stdg_ctx* ctx, double* t);
+int stdg_set_time(stdg_ctx* ctx, double t);
+
+/* Total energy of each shot's carried state (Eq. SP3F): out[n_shots]. */
+int stdg_energy(stdg_ctx* ctx, double* out);
+
+/* Receiver records since the last stdg_set_receivers / stdg_set_sources:
+ * out[n_shots][n_recorded_steps][n_rec][dim]; `cap` = capacity in doubles.
+ * Returns the number of recorded steps (>= 0) or an error code. */
+int stdg_read_receivers(stdg_ctx* ctx, double* out, int64_t cap);
+
+/* y = A x for one slab of size dt (Eq. velocity.sys, or Eq. velocity.sys.cn for CN),
+ * canonical velocity layout, one shot, FP64.  Host pointers. */
+int stdg_apply_operator(stdg_ctx* ctx, double dt, const double* x, double* y);
+
+/* Same on device buffers owned by the caller (FP64; or FP32 when fp32 != 0, using
+ * the FP32 copy of the blocks). */
+int stdg_apply_operator_device(stdg_ctx* ctx, double dt, const void* x_dev, void* y_dev, int fp32);
+
+/* Sizes: what = 0 n_elem, 1 n_face, 2 N_phi, 3 N_psi, 4 N_gamma, 5 stress comps s,
+ * 6 n_shots, 7 velocity values per shot and slab, 8 n_rec, 9 n_boundary_faces,
+ * 10 device bytes held. */
+int stdg_query(stdg_ctx* ctx, int what, int64_t* out);
+
+/* Face table as built by stdg_set_mesh: l(j), r(j) (-1 on the boundary). */
+int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);
+
+/* Average device time of `n` launches of the operator's face kernel (fp32 != 0: the
+ * FP32 one) on the context stream, measured with CUDA events: *ms_out. */
+int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STDG_H */

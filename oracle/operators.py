@@ -156,7 +156,10 @@ class Discretization:
         self.E = stiffness_tensor(self.lam_f, self.mu_f, self.dim)     # (nf, d, d, d, d)
 
     # ---- space-time blocks ----------------------------------------------------------
-    def spacetime(self, dt):
+    def spacetime(self, dt, inverse="inv"):
+        """Space-time blocks for step dt.  inverse="solve" forms (M^st_j)^{-1} by LU solves
+        instead of explicit inversion: the same matrix up to rounding, used to measure the
+        oracle's own rounding spread on ill-conditioned dual mass matrices."""
         tm = self.tm
         W, T, g0 = tm["W"], tm["T"], tm["g0"]
         self.dt = dt
@@ -165,7 +168,10 @@ class Discretization:
         self.Qst = np.einsum("ab,fslmk->fslambk", dt * W, self.Qt).reshape(
             self.Qt.shape[:3] + (self.Ng * self.Npsi, self.Ng * self.Nphi))
         Mst = np.einsum("ab,fkm->fakbm", T, self.Mdual).reshape(-1, self.Ng * self.Npsi, self.Ng * self.Npsi)
-        self.Mst_inv = np.linalg.inv(Mst)
+        if inverse == "solve":
+            self.Mst_inv = np.linalg.solve(Mst, np.broadcast_to(np.eye(Mst.shape[1]), Mst.shape).copy())
+        else:
+            self.Mst_inv = np.linalg.inv(Mst)
         self.Mminus = np.einsum("a,fkm->fakm", g0, self.Mdual).reshape(-1, self.Ng * self.Npsi, self.Npsi)
         self.Mbar_st = np.einsum("ab,ekm->eakbm", T, self.Mbar).reshape(-1, self.Ng * self.Nphi, self.Ng * self.Nphi)
         self.Mbar_minus = np.einsum("a,ekm->eakm", g0, self.Mbar).reshape(-1, self.Ng * self.Nphi, self.Nphi)
@@ -174,9 +180,9 @@ class Discretization:
     def vel_size(self):
         return self.mesh.n_elem * self.dim * self.Ng * self.Nphi
 
-    def assemble(self, dt, scheme):
+    def assemble(self, dt, scheme, inverse="inv"):
         """Sparse A of Eq. velocity.sys (scheme 'stdg') or Eq. velocity.sys.cn ('cn')."""
-        self.spacetime(dt)
+        self.spacetime(dt, inverse)
         c = 0.25 if scheme == "cn" else 1.0
         m, d = self.mesh, self.dim
         nb = self.Ng * self.Nphi

@@ -1,0 +1,248 @@
+"""ctypes binding of the C ABI in include/stdg.h (argument marshalling only).
+
+Every function of the header is exposed under its own name; ``Solver`` is a thin
+object wrapper that owns one context.  All arithmetic runs in libstdg.so: if the
+library is missing this module raises instead of falling back to anything else.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libstdg.so")
+
+STDG_OK, STDG_EINVAL, STDG_EMESH, STDG_ENOMEM, STDG_ECUDA, STDG_ENOTCONV, STDG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+SCHEME = {"cn": 0, "stdg": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
+
+
+class stdg_options(C.Structure):
+    _fields_ = [("p", C.c_int), ("p_gamma", C.c_int), ("scheme", C.c_int), ("precision", C.c_int),
+                ("rel_tol", C.c_double), ("max_iters", C.c_int), ("gmres_restart", C.c_int),
+                ("inner_tol", C.c_double), ("use_graph", C.c_int)]
+
+
+class stdg_stats(C.Structure):
+    _fields_ = [("iters_total", C.c_int), ("iters_max", C.c_int), ("refinements", C.c_int),
+                ("final_rel_res", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+
+SIGNATURES = {
+    "stdg_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(stdg_options), _P]),
+    "stdg_destroy": (None, [_P]),
+    "stdg_last_error": (C.c_char_p, [_P]),
+    "stdg_set_mesh": (C.c_int, [_P, C.c_int64, _D, C.c_int64, _I32, _D]),
+    "stdg_set_material": (C.c_int, [_P, _D, _D, _D]),
+    "stdg_set_shots": (C.c_int, [_P, C.c_int]),
+    "stdg_set_state": (C.c_int, [_P, C.c_int, _D, _D]),
+    "stdg_get_state": (C.c_int, [_P, C.c_int, _D, _D]),
+    "stdg_set_plane_wave": (C.c_int, [_P, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double]),
+    "stdg_set_sources": (C.c_int, [_P, C.c_int, _D, _D, C.c_double, C.c_double, C.c_double]),
+    "stdg_set_receivers": (C.c_int, [_P, C.c_int, _D]),
+    "stdg_step": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(stdg_stats)]),
+    "stdg_get_time": (C.c_int, [_P, _D]),
+    "stdg_set_time": (C.c_int, [_P, C.c_double]),
+    "stdg_energy": (C.c_int, [_P, _D]),
+    "stdg_read_receivers": (C.c_int, [_P, _D, C.c_int64]),
+    "stdg_apply_operator": (C.c_int, [_P, C.c_double, _D, _D]),
+    "stdg_apply_operator_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
+    "stdg_query": (C.c_int, [_P, C.c_int, _I64]),
+    "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
+    "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
+}
+
+_lib = None
+
+
+def load(path=None):
+    """Load libstdg.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libstdg.so not found at %s: run paper_1802_04516_gb300.build.build()" % p)
+    lib = C.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(SIGNATURES)
+
+
+class StdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("stdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Solver:
+    """One library context: a mesh, a medium, shots, and the stepping state."""
+
+    def __init__(self, dim, p, p_gamma, scheme="stdg", precision="fp64", rel_tol=1e-8, max_iters=5000,
+                 gmres_restart=30, inner_tol=1e-4, use_graph=True, stream=None):
+        self.lib = load()
+        self.dim = dim
+        opt = stdg_options(p, p_gamma, SCHEME[scheme], PRECISION[precision], rel_tol, max_iters, gmres_restart,
+                           inner_tol, 1 if use_graph else 0)
+        h = _P()
+        rc = self.lib.stdg_create(C.byref(h), dim, C.byref(opt), _P(stream or 0))
+        if rc != 0:
+            raise StdgError(rc, "stdg_create rejected the options")
+        self.h = h
+        self.last_stats = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stdg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _chk(self, rc, allow=()):
+        if rc < 0 and rc not in allow:
+            raise StdgError(rc, self.lib.stdg_last_error(self.h).decode())
+        return rc
+
+    def query(self, what):
+        v = C.c_int64()
+        self._chk(self.lib.stdg_query(self.h, what, C.byref(v)))
+        return v.value
+
+    n_elem = property(lambda s: s.query(0))
+    n_face = property(lambda s: s.query(1))
+    Nphi = property(lambda s: s.query(2))
+    Npsi = property(lambda s: s.query(3))
+    Ng = property(lambda s: s.query(4))
+    n_sig = property(lambda s: s.query(5))
+    n_shots = property(lambda s: s.query(6))
+    nvel = property(lambda s: s.query(7))
+
+    def set_mesh(self, xyz, elem_vert, period=None):
+        xyz = _f64(xyz)
+        ev = np.ascontiguousarray(elem_vert, dtype=np.int32)
+        per = None if period is None else _f64(period)
+        self._chk(self.lib.stdg_set_mesh(self.h, xyz.shape[0], _d(xyz), ev.shape[0], ev.ctypes.data_as(_I32),
+                                         None if per is None else _d(per)))
+
+    def set_material(self, lam, mu, rho):
+        lam, mu, rho = _f64(lam), _f64(mu), _f64(rho)
+        self._chk(self.lib.stdg_set_material(self.h, _d(lam), _d(mu), _d(rho)))
+
+    def set_shots(self, n):
+        self._chk(self.lib.stdg_set_shots(self.h, n))
+
+    def set_state(self, v_tr, sig_tr, shot=0):
+        v, s = _f64(v_tr), _f64(sig_tr)
+        self._chk(self.lib.stdg_set_state(self.h, shot, _d(v), _d(s)))
+
+    def get_state(self, shot=0):
+        v = np.zeros((self.n_elem, self.dim, self.Nphi))
+        s = np.zeros((self.n_face, self.n_sig, self.Npsi))
+        self._chk(self.lib.stdg_get_state(self.h, shot, _d(v), _d(s)))
+        return v, s
+
+    def set_plane_wave(self, kind, n, pol=None, amp=1.0, t=0.0, shot=0):
+        n = _f64(n)
+        pol = None if pol is None else _f64(pol)
+        self._chk(self.lib.stdg_set_plane_wave(self.h, shot, kind, _d(n), None if pol is None else _d(pol), amp, t))
+
+    def set_sources(self, xs, direction, f0, t_delay, a1):
+        xs, dr = _f64(np.atleast_2d(xs)), _f64(np.atleast_2d(direction))
+        self._chk(self.lib.stdg_set_sources(self.h, xs.shape[0], _d(xs), _d(dr), f0, t_delay, a1))
+
+    def set_receivers(self, xr):
+        xr = _f64(np.atleast_2d(xr))
+        self.n_rec = xr.shape[0]
+        self._chk(self.lib.stdg_set_receivers(self.h, xr.shape[0], _d(xr)))
+
+    def step(self, dt, n_steps=1, allow_notconv=False):
+        st = stdg_stats()
+        rc = self.lib.stdg_step(self.h, dt, n_steps, C.byref(st))
+        self.last_stats = st.as_dict()
+        self._chk(rc, allow=(STDG_ENOTCONV,) if allow_notconv else ())
+        return self.last_stats
+
+    @property
+    def time(self):
+        t = C.c_double()
+        self._chk(self.lib.stdg_get_time(self.h, C.byref(t)))
+        return t.value
+
+    @time.setter
+    def time(self, t):
+        self._chk(self.lib.stdg_set_time(self.h, t))
+
+    def energy(self):
+        out = np.zeros(self.n_shots)
+        self._chk(self.lib.stdg_energy(self.h, _d(out)))
+        return out
+
+    def read_receivers(self, max_steps=100000):
+        n_rec = getattr(self, "n_rec", 0)
+        if n_rec == 0:
+            return np.zeros((self.n_shots, 0, 0, self.dim))
+        cap = self.n_shots * max_steps * n_rec * self.dim
+        buf = np.zeros(cap)
+        k = self._chk(self.lib.stdg_read_receivers(self.h, _d(buf), cap))
+        return buf[: self.n_shots * k * n_rec * self.dim].reshape(self.n_shots, k, n_rec, self.dim)
+
+    def apply_operator(self, dt, x):
+        x = _f64(x).ravel()
+        y = np.zeros_like(x)
+        self._chk(self.lib.stdg_apply_operator(self.h, dt, _d(x), _d(y)))
+        return y
+
+    def apply_operator_device(self, dt, x_ptr, y_ptr, fp32=False):
+        self._chk(self.lib.stdg_apply_operator_device(self.h, dt, _P(x_ptr), _P(y_ptr), 1 if fp32 else 0))
+
+    def get_faces(self):
+        fl = np.zeros(self.n_face, dtype=np.int32)
+        fr = np.zeros(self.n_face, dtype=np.int32)
+        self._chk(self.lib.stdg_get_faces(self.h, fl.ctypes.data_as(_I32), fr.ctypes.data_as(_I32)))
+        return fl, fr
+
+    def time_operator(self, dt, fp32=False, n=20):
+        ms = C.c_double()
+        self._chk(self.lib.stdg_time_operator(self.h, dt, 1 if fp32 else 0, n, C.byref(ms)))
+        return ms.value
+
+
+def solver_from_workload(w, precision="fp64", rel_tol=1e-8, max_iters=5000, gmres_restart=30, inner_tol=1e-4,
+                         use_graph=True, stream=None, with_sources=True, with_receivers=True):
+    """Build a Solver for a ``synth.Workload`` (mesh, media, plane wave or sources, receivers)."""
+    s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol, max_iters, gmres_restart, inner_tol, use_graph,
+               stream)
+    s.set_mesh(w.xyz, w.elem_vert, w.period)
+    s.set_material(w.lam, w.mu, w.rho)
+    if with_sources and w.shots_xs is not None:
+        s.set_sources(w.shots_xs, w.shots_dir, w.f0, w.t_delay, w.a1)
+    if w.plane_wave is not None:
+        pw = w.plane_wave
+        s.set_plane_wave(pw["kind"], pw["n"], pw.get("pol"), pw["amp"])
+    if with_receivers and w.receivers is not None:
+        s.set_receivers(w.receivers)
+    return s

@@ -1,0 +1,592 @@
+// C ABI of the library (declared in include/stdg.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "stdg_internal.h"
+
+namespace stdg {
+void solver_invalidate_graph(stdg_ctx* c);
+double* solver_dparams(stdg_ctx* c);
+
+int dev_alloc(stdg_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? STDG_ENOMEM : STDG_ECUDA;
+    }
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    return STDG_OK;
+}
+
+static void dev_free(stdg_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+void dev_free_all(stdg_ctx* c) {
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->bytes = 0;
+}
+
+static bool all_finite(const double* a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+// phi_k at a point given in the element's frame (host evaluation for sources/receivers)
+static void eval_phi_host(const stdg_ctx* c, int64_t e, const double* x, double* phi) {
+    const int d = c->dim, NP = c->Nphi, nv = d + 1;
+    double xi[3] = {0, 0, 0};
+    for (int r = 0; r < d; ++r)
+        for (int a = 0; a < d; ++a) xi[r] += c->hm.Jinv[(e * d + r) * d + a] * (x[a] - c->hm.X[(e * nv) * d + a]);
+    double mono[kMaxNP];
+    for (int a = 0; a < NP; ++a) {
+        double v = 1.0;
+        for (int r = 0; r < d; ++r)
+            for (int q = 0; q < c->rt.exps[a][r]; ++q) v *= xi[r];
+        mono[a] = v;
+    }
+    for (int k = 0; k < NP; ++k) {
+        double v = 0;
+        for (int a = 0; a < NP; ++a) v += c->rt.coef[a * NP + k] * mono[a];
+        phi[k] = v;
+    }
+}
+
+static int alloc_state(stdg_ctx* c, int n_shots) {
+    dev_free(c, c->d_vtr);
+    dev_free(c, c->d_sigtr);
+    dev_free(c, c->d_energy);
+    c->d_vtr = c->d_sigtr = c->d_energy = nullptr;
+    int rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_vtr, sizeof(double) * c->ntr * n_shots)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_sigtr, sizeof(double) * c->nsig * n_shots)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_energy, sizeof(double) * std::max(1, n_shots))) != STDG_OK) return rc;
+    STDG_CUDA(c, cudaMemsetAsync(c->d_vtr, 0, sizeof(double) * c->ntr * n_shots, c->stream));
+    STDG_CUDA(c, cudaMemsetAsync(c->d_sigtr, 0, sizeof(double) * c->nsig * n_shots, c->stream));
+    c->n_shots = n_shots;
+    c->rec_steps = 0;
+    solver_invalidate_graph(c);
+    return STDG_OK;
+}
+
+static int ensure_fp32(stdg_ctx* c) {
+    if (c->d_D32) return STDG_OK;
+    int rc;
+    const int64_t nD = c->n_face * 2 * c->dim * c->Nphi * c->Nphi;
+    if ((rc = dev_alloc(c, (void**)&c->d_D32, sizeof(float) * nD)) != STDG_OK) return rc;
+    STDG_CUDA(c, launch_to_fp32(c));
+    return STDG_OK;
+}
+
+static int upload_material32(stdg_ctx* c) {
+    if (!c->have_material || !c->d_D32) return STDG_OK;
+    std::vector<float> lf(c->n_face), mf(c->n_face), rj(c->n_elem);
+    std::vector<double> l(c->n_face), m(c->n_face), r(c->n_elem);
+    STDG_CUDA(c, cudaMemcpy(l.data(), c->d_lamf, sizeof(double) * c->n_face, cudaMemcpyDeviceToHost));
+    STDG_CUDA(c, cudaMemcpy(m.data(), c->d_muf, sizeof(double) * c->n_face, cudaMemcpyDeviceToHost));
+    STDG_CUDA(c, cudaMemcpy(r.data(), c->d_rhoJ, sizeof(double) * c->n_elem, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < c->n_face; ++i) { lf[i] = (float)l[i]; mf[i] = (float)m[i]; }
+    for (int64_t i = 0; i < c->n_elem; ++i) rj[i] = (float)r[i];
+    STDG_CUDA(c, cudaMemcpy(c->d_lamf32, lf.data(), sizeof(float) * c->n_face, cudaMemcpyHostToDevice));
+    STDG_CUDA(c, cudaMemcpy(c->d_muf32, mf.data(), sizeof(float) * c->n_face, cudaMemcpyHostToDevice));
+    STDG_CUDA(c, cudaMemcpy(c->d_rhoJ32, rj.data(), sizeof(float) * c->n_elem, cudaMemcpyHostToDevice));
+    return STDG_OK;
+}
+
+}  // namespace stdg
+
+using namespace stdg;
+
+#define CHECK_CTX(c) do { if (!(c)) return STDG_EINVAL; } while (0)
+#define NEED_MESH(c) do { if (!(c)->have_mesh) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_mesh first"); } while (0)
+#define NEED_ALL(c) do { NEED_MESH(c); if (!(c)->have_material) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_material first"); } while (0)
+
+extern "C" {
+
+int stdg_create(stdg_ctx** out, int dim, const stdg_options* opt, void* cuda_stream) {
+    if (!out || !opt) return STDG_EINVAL;
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return STDG_EINVAL;
+    if (opt->p < 1 || opt->p > (dim == 2 ? 4 : 3)) return STDG_EINVAL;
+    if (opt->p_gamma < 0 || opt->p_gamma > 3) return STDG_EINVAL;
+    if (opt->scheme != STDG_SCHEME_CN && opt->scheme != STDG_SCHEME_STDG) return STDG_EINVAL;
+    if (opt->scheme == STDG_SCHEME_CN && opt->p_gamma != 0) return STDG_EINVAL;
+    if (opt->precision != STDG_FP64 && opt->precision != STDG_MIXED_FP32) return STDG_EINVAL;
+    if (!(opt->rel_tol > 0.0) || opt->max_iters < 1) return STDG_EINVAL;
+    stdg_ctx* c = new stdg_ctx();
+    c->dim = dim;
+    c->opt = *opt;
+    if (!(c->opt.inner_tol > 0.0)) c->opt.inner_tol = 1e-4;
+    if (c->opt.gmres_restart <= 0) c->opt.gmres_restart = 30;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreate(&c->stream);   // blocking: ordered with the legacy stream
+        if (e != cudaSuccess) { delete c; return STDG_ECUDA; }
+        c->own_stream = true;
+    }
+    build_ref_tables(dim, opt->p, opt->p_gamma, &c->rt);
+    c->Nphi = c->rt.Nphi;
+    c->Npsi = c->rt.Npsi;
+    c->Ng = c->rt.Ng;
+    c->s = c->rt.s;
+    if (dev_alloc(c, (void**)&c->d_rt, sizeof(RefTables)) != STDG_OK ||
+        cudaMemcpy(c->d_rt, &c->rt, sizeof(RefTables), cudaMemcpyHostToDevice) != cudaSuccess) {
+        stdg_destroy(c);
+        return STDG_ECUDA;
+    }
+    double gl[16];
+    gauss_legendre01(8, gl, gl + 8);
+    if (dev_alloc(c, (void**)&c->d_gl8, sizeof(gl)) != STDG_OK ||
+        cudaMemcpy(c->d_gl8, gl, sizeof(gl), cudaMemcpyHostToDevice) != cudaSuccess) {
+        stdg_destroy(c);
+        return STDG_ECUDA;
+    }
+    *out = c;
+    return STDG_OK;
+}
+
+void stdg_destroy(stdg_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    solver_free(c);
+    dev_free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* stdg_last_error(const stdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
+                  const double* period) {
+    CHECK_CTX(c);
+    if (!xyz || !elem_vert || n_vert < c->dim + 1 || n_elem < 1 || n_elem > (int64_t)INT32_MAX / 8)
+        STDG_FAIL(c, STDG_EINVAL, "bad mesh arguments");
+    if (period && !all_finite(period, c->dim)) STDG_FAIL(c, STDG_EINVAL, "non-finite period");
+    // release everything mesh-dependent
+    solver_free(c);
+    void* keep_rt = c->d_rt;
+    void* keep_gl = c->d_gl8;
+    for (void* p : c->allocs)
+        if (p != keep_rt && p != keep_gl) cudaFree(p);
+    c->allocs.assign({keep_rt, keep_gl});
+    c->d_face_l = c->d_face_r = nullptr;
+    c->d_X = c->d_Jinv = c->d_detJ = c->d_faceX = c->d_shift = c->d_normal = c->d_xc = c->d_hj = nullptr;
+    c->d_D = c->d_L = c->d_Mdual = nullptr;
+    c->d_D32 = nullptr;
+    c->d_lamf = c->d_muf = c->d_rhoJ = nullptr;
+    c->d_lamf32 = c->d_muf32 = c->d_rhoJ32 = nullptr;
+    c->d_vtr = c->d_sigtr = c->d_b = c->d_x = c->d_energy = c->d_sigtmp = nullptr;
+    c->d_src = nullptr;
+    c->d_rec_elem = nullptr;
+    c->d_rec_phi = c->d_records = nullptr;
+    c->have_mesh = c->have_material = false;
+    c->have_sources = 0;
+    c->n_rec = 0;
+    c->t = 0.0;
+
+    int rc = build_host_mesh(c->dim, n_vert, xyz, n_elem, elem_vert, period, &c->hm, &c->err);
+    if (rc != STDG_OK) return rc;
+    const int d = c->dim, NP = c->Nphi, nv = d + 1;
+    c->n_elem = n_elem;
+    c->n_face = c->hm.n_face;
+    c->nvel = n_elem * d * c->Ng * NP;
+    c->ntr = n_elem * d * NP;
+    c->nsig = c->n_face * c->s * c->Npsi;
+    const int64_t nf = c->n_face;
+#define ALLOC(ptr, bytes) do { if ((rc = dev_alloc(c, (void**)&(ptr), (bytes))) != STDG_OK) return rc; } while (0)
+#define UP(dst, src, bytes) STDG_CUDA(c, cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice))
+    ALLOC(c->d_face_l, sizeof(int32_t) * nf);
+    ALLOC(c->d_face_r, sizeof(int32_t) * nf);
+    ALLOC(c->d_X, sizeof(double) * n_elem * nv * d);
+    ALLOC(c->d_Jinv, sizeof(double) * n_elem * d * d);
+    ALLOC(c->d_detJ, sizeof(double) * n_elem);
+    ALLOC(c->d_faceX, sizeof(double) * nf * d * d);
+    ALLOC(c->d_shift, sizeof(double) * nf * d);
+    ALLOC(c->d_normal, sizeof(double) * nf * d);
+    ALLOC(c->d_xc, sizeof(double) * nf * d);
+    ALLOC(c->d_hj, sizeof(double) * nf);
+    ALLOC(c->d_D, sizeof(double) * nf * 2 * d * NP * NP);
+    ALLOC(c->d_L, sizeof(double) * nf * NP * NP);
+    ALLOC(c->d_Mdual, sizeof(double) * nf * NP * NP);
+    ALLOC(c->d_lamf, sizeof(double) * nf);
+    ALLOC(c->d_muf, sizeof(double) * nf);
+    ALLOC(c->d_rhoJ, sizeof(double) * n_elem);
+    ALLOC(c->d_lamf32, sizeof(float) * nf);
+    ALLOC(c->d_muf32, sizeof(float) * nf);
+    ALLOC(c->d_rhoJ32, sizeof(float) * n_elem);
+    ALLOC(c->d_b, sizeof(double) * c->nvel);
+    ALLOC(c->d_sigtmp, sizeof(double) * c->nsig);
+    ALLOC(c->d_x, sizeof(double) * c->nvel);
+    UP(c->d_face_l, c->hm.face_l.data(), sizeof(int32_t) * nf);
+    UP(c->d_face_r, c->hm.face_r.data(), sizeof(int32_t) * nf);
+    UP(c->d_X, c->hm.X.data(), sizeof(double) * n_elem * nv * d);
+    UP(c->d_Jinv, c->hm.Jinv.data(), sizeof(double) * n_elem * d * d);
+    UP(c->d_detJ, c->hm.detJ.data(), sizeof(double) * n_elem);
+    UP(c->d_faceX, c->hm.face_X.data(), sizeof(double) * nf * d * d);
+    UP(c->d_shift, c->hm.shift.data(), sizeof(double) * nf * d);
+    UP(c->d_normal, c->hm.normal.data(), sizeof(double) * nf * d);
+    UP(c->d_xc, c->hm.xc.data(), sizeof(double) * nf * d);
+    UP(c->d_hj, c->hm.hj.data(), sizeof(double) * nf);
+    // blocks D_{i,j} and dual mass matrices, exact for degree 2p + 1 on every sub-cell
+    Rule rv = simplex_rule(d, c->rt.p + 2), rf = simplex_rule(d - 1, c->rt.p + 2);
+    std::vector<double> pv, pf;
+    for (int q = 0; q < rv.n(); ++q) {
+        for (int a = 0; a < d; ++a) pv.push_back(rv.pts[q * d + a]);
+        pv.push_back(rv.wts[q]);
+    }
+    for (int q = 0; q < rf.n(); ++q) {
+        for (int a = 0; a < d - 1; ++a) pf.push_back(rf.pts[q * (d - 1) + a]);
+        pf.push_back(rf.wts[q]);
+    }
+    double *d_rv = nullptr, *d_rf = nullptr;
+    ALLOC(d_rv, sizeof(double) * pv.size());
+    ALLOC(d_rf, sizeof(double) * pf.size());
+    UP(d_rv, pv.data(), sizeof(double) * pv.size());
+    UP(d_rf, pf.data(), sizeof(double) * pf.size());
+    STDG_CUDA(c, launch_precompute(c, d_rv, d_rf, rv.n(), rf.n()));
+    cudaError_t e = launch_orthonormalize(c);
+    if (e == cudaErrorInvalidValue) STDG_FAIL(c, STDG_EMESH, "dual mass matrix not positive definite");
+    STDG_CUDA(c, e);
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, d_rv);
+    dev_free(c, d_rf);
+    dev_free(c, c->d_Mdual);   // only the Cholesky factors are kept
+    c->d_Mdual = nullptr;
+#undef ALLOC
+#undef UP
+    c->have_mesh = true;
+    if ((rc = alloc_state(c, 1)) != STDG_OK) return rc;
+    if ((rc = solver_setup(c)) != STDG_OK) return rc;
+    if (c->opt.precision != STDG_FP64 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return STDG_OK;
+}
+
+int stdg_set_material(stdg_ctx* c, const double* lambda, const double* mu, const double* rho) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    const int64_t ne = c->n_elem, nf = c->n_face;
+    if (!lambda || !mu || !rho) STDG_FAIL(c, STDG_EINVAL, "null material array");
+    for (int64_t i = 0; i < ne; ++i)
+        if (!std::isfinite(lambda[i]) || !std::isfinite(mu[i]) || !std::isfinite(rho[i]) || !(mu[i] > 0) ||
+            !(rho[i] > 0) || lambda[i] < 0)
+            STDG_FAIL(c, STDG_EINVAL, "material must be finite with lambda >= 0, mu > 0, rho > 0");
+    c->lam_e.assign(lambda, lambda + ne);
+    c->mu_e.assign(mu, mu + ne);
+    c->rho_e.assign(rho, rho + ne);
+    // E_j: sub-cell-measure-weighted mean over the dual cell (|T_{i,j}| = |T_i| / (d+1))
+    std::vector<double> lf(nf), mf(nf), rj(ne);
+    for (int64_t f = 0; f < nf; ++f) {
+        const int64_t l = c->hm.face_l[f], r = c->hm.face_r[f];
+        double wl = c->hm.detJ[l], wr = r >= 0 ? c->hm.detJ[r] : 0.0;
+        lf[f] = (wl * lambda[l] + (r >= 0 ? wr * lambda[r] : 0.0)) / (wl + wr);
+        mf[f] = (wl * mu[l] + (r >= 0 ? wr * mu[r] : 0.0)) / (wl + wr);
+    }
+    for (int64_t i = 0; i < ne; ++i) rj[i] = rho[i] * c->hm.detJ[i];
+    STDG_CUDA(c, cudaMemcpy(c->d_lamf, lf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+    STDG_CUDA(c, cudaMemcpy(c->d_muf, mf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+    STDG_CUDA(c, cudaMemcpy(c->d_rhoJ, rj.data(), sizeof(double) * ne, cudaMemcpyHostToDevice));
+    c->have_material = true;
+    return upload_material32(c);
+}
+
+int stdg_set_shots(stdg_ctx* c, int n_shots) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    if (n_shots < 1) STDG_FAIL(c, STDG_EINVAL, "n_shots must be >= 1");
+    c->have_sources = 0;
+    return alloc_state(c, n_shots);
+}
+
+int stdg_set_state(stdg_ctx* c, int shot, const double* v_tr, const double* sig_tr) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    if (shot < 0 || shot >= c->n_shots || !v_tr || !sig_tr) STDG_FAIL(c, STDG_EINVAL, "bad shot or null state");
+    if (!all_finite(v_tr, c->ntr) || !all_finite(sig_tr, c->nsig)) STDG_FAIL(c, STDG_EINVAL, "non-finite state");
+    STDG_CUDA(c, cudaMemcpyAsync(c->d_vtr + shot * c->ntr, v_tr, sizeof(double) * c->ntr, cudaMemcpyHostToDevice, c->stream));
+    // stress arrives in the Taylor-monomial basis; the state is kept in orthonormal coordinates
+    STDG_CUDA(c, cudaMemcpyAsync(c->d_sigtmp, sig_tr, sizeof(double) * c->nsig, cudaMemcpyHostToDevice, c->stream));
+    STDG_CUDA(c, launch_sig_convert(c, c->d_sigtmp, c->d_sigtr + shot * c->nsig, 0));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return STDG_OK;
+}
+
+int stdg_get_state(stdg_ctx* c, int shot, double* v_tr, double* sig_tr) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    if (shot < 0 || shot >= c->n_shots) STDG_FAIL(c, STDG_EINVAL, "bad shot");
+    if (v_tr) STDG_CUDA(c, cudaMemcpyAsync(v_tr, c->d_vtr + shot * c->ntr, sizeof(double) * c->ntr, cudaMemcpyDeviceToHost, c->stream));
+    if (sig_tr) {
+        STDG_CUDA(c, launch_sig_convert(c, c->d_sigtr + shot * c->nsig, c->d_sigtmp, 1));
+        STDG_CUDA(c, cudaMemcpyAsync(sig_tr, c->d_sigtmp, sizeof(double) * c->nsig, cudaMemcpyDeviceToHost, c->stream));
+    }
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return STDG_OK;
+}
+
+int stdg_set_plane_wave(stdg_ctx* c, int shot, int kind, const double* n, const double* pol, double amp, double t) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (shot < 0 || shot >= c->n_shots || !n || (kind != 0 && kind != 1)) STDG_FAIL(c, STDG_EINVAL, "bad plane-wave arguments");
+    if (!all_finite(n, c->dim) || (pol && !all_finite(pol, c->dim)) || !std::isfinite(amp) || !std::isfinite(t))
+        STDG_FAIL(c, STDG_EINVAL, "non-finite plane-wave argument");
+    double nn = 0;
+    for (int a = 0; a < c->dim; ++a) nn += n[a] * n[a];
+    if (!(nn > 0)) STDG_FAIL(c, STDG_EINVAL, "zero wave vector");
+    if (kind == 1 && c->dim == 3 && !pol) STDG_FAIL(c, STDG_EINVAL, "3D S wave needs a polarisation");
+    Rule r = simplex_rule(c->dim, 2 * c->rt.p + 8);
+    std::vector<double> pr;
+    for (int q = 0; q < r.n(); ++q) {
+        for (int a = 0; a < c->dim; ++a) pr.push_back(r.pts[q * c->dim + a]);
+        pr.push_back(r.wts[q]);
+    }
+    double* d_r = nullptr;
+    int rc = dev_alloc(c, (void**)&d_r, sizeof(double) * pr.size());
+    if (rc != STDG_OK) return rc;
+    STDG_CUDA(c, cudaMemcpy(d_r, pr.data(), sizeof(double) * pr.size(), cudaMemcpyHostToDevice));
+    STDG_CUDA(c, launch_project_plane_wave(c, shot, kind, n, pol, amp, t, d_r, r.n()));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, d_r);
+    c->t = t;
+    return STDG_OK;
+}
+
+int stdg_set_sources(stdg_ctx* c, int n_shots, const double* xs, const double* dir, double f0, double t_delay, double a1) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    const int d = c->dim, NP = c->Nphi;
+    if (n_shots < 1 || !xs || !dir) STDG_FAIL(c, STDG_EINVAL, "bad source arguments");
+    if (!all_finite(xs, (int64_t)n_shots * d) || !all_finite(dir, (int64_t)n_shots * d) || !std::isfinite(f0) ||
+        !std::isfinite(t_delay) || !std::isfinite(a1))
+        STDG_FAIL(c, STDG_EINVAL, "non-finite source argument");
+    int rc = alloc_state(c, n_shots);
+    if (rc != STDG_OK) return rc;
+    std::vector<double> host((size_t)n_shots * (d + NP));
+    c->src_elem.assign(n_shots, 0);
+    for (int s = 0; s < n_shots; ++s) {
+        double y[3];
+        int64_t e = locate_point(c->hm, xs + s * d, y);
+        if (e < 0) STDG_FAIL(c, STDG_EINVAL, "source outside the mesh");
+        c->src_elem[s] = e;
+        for (int a = 0; a < d; ++a) host[s * (d + NP) + a] = dir[s * d + a];
+        eval_phi_host(c, e, y, &host[s * (d + NP) + d]);
+    }
+    dev_free(c, c->d_src);
+    c->d_src = nullptr;
+    if ((rc = dev_alloc(c, (void**)&c->d_src, sizeof(double) * host.size())) != STDG_OK) return rc;
+    STDG_CUDA(c, cudaMemcpy(c->d_src, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice));
+    c->src_f0 = f0;
+    c->src_td = t_delay;
+    c->src_a1 = a1;
+    c->have_sources = 1;
+    solver_invalidate_graph(c);
+    return STDG_OK;
+}
+
+int stdg_set_receivers(stdg_ctx* c, int n_rec, const double* xr) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    const int d = c->dim, NP = c->Nphi;
+    if (n_rec < 0 || (n_rec > 0 && !xr)) STDG_FAIL(c, STDG_EINVAL, "bad receiver arguments");
+    if (n_rec > 0 && !all_finite(xr, (int64_t)n_rec * d)) STDG_FAIL(c, STDG_EINVAL, "non-finite receiver position");
+    std::vector<int32_t> el(n_rec);
+    std::vector<double> phi((size_t)n_rec * NP);
+    for (int r = 0; r < n_rec; ++r) {
+        double y[3];
+        int64_t e = locate_point(c->hm, xr + r * d, y);
+        if (e < 0) STDG_FAIL(c, STDG_EINVAL, "receiver outside the mesh");
+        el[r] = (int32_t)e;
+        eval_phi_host(c, e, y, &phi[r * NP]);
+    }
+    dev_free(c, c->d_rec_elem);
+    dev_free(c, c->d_rec_phi);
+    dev_free(c, c->d_records);
+    c->d_rec_elem = nullptr;
+    c->d_rec_phi = c->d_records = nullptr;
+    c->n_rec = n_rec;
+    c->rec_steps = 0;
+    c->rec_cap_steps = 0;
+    solver_invalidate_graph(c);
+    if (n_rec == 0) return STDG_OK;
+    int rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_rec_elem, sizeof(int32_t) * n_rec)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_rec_phi, sizeof(double) * n_rec * NP)) != STDG_OK) return rc;
+    STDG_CUDA(c, cudaMemcpy(c->d_rec_elem, el.data(), sizeof(int32_t) * n_rec, cudaMemcpyHostToDevice));
+    STDG_CUDA(c, cudaMemcpy(c->d_rec_phi, phi.data(), sizeof(double) * n_rec * NP, cudaMemcpyHostToDevice));
+    return STDG_OK;
+}
+
+static int ensure_records(stdg_ctx* c, int n_steps) {
+    if (c->n_rec == 0) return STDG_OK;
+    const int64_t need = c->rec_steps + n_steps;
+    if (need <= c->rec_cap_steps) return STDG_OK;
+    int64_t cap = std::max<int64_t>(need, std::max<int64_t>(256, 2 * c->rec_cap_steps));
+    const int64_t per = (int64_t)c->n_rec * c->dim;
+    double* nb = nullptr;
+    int rc = dev_alloc(c, (void**)&nb, sizeof(double) * per * cap * c->n_shots);
+    if (rc != STDG_OK) return rc;
+    if (c->d_records && c->rec_steps > 0)
+        for (int s = 0; s < c->n_shots; ++s)
+            STDG_CUDA(c, cudaMemcpy(nb + s * cap * per, c->d_records + s * c->rec_cap_steps * per,
+                                    sizeof(double) * per * c->rec_steps, cudaMemcpyDeviceToDevice));
+    dev_free(c, c->d_records);
+    c->d_records = nb;
+    c->rec_cap_steps = cap;
+    solver_invalidate_graph(c);
+    return STDG_OK;
+}
+
+int stdg_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* out) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!(dt > 0) || !std::isfinite(dt) || n_steps < 0) STDG_FAIL(c, STDG_EINVAL, "dt must be > 0 and n_steps >= 0");
+    if (out) std::memset(out, 0, sizeof(*out));
+    if (n_steps == 0) return STDG_OK;
+    if (c->n_rec > 0 && c->rec_steps == 0 && c->rec_cap_steps == 0) { /* first use */ }
+    int rc = ensure_records(c, n_steps);
+    if (rc != STDG_OK) return rc;
+    return solver_step(c, dt, n_steps, out);
+}
+
+int stdg_get_time(stdg_ctx* c, double* t) {
+    CHECK_CTX(c);
+    if (!t) return STDG_EINVAL;
+    *t = c->t;
+    return STDG_OK;
+}
+
+int stdg_set_time(stdg_ctx* c, double t) {
+    CHECK_CTX(c);
+    if (!std::isfinite(t)) STDG_FAIL(c, STDG_EINVAL, "non-finite time");
+    c->t = t;
+    return STDG_OK;
+}
+
+int stdg_energy(stdg_ctx* c, double* out) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!out) return STDG_EINVAL;
+    for (int s = 0; s < c->n_shots; ++s) {
+        STDG_CUDA(c, launch_energy(c, s, c->d_energy + s));
+    }
+    STDG_CUDA(c, cudaMemcpyAsync(out, c->d_energy, sizeof(double) * c->n_shots, cudaMemcpyDeviceToHost, c->stream));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return STDG_OK;
+}
+
+int stdg_read_receivers(stdg_ctx* c, double* out, int64_t cap) {
+    CHECK_CTX(c);
+    if (c->n_rec == 0 || c->rec_steps == 0) return 0;
+    const int64_t per = (int64_t)c->n_rec * c->dim;
+    if (!out || cap < per * c->rec_steps * c->n_shots) STDG_FAIL(c, STDG_EINVAL, "receiver buffer too small");
+    for (int s = 0; s < c->n_shots; ++s)
+        STDG_CUDA(c, cudaMemcpyAsync(out + s * c->rec_steps * per, c->d_records + s * c->rec_cap_steps * per,
+                                     sizeof(double) * per * c->rec_steps, cudaMemcpyDeviceToHost, c->stream));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return (int)c->rec_steps;
+}
+
+int stdg_apply_operator(stdg_ctx* c, double dt, const double* x, double* y) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!x || !y || !(dt > 0)) STDG_FAIL(c, STDG_EINVAL, "bad operator arguments");
+    double *dx = nullptr, *dy = nullptr;
+    int rc;
+    if ((rc = dev_alloc(c, (void**)&dx, sizeof(double) * c->nvel)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&dy, sizeof(double) * c->nvel)) != STDG_OK) { dev_free(c, dx); return rc; }
+    STDG_CUDA(c, cudaMemcpyAsync(dx, x, sizeof(double) * c->nvel, cudaMemcpyHostToDevice, c->stream));
+    STDG_CUDA(c, launch_apply(c, dt, dx, dy, 1.0));
+    STDG_CUDA(c, cudaMemcpyAsync(y, dy, sizeof(double) * c->nvel, cudaMemcpyDeviceToHost, c->stream));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, dx);
+    dev_free(c, dy);
+    return STDG_OK;
+}
+
+int stdg_apply_operator_device(stdg_ctx* c, double dt, const void* x_dev, void* y_dev, int fp32) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!x_dev || !y_dev || !(dt > 0)) STDG_FAIL(c, STDG_EINVAL, "bad operator arguments");
+    if (fp32) {
+        int rc = ensure_fp32(c);
+        if (rc != STDG_OK) return rc;
+        if ((rc = upload_material32(c)) != STDG_OK) return rc;
+        STDG_CUDA(c, launch_apply32(c, dt, (const float*)x_dev, (float*)y_dev, 1.0));
+    } else {
+        STDG_CUDA(c, launch_apply(c, dt, (const double*)x_dev, (double*)y_dev, 1.0));
+    }
+    return STDG_OK;
+}
+
+int stdg_query(stdg_ctx* c, int what, int64_t* out) {
+    CHECK_CTX(c);
+    if (!out) return STDG_EINVAL;
+    switch (what) {
+        case 0: *out = c->n_elem; break;
+        case 1: *out = c->n_face; break;
+        case 2: *out = c->Nphi; break;
+        case 3: *out = c->Npsi; break;
+        case 4: *out = c->Ng; break;
+        case 5: *out = c->s; break;
+        case 6: *out = c->n_shots; break;
+        case 7: *out = c->nvel; break;
+        case 8: *out = c->n_rec; break;
+        case 9: *out = c->hm.n_bnd; break;
+        case 10: *out = (int64_t)c->bytes; break;
+        default: STDG_FAIL(c, STDG_EINVAL, "unknown query");
+    }
+    return STDG_OK;
+}
+
+int stdg_get_faces(stdg_ctx* c, int32_t* face_l, int32_t* face_r) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    if (face_l) std::memcpy(face_l, c->hm.face_l.data(), sizeof(int32_t) * c->n_face);
+    if (face_r) std::memcpy(face_r, c->hm.face_r.data(), sizeof(int32_t) * c->n_face);
+    return STDG_OK;
+}
+
+int stdg_time_operator(stdg_ctx* c, double dt, int fp32, int n, double* ms_out) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (n < 1 || !ms_out) STDG_FAIL(c, STDG_EINVAL, "bad timing arguments");
+    int rc;
+    if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
+    if (fp32 && (rc = upload_material32(c)) != STDG_OK) return rc;
+    void *dx = nullptr, *dy = nullptr;
+    const size_t bytes = (fp32 ? sizeof(float) : sizeof(double)) * c->nvel;
+    if ((rc = dev_alloc(c, &dx, bytes)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, &dy, bytes)) != STDG_OK) { dev_free(c, dx); return rc; }
+    STDG_CUDA(c, cudaMemsetAsync(dx, 0, bytes, c->stream));
+    STDG_CUDA(c, cudaMemsetAsync(dy, 0, bytes, c->stream));
+    STDG_CUDA(c, launch_face_only(c, dt, dx, dy, 1.0, fp32));   // warm-up
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < n; ++i) STDG_CUDA(c, launch_face_only(c, dt, dx, dy, 1.0, fp32));
+    cudaEventRecord(e1, c->stream);
+    STDG_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = ms / n;
+    dev_free(c, dx);
+    dev_free(c, dy);
+    return STDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal declarations of the stdg library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "stdg.h"
+
+namespace stdg {
+
+constexpr int kMaxNP = 20;   // N_phi = N_psi <= 20 (3D p=3, 2D p=4: 15)
+constexpr int kMaxNG = 4;    // N_gamma <= 4
+
+// Reference-element and time-basis tables, built on the host (host_setup.cpp) and
+// copied to the device once per context.
+struct RefTables {
+    int dim, p, pg, Nphi, Npsi, Ng, s;
+    int exps[kMaxNP][3];          // monomial exponents, graded-lex (dual basis and Vandermonde)
+    double coef[kMaxNP * kMaxNP]; // phi_k(xi) = sum_a coef[a*Nphi + k] xi^a
+    double Mref[kMaxNP * kMaxNP]; // int_{ref simplex} phi_k phi_m
+    double MrefInv[kMaxNP * kMaxNP];
+    double tnodes[kMaxNG], W[kMaxNG], g0[kMaxNG], g1[kMaxNG];
+    double T[kMaxNG * kMaxNG];    // gamma(1) gamma(1)^T - K
+    double Tinv[kMaxNG * kMaxNG];
+    double S[kMaxNG * kMaxNG];    // W T^{-1} W  (time factor of the Schur term)
+    double Tinv_g0[kMaxNG];       // T^{-1} gamma(0)
+    double u_tr[kMaxNG];          // gamma(1)^T T^{-1} W  (stress trace weights)
+    double kappa;                 // gamma(1)^T T^{-1} gamma(0)
+};
+
+// A quadrature rule on a reference simplex: points (n x dim, barycentric-free
+// reference coordinates) and weights summing to 1/dim!.
+struct Rule {
+    int dim = 0;
+    std::vector<double> pts, wts;
+    int n() const { return (int)wts.size(); }
+};
+
+void build_ref_tables(int dim, int p, int pg, RefTables* out);
+Rule simplex_rule(int dim, int n_per_dir);
+void gauss_legendre01(int n, double* x, double* w);
+void lagrange_time(const RefTables& rt, double tau, double* val);
+
+// Host-side mesh connectivity (Sec. 3): faces, l(j), r(j), normals, dual cells.
+struct HostMesh {
+    int dim = 0;
+    int64_t n_elem = 0, n_face = 0, n_bnd = 0;
+    std::vector<double> X;        // unwrapped element vertices [e][dim+1][dim]
+    std::vector<double> Jinv;     // [e][dim][dim]  xi = Jinv (x - X0)
+    std::vector<double> detJ;     // [e]
+    std::vector<int32_t> face_l, face_r;   // r = -1 on the boundary
+    std::vector<int8_t> face_fl, face_fr;  // local face index (opposite local vertex)
+    std::vector<int32_t> elem_face;        // [e][dim+1]
+    std::vector<double> face_X;   // face vertices in the frame of l(j) [f][dim][dim]
+    std::vector<double> shift;    // r-frame -> l-frame translation [f][dim]
+    std::vector<double> normal;   // unit, from l to r [f][dim]
+    std::vector<double> xc, hj;   // dual-cell centre (l frame) and scale
+    std::vector<double> period;   // dim entries (0 = not periodic), empty if none
+};
+
+// Returns STDG_OK or STDG_EMESH (message in err).
+int build_host_mesh(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* ev,
+                    const double* period, HostMesh* m, std::string* err);
+// Element containing x (lowest index wins); writes the point in that element's frame.
+int64_t locate_point(const HostMesh& m, const double* x, double* x_local);
+
+// Krylov workspace and step graph state live in the context.
+struct Scalars;   // device-side solver scalars (defined in solver.cu)
+
+}  // namespace stdg
+
+struct stdg_ctx {
+    int dim = 0;
+    stdg_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool have_mesh = false, have_material = false;
+
+    stdg::RefTables rt{};
+    stdg::HostMesh hm;
+    int Nphi = 0, Npsi = 0, Ng = 0, s = 0;
+    int64_t n_elem = 0, n_face = 0;
+    int64_t nvel = 0;      // velocity values per shot per slab: n_elem*dim*Ng*Nphi
+    int64_t ntr = 0;       // velocity trace values per shot: n_elem*dim*Nphi
+    int64_t nsig = 0;      // stress trace values per shot: n_face*s*Npsi
+    int n_shots = 1;
+    double t = 0.0;
+
+    // ---- device: tables and geometry
+    stdg::RefTables* d_rt = nullptr;
+    int32_t *d_face_l = nullptr, *d_face_r = nullptr;
+    double *d_X = nullptr, *d_Jinv = nullptr, *d_detJ = nullptr;
+    double *d_faceX = nullptr, *d_shift = nullptr, *d_normal = nullptr, *d_xc = nullptr, *d_hj = nullptr;
+    double *d_D = nullptr;      // orthonormalised blocks D~_{i,j} [face][side][l][n][m] (FP64)
+    double *d_L = nullptr;      // Cholesky factors of the dual mass matrices (lower, [face][m][m'])
+    double *d_Mdual = nullptr;  // dual mass matrices (set-up workspace)
+    float *d_D32 = nullptr;     // FP32 copy of D~
+    double *d_lamf = nullptr, *d_muf = nullptr, *d_rhoJ = nullptr;    // per face / element
+    float *d_lamf32 = nullptr, *d_muf32 = nullptr, *d_rhoJ32 = nullptr;
+
+    // ---- device: state (shot-major)
+    double *d_vtr = nullptr, *d_sigtr = nullptr;
+    double *d_b = nullptr, *d_x = nullptr;      // per shot slab RHS and solution
+    double *d_sigtmp = nullptr;                  // one shot's stress trace (basis conversions)
+    double *d_energy = nullptr;
+
+    // ---- sources / receivers
+    int have_sources = 0;
+    std::vector<int64_t> src_elem;     // per shot
+    double *d_src = nullptr;           // per shot: [dim dir][Nphi phi(x_s)]
+    int32_t *d_src_elem = nullptr;
+    double src_f0 = 0, src_td = 0, src_a1 = 0;
+    double* d_gl8 = nullptr;           // 8-point Gauss-Legendre rule on [0,1]: nodes, weights
+    std::vector<double> lam_e, mu_e, rho_e;   // host copies of the material
+    int n_rec = 0;
+    int32_t *d_rec_elem = nullptr;
+    double *d_rec_phi = nullptr;       // [rec][Nphi]
+    double *d_records = nullptr;       // [shot][cap_steps][rec][dim]
+    int64_t rec_cap_steps = 0, rec_steps = 0;
+
+    // ---- solver workspace (solver.cu)
+    void* ws = nullptr;
+
+    // bookkeeping
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+};
+
+// Error helpers
+#define STDG_FAIL(ctx, code, msg) do { (ctx)->err = (msg); return (code); } while (0)
+#define STDG_CUDA(ctx, call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { \
+    (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+    return e_ == cudaErrorMemoryAllocation ? STDG_ENOMEM : STDG_ECUDA; } } while (0)
+
+namespace stdg {
+int dev_alloc(stdg_ctx* c, void** p, size_t bytes);
+void dev_free_all(stdg_ctx* c);
+
+// kernels.cu -- launchers (all on c->stream); return cudaGetLastError()
+cudaError_t launch_precompute(stdg_ctx* c, const double* d_rule_v, const double* d_rule_f, int nq_v, int nq_f);
+cudaError_t launch_orthonormalize(stdg_ctx* c);
+cudaError_t launch_sig_convert(stdg_ctx* c, const double* in, double* out, int dir);
+cudaError_t launch_to_fp32(stdg_ctx* c);
+// y = A x (cfac scales the Schur part; 1 for the operator).  With xidx != null the input is
+// x + (*xidx) * ld, the index read on the device (Krylov basis column j).
+cudaError_t launch_apply(stdg_ctx* c, double dt, const double* x, double* y, double cfac,
+                         const int* xidx = nullptr, int64_t ld = 0);
+cudaError_t launch_apply32(stdg_ctx* c, double dt, const float* x, float* y, double cfac,
+                           const int* xidx = nullptr, int64_t ld = 0);
+cudaError_t launch_face_only(stdg_ctx* c, double dt, const void* x, void* y, double cfac, int fp32);
+cudaError_t launch_rhs(stdg_ctx* c, double dt, const double* dparams, int shot, double* b);
+cudaError_t launch_stress_update(stdg_ctx* c, double dt, int shot, const double* x);
+cudaError_t launch_traces(stdg_ctx* c, int shot, const double* x);
+cudaError_t launch_receivers(stdg_ctx* c, const double* dparams, int shot);
+cudaError_t launch_energy(stdg_ctx* c, int shot, double* d_out);
+cudaError_t launch_project_plane_wave(stdg_ctx* c, int shot, int kind, const double* n, const double* pol,
+                                      double amp, double t, const double* d_rule, int nq);
+cudaError_t launch_initial_guess(stdg_ctx* c, int shot, double* x);
+
+// solver.cu
+int solver_setup(stdg_ctx* c);
+void solver_free(stdg_ctx* c);
+int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st);
+}  // namespace stdg
