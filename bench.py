@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the staggered space-time DG solver (arXiv:1802.04516).
+
+Workload: the 2D layered medium on [0,2]x[0,1] with 448x224x2 = 200,704 jittered
+triangles, 1% slivers, free surface, p = p_gamma = 3, one Ricker point source, 16
+receivers, dt at 10x the explicit CFL.  One "step" is one space-time slab of the whole
+path: right-hand side, the preconditioned Krylov solve of the Schur velocity system to
+1e-8 relative residual, stress back-substitution, traces and receivers.
+
+Metric: space-time DOF-steps/s = (velocity + stress space-time DOFs per slab) x steps x
+shots / time.  `value` is the mixed-precision path (FP32 operator and Krylov, FP64
+refinement); the FP64 path is reported under "fp64".  With --gpus N (torchrun) every rank
+runs its own independent shot on its own GPU (weak scaling, no collective on the data
+path); the timed region is bracketed by barriers and the max over ranks is used.
+
+--impl reference times the CPU oracle (explicit sparse assembly + SuperLU) on a bounded
+sample of the same construction.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_TFLOPS = 1.25          # nominal dense FP64 of one GB300 (no measured figure in the peaks file)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def dofs_per_slab(w, n_face):
+    from math import comb
+    nphi = comb(w.p + w.dim, w.dim)
+    ng = w.p_gamma + 1
+    s = 3 if w.dim == 2 else 6
+    return w.n_elem * w.dim * nphi * ng + n_face * s * nphi * ng
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def build_solver(w, precision, stream, shot_offset=0.0):
+    from paper_1802_04516_gb300.binding import Solver
+    s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=30,
+               inner_tol=1e-3 if precision != "fp64" else 1e-4, use_graph=True, stream=stream, preconditioner=1)
+    s.set_mesh(w.xyz, w.elem_vert, w.period)
+    s.set_material(w.lam, w.mu, w.rho)
+    xs = np.array(w.shots_xs) + np.array([shot_offset, 0.0])
+    s.set_sources(xs, w.shots_dir, w.f0, w.t_delay, w.a1)
+    s.set_receivers(w.receivers)
+    return s
+
+
+def time_steps(torch, s, w, steps, warmup, stream, dist):
+    for _ in range(warmup):
+        s.step(w.dt, 1)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters, launches = [], 0
+    e0.record(stream)
+    for _ in range(steps):
+        st = s.step(w.dt, 1)
+        iters.append(st["iters_max"])
+        launches += s.query(11)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, iters, launches, st
+
+
+def e2e_steps(torch, s, w, steps, stream):
+    """Same metric through the C ABI with host buffers: per step, upload the carried state
+    from pinned host memory, step, read the state and the receivers back to the host."""
+    v0, s0 = s.get_state()
+    v = torch.empty(v0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    sig = torch.empty(s0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    v[...] = v0
+    sig[...] = s0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rec_bytes = 0
+    for _ in range(steps):
+        s.set_state(v, sig)
+        s.step(w.dt, 1)
+        s.get_state(out=(v, sig))
+    rec = s.read_receivers()
+    rec_bytes = rec.nbytes // max(1, rec.shape[1])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dt * 1e3, v.nbytes + sig.nbytes, v.nbytes + sig.nbytes + rec_bytes
+
+
+def face_kernel_roofline(s, w, fp32, n_face, pk):
+    """Algorithmic bytes / FLOPs of one launch of the operator's face kernel, its measured
+    average duration (CUDA events on the library stream) and the fraction of peak."""
+    from math import comb
+    nphi = comb(w.p + w.dim, w.dim)
+    ng = w.p_gamma + 1
+    d = w.dim
+    ns = 3 if d == 2 else 6
+    wsz = 4 if fp32 else 8
+    nvel = w.n_elem * d * ng * nphi
+    bytes_alg = n_face * (2 * d * nphi * nphi * wsz + 2 * wsz + 8) + nvel * wsz * 3
+    per_face = (2 * (d * d * ng * nphi) * nphi * 2          # D~^T v, both sides
+                + ns * ng * nphi * (d + 3)                 # E : g
+                + ns * ng * nphi * ng * 2                  # time factor S
+                + 2 * (d * ng * nphi) * (d * nphi) * 2)    # D~ h, both sides
+    flops = n_face * per_face
+    ms = s.time_operator(w.dt, fp32=fp32, n=20)
+    if fp32:
+        peak = float(pk.get("hbm_gbs", 6800.0))
+        achieved = bytes_alg / (ms * 1e-3) / 1e9
+        return {"kernel": "face_apply_kernel<float>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
+                "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "face_apply_kernel<double>", "bound": "alu", "achieved": round(achieved, 4),
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+            "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
+            "peak_source": "nominal FP64 1.25 TFLOP/s"}
+
+
+def cpu_baseline(max_seconds=25.0, ny=12, steps=20):
+    """The oracle as it stands (assembly + SuperLU, one core) on a bounded sample of the
+    same construction: ny x 2ny cells, steps slabs; DOF-steps/s over the solve phase."""
+    import synth
+    from oracle.stepper import Simulation
+    w = synth.scaled("c2", ny=ny, steps=steps)
+    t0 = time.perf_counter()
+    sim = Simulation.from_workload(w)
+    sim.set_source(w.shots_xs[0], w.shots_dir[0], w.f0, w.t_delay, w.a1)
+    sim.step(1)                                    # factorisation happens here
+    t1 = time.perf_counter()
+    k = 0
+    while k < steps and time.perf_counter() - t1 < max_seconds:
+        sim.step(1)
+        k += 1
+    t2 = time.perf_counter()
+    rate = dofs_per_slab(w, sim.mesh.n_face) * k / (t2 - t1)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": rate, "unit": "DOF-steps/s", "cores": 1, "cores_available": cores, "kind": "oracle",
+            "sample": "%d-triangle copy of the construction (%dx%d cells), %d slabs after assembly+LU (%.1fs)"
+                      % (w.n_elem, 2 * ny, ny, k, t1 - t0), "seconds": round(t2 - t0, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    cb = cpu_baseline(max_seconds=max(5.0, 4.0 * steps), steps=max(steps + args.warmup, 3))
+    line = {"impl": "reference", "metric": "space-time DOF-steps/s (velocity+stress) at 1e-8 rel residual",
+            "value": cb["value"], "unit": "DOF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "c2_layered_slivers_p3 (scaled copy, CPU oracle)",
+                                            "sample": cb["sample"]},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "DOF-steps/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--ny", type=int, default=224, help="cells in y (224 = the 200,704-triangle mesh)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+        dist = tdist
+    torch.cuda.set_device(local)
+    from paper_1802_04516_gb300 import build as _b
+    if rank == 0:
+        _b.build()
+    if dist is not None:
+        dist.barrier()
+    import synth
+    w = synth.c2_layered_slivers(ny=args.ny, steps=args.steps)
+    stream = torch.cuda.Stream()
+    pk = peaks()
+    with torch.cuda.stream(stream):
+        s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=0.01 * rank)
+        n_face = s.n_face
+        dofs = dofs_per_slab(w, n_face)
+        sampler = ClockSampler(local)
+        sampler.start()
+        ms, iters, launches, st = time_steps(torch, s, w, args.steps, args.warmup, stream, dist)
+        clocks = sampler.stop()
+        value = world * dofs * args.steps / (ms * 1e-3)
+        roof = face_kernel_roofline(s, w, True, n_face, pk)
+        e2e_ms, h2d, d2h = e2e_steps(torch, s, w, max(1, args.steps // 2), stream)
+        e2e_value = dofs * max(1, args.steps // 2) / (e2e_ms * 1e-3) * world
+        fp64 = None
+        if not args.no_fp64 and args.fp64_steps > 0:
+            s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=0.01 * rank)
+            ms64, it64, _, _ = time_steps(torch, s64, w, args.fp64_steps, 1, stream, dist)
+            fp64 = {"value": world * dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
+                    "krylov_iters_per_step": it64, "roofline": face_kernel_roofline(s64, w, False, n_face, pk)}
+            s64.close()
+    if rank != 0:
+        return
+    cb = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": "space-time DOF-steps/s (velocity+stress) at 1e-8 rel residual, mixed FP32/FP64",
+        "value": value, "unit": "DOF-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 operator/Krylov + f64 refinement", "data": "synthetic",
+        "config": {"workload": "c2_layered_slivers_p3: %d triangles (448x224x2, 1%% slivers), p=p_gamma=3, "
+                               "1 Ricker shot/GPU, 16 receivers, dt=%.4g (10x CFL)" % (w.n_elem, w.dt),
+                   "dofs_per_slab": dofs, "n_face": n_face, "preconditioner": "block Jacobi (Pre1)",
+                   "gmres_restart": 30, "l2": "working set (blocks, Krylov basis) > 129 MB L2; no flush",
+                   "parallelism": "independent shot per GPU"},
+        "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"], "refinements_last": st["refinements"],
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "DOF-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "fp64": fp64,
+        "cpu_baseline": cb,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -61,6 +61,8 @@ typedef struct {
     int gmres_restart;  /* GMRES(m) restart length                                      */
     double inner_tol;   /* relative tolerance of the FP32 inner solve (mixed precision)  */
     int use_graph;      /* 1: one CUDA graph per step with device-side loops; 0: host loop */
+    int preconditioner; /* 0: none; 1: block Jacobi "Pre1" (Appendix A, Eq. pre1): exact inverse of
+                           every element's diagonal block, applied on the right (GMRES) or as PCG */
 } stdg_options;
 
 typedef struct {
@@ -142,11 +144,16 @@ int stdg_apply_operator_device(stdg_ctx* ctx, double dt, const void* x_dev, void
 
 /* Sizes: what = 0 n_elem, 1 n_face, 2 N_phi, 3 N_psi, 4 N_gamma, 5 stress comps s,
  * 6 n_shots, 7 velocity values per shot and slab, 8 n_rec, 9 n_boundary_faces,
- * 10 device bytes held. */
+ * 10 device bytes held, 11 kernel executions of the library during the last stdg_step
+ * call (counted on the device, including every iteration of the device-side loops). */
 int stdg_query(stdg_ctx* ctx, int what, int64_t* out);
 
 /* Face table as built by stdg_set_mesh: l(j), r(j) (-1 on the boundary). */
 int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);
+
+/* z = P^{-1} r with the block-Jacobi preconditioner Pre1 for slab size dt (canonical
+ * velocity layout, one shot, FP64, host pointers).  Requires preconditioner = 1. */
+int stdg_apply_preconditioner(stdg_ctx* ctx, double dt, const double* r, double* z);
 
 /* Average device time of `n` launches of the operator's face kernel (fp32 != 0: the
  * FP32 one) on the context stream, measured with CUDA events: *ms_out. */

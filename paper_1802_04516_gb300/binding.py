@@ -20,7 +20,7 @@ PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
 class stdg_options(C.Structure):
     _fields_ = [("p", C.c_int), ("p_gamma", C.c_int), ("scheme", C.c_int), ("precision", C.c_int),
                 ("rel_tol", C.c_double), ("max_iters", C.c_int), ("gmres_restart", C.c_int),
-                ("inner_tol", C.c_double), ("use_graph", C.c_int)]
+                ("inner_tol", C.c_double), ("use_graph", C.c_int), ("preconditioner", C.c_int)]
 
 
 class stdg_stats(C.Structure):
@@ -58,6 +58,7 @@ SIGNATURES = {
     "stdg_query": (C.c_int, [_P, C.c_int, _I64]),
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
+    "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
 }
 
 _lib = None
@@ -103,11 +104,11 @@ class Solver:
     """One library context: a mesh, a medium, shots, and the stepping state."""
 
     def __init__(self, dim, p, p_gamma, scheme="stdg", precision="fp64", rel_tol=1e-8, max_iters=5000,
-                 gmres_restart=30, inner_tol=1e-4, use_graph=True, stream=None):
+                 gmres_restart=30, inner_tol=1e-4, use_graph=True, stream=None, preconditioner=1):
         self.lib = load()
         self.dim = dim
         opt = stdg_options(p, p_gamma, SCHEME[scheme], PRECISION[precision], rel_tol, max_iters, gmres_restart,
-                           inner_tol, 1 if use_graph else 0)
+                           inner_tol, 1 if use_graph else 0, int(preconditioner))
         h = _P()
         rc = self.lib.stdg_create(C.byref(h), dim, C.byref(opt), _P(stream or 0))
         if rc != 0:
@@ -159,9 +160,13 @@ class Solver:
         v, s = _f64(v_tr), _f64(sig_tr)
         self._chk(self.lib.stdg_set_state(self.h, shot, _d(v), _d(s)))
 
-    def get_state(self, shot=0):
-        v = np.zeros((self.n_elem, self.dim, self.Nphi))
-        s = np.zeros((self.n_face, self.n_sig, self.Npsi))
+    def get_state(self, shot=0, out=None):
+        """(v_tr, sig_tr); ``out`` = (v, sig) preallocated float64 arrays (e.g. pinned host memory)."""
+        if out is None:
+            v = np.zeros((self.n_elem, self.dim, self.Nphi))
+            s = np.zeros((self.n_face, self.n_sig, self.Npsi))
+        else:
+            v, s = out
         self._chk(self.lib.stdg_get_state(self.h, shot, _d(v), _d(s)))
         return v, s
 
@@ -219,6 +224,12 @@ class Solver:
     def apply_operator_device(self, dt, x_ptr, y_ptr, fp32=False):
         self._chk(self.lib.stdg_apply_operator_device(self.h, dt, _P(x_ptr), _P(y_ptr), 1 if fp32 else 0))
 
+    def apply_preconditioner(self, dt, r):
+        r = _f64(r).ravel()
+        z = np.zeros_like(r)
+        self._chk(self.lib.stdg_apply_preconditioner(self.h, dt, _d(r), _d(z)))
+        return z
+
     def get_faces(self):
         fl = np.zeros(self.n_face, dtype=np.int32)
         fr = np.zeros(self.n_face, dtype=np.int32)
@@ -232,10 +243,10 @@ class Solver:
 
 
 def solver_from_workload(w, precision="fp64", rel_tol=1e-8, max_iters=5000, gmres_restart=30, inner_tol=1e-4,
-                         use_graph=True, stream=None, with_sources=True, with_receivers=True):
+                         use_graph=True, stream=None, with_sources=True, with_receivers=True, preconditioner=1):
     """Build a Solver for a ``synth.Workload`` (mesh, media, plane wave or sources, receivers)."""
     s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol, max_iters, gmres_restart, inner_tol, use_graph,
-               stream)
+               stream, preconditioner)
     s.set_mesh(w.xyz, w.elem_vert, w.period)
     s.set_material(w.lam, w.mu, w.rho)
     if with_sources and w.shots_xs is not None:

@@ -104,6 +104,44 @@ static int upload_material32(stdg_ctx* c) {
     return STDG_OK;
 }
 
+// Block-Jacobi preconditioner set-up: per-element eigen-decomposition (dt-independent).
+static int setup_pre1(stdg_ctx* c) {
+    const int n = c->dim * c->Nphi;
+    const int64_t ne = c->n_elem;
+    int rc;
+    if (!c->d_preV) {
+        if ((rc = dev_alloc(c, (void**)&c->d_preV, sizeof(double) * ne * n * n)) != STDG_OK) return rc;
+        if ((rc = dev_alloc(c, (void**)&c->d_preLam, sizeof(double) * ne * n)) != STDG_OK) return rc;
+        if ((rc = dev_alloc(c, (void**)&c->d_preB, sizeof(double) * ne * n * c->Ng * c->Ng)) != STDG_OK) return rc;
+        if (c->opt.precision != STDG_FP64) {
+            if ((rc = dev_alloc(c, (void**)&c->d_preV32, sizeof(float) * ne * n * n)) != STDG_OK) return rc;
+            if ((rc = dev_alloc(c, (void**)&c->d_preB32, sizeof(float) * ne * n * c->Ng * c->Ng)) != STDG_OK) return rc;
+        }
+    }
+    double* d_Rinv = nullptr;
+    int* d_status = nullptr;
+    if ((rc = dev_alloc(c, (void**)&d_Rinv, sizeof(double) * c->Nphi * c->Nphi)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&d_status, sizeof(int))) != STDG_OK) return rc;
+    std::vector<double> Ri(c->Nphi * c->Nphi);
+    for (int i = 0; i < c->Nphi * c->Nphi; ++i) Ri[i] = c->rt.MrefLinv[i];
+    STDG_CUDA(c, cudaMemcpy(d_Rinv, Ri.data(), sizeof(double) * Ri.size(), cudaMemcpyHostToDevice));
+    STDG_CUDA(c, cudaMemset(d_status, 0, sizeof(int)));
+    STDG_CUDA(c, launch_pre1_setup(c, d_Rinv, c->d_elem_face, d_status));
+    int status = 0;
+    STDG_CUDA(c, cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, d_Rinv);
+    dev_free(c, d_status);
+    if (status) STDG_FAIL(c, STDG_ECUDA, "block-Jacobi eigen-decomposition did not converge");
+    if (c->d_preV32) {
+        const int64_t nv = ne * n * n;
+        extern cudaError_t launch_cast32(stdg_ctx*, const double*, float*, int64_t);
+        STDG_CUDA(c, launch_cast32(c, c->d_preV, c->d_preV32, nv));
+    }
+    c->pre_dt = -1.0;
+    return STDG_OK;
+}
+
 }  // namespace stdg
 
 using namespace stdg;
@@ -182,6 +220,10 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
         if (p != keep_rt && p != keep_gl) cudaFree(p);
     c->allocs.assign({keep_rt, keep_gl});
     c->d_face_l = c->d_face_r = nullptr;
+    c->d_elem_face = nullptr;
+    c->d_preV = c->d_preLam = c->d_preB = nullptr;
+    c->d_preV32 = c->d_preB32 = nullptr;
+    c->pre_dt = -1.0;
     c->d_X = c->d_Jinv = c->d_detJ = c->d_faceX = c->d_shift = c->d_normal = c->d_xc = c->d_hj = nullptr;
     c->d_D = c->d_L = c->d_Mdual = nullptr;
     c->d_D32 = nullptr;
@@ -208,6 +250,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
 #define ALLOC(ptr, bytes) do { if ((rc = dev_alloc(c, (void**)&(ptr), (bytes))) != STDG_OK) return rc; } while (0)
 #define UP(dst, src, bytes) STDG_CUDA(c, cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice))
     ALLOC(c->d_face_l, sizeof(int32_t) * nf);
+    ALLOC(c->d_elem_face, sizeof(int32_t) * n_elem * nv);
     ALLOC(c->d_face_r, sizeof(int32_t) * nf);
     ALLOC(c->d_X, sizeof(double) * n_elem * nv * d);
     ALLOC(c->d_Jinv, sizeof(double) * n_elem * d * d);
@@ -230,6 +273,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     ALLOC(c->d_sigtmp, sizeof(double) * c->nsig);
     ALLOC(c->d_x, sizeof(double) * c->nvel);
     UP(c->d_face_l, c->hm.face_l.data(), sizeof(int32_t) * nf);
+    UP(c->d_elem_face, c->hm.elem_face.data(), sizeof(int32_t) * n_elem * nv);
     UP(c->d_face_r, c->hm.face_r.data(), sizeof(int32_t) * nf);
     UP(c->d_X, c->hm.X.data(), sizeof(double) * n_elem * nv * d);
     UP(c->d_Jinv, c->hm.Jinv.data(), sizeof(double) * n_elem * d * d);
@@ -287,6 +331,7 @@ int stdg_set_material(stdg_ctx* c, const double* lambda, const double* mu, const
     c->mu_e.assign(mu, mu + ne);
     c->rho_e.assign(rho, rho + ne);
     // E_j: sub-cell-measure-weighted mean over the dual cell (|T_{i,j}| = |T_i| / (d+1))
+    int rc;
     std::vector<double> lf(nf), mf(nf), rj(ne);
     for (int64_t f = 0; f < nf; ++f) {
         const int64_t l = c->hm.face_l[f], r = c->hm.face_r[f];
@@ -299,7 +344,10 @@ int stdg_set_material(stdg_ctx* c, const double* lambda, const double* mu, const
     STDG_CUDA(c, cudaMemcpy(c->d_muf, mf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
     STDG_CUDA(c, cudaMemcpy(c->d_rhoJ, rj.data(), sizeof(double) * ne, cudaMemcpyHostToDevice));
     c->have_material = true;
-    return upload_material32(c);
+    rc = upload_material32(c);
+    if (rc != STDG_OK) return rc;
+    if (c->opt.preconditioner) return setup_pre1(c);
+    return STDG_OK;
 }
 
 int stdg_set_shots(stdg_ctx* c, int n_shots) {
@@ -545,6 +593,7 @@ int stdg_query(stdg_ctx* c, int what, int64_t* out) {
         case 8: *out = c->n_rec; break;
         case 9: *out = c->hm.n_bnd; break;
         case 10: *out = (int64_t)c->bytes; break;
+        case 11: *out = c->last_launches; break;
         default: STDG_FAIL(c, STDG_EINVAL, "unknown query");
     }
     return STDG_OK;
@@ -555,6 +604,28 @@ int stdg_get_faces(stdg_ctx* c, int32_t* face_l, int32_t* face_r) {
     NEED_MESH(c);
     if (face_l) std::memcpy(face_l, c->hm.face_l.data(), sizeof(int32_t) * c->n_face);
     if (face_r) std::memcpy(face_r, c->hm.face_r.data(), sizeof(int32_t) * c->n_face);
+    return STDG_OK;
+}
+
+int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!c->opt.preconditioner || !c->d_preV) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
+    if (!r || !z || !(dt > 0)) STDG_FAIL(c, STDG_EINVAL, "bad preconditioner arguments");
+    if (c->pre_dt != dt) {
+        STDG_CUDA(c, launch_pre1_time(c, dt));
+        c->pre_dt = dt;
+    }
+    double *dr = nullptr, *dz = nullptr;
+    int rc;
+    if ((rc = dev_alloc(c, (void**)&dr, sizeof(double) * c->nvel)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, (void**)&dz, sizeof(double) * c->nvel)) != STDG_OK) { dev_free(c, dr); return rc; }
+    STDG_CUDA(c, cudaMemcpyAsync(dr, r, sizeof(double) * c->nvel, cudaMemcpyHostToDevice, c->stream));
+    STDG_CUDA(c, launch_pre1_apply(c, dr, dz, nullptr, 0));
+    STDG_CUDA(c, cudaMemcpyAsync(z, dz, sizeof(double) * c->nvel, cudaMemcpyDeviceToHost, c->stream));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, dr);
+    dev_free(c, dz);
     return STDG_OK;
 }
 

@@ -143,6 +143,18 @@ void build_ref_tables(int dim, int p, int pg, RefTables* rt) {
     }
     std::memcpy(rt->MrefInv, rt->Mref, sizeof(double) * n * n);
     invert(n, rt->MrefInv);
+    {   // Cholesky factor R of M_ref and its inverse (lower triangular)
+        std::vector<double> R(n * n, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double s = rt->Mref[i * n + j];
+                for (int k = 0; k < j; ++k) s -= R[i * n + k] * R[j * n + k];
+                R[i * n + j] = i == j ? std::sqrt(s) : s / R[j * n + j];
+            }
+        invert(n, R.data());
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) rt->MrefLinv[i * n + j] = j <= i ? R[i * n + j] : 0.0;
+    }
     // time basis on the Gauss-Legendre points of [0,1]
     int G = rt->Ng;
     gauss_legendre01(G, rt->tnodes, rt->W);

@@ -223,12 +223,12 @@ cudaError_t launch_precompute(stdg_ctx* c, const double* d_rule_v, const double*
         cudaFuncSetAttribute(pair_blocks_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pair_blocks_kernel<2><<<grid, 128, smem, c->stream>>>(c->d_rt, c->n_face, c->d_face_l, c->d_face_r, c->d_X, c->d_Jinv,
                                                               c->d_faceX, c->d_shift, c->d_normal, c->d_xc, c->d_hj,
-                                                              d_rule_v, nq_v, d_rule_f, nq_f, c->d_D, c->d_Mdual);
+                                                              d_rule_v, nq_v, d_rule_f, nq_f, c->d_D, c->d_Mdual); note_launch(c);
     } else {
         cudaFuncSetAttribute(pair_blocks_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pair_blocks_kernel<3><<<grid, 128, smem, c->stream>>>(c->d_rt, c->n_face, c->d_face_l, c->d_face_r, c->d_X, c->d_Jinv,
                                                               c->d_faceX, c->d_shift, c->d_normal, c->d_xc, c->d_hj,
-                                                              d_rule_v, nq_v, d_rule_f, nq_f, c->d_D, c->d_Mdual);
+                                                              d_rule_v, nq_v, d_rule_f, nq_f, c->d_D, c->d_Mdual); note_launch(c);
     }
     return cudaGetLastError();
 }
@@ -278,7 +278,7 @@ cudaError_t launch_orthonormalize(stdg_ctx* c) {
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
     orthonormalize_kernel<<<(unsigned)((c->n_face + 127) / 128), 128, 0, c->stream>>>(c->n_face, c->Nphi, c->dim, c->d_Mdual,
-                                                                                    c->d_L, c->d_D, d_bad);
+                                                                                    c->d_L, c->d_D, d_bad); note_launch(c);
     int bad = 0;
     cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaStreamSynchronize(c->stream);
@@ -317,7 +317,7 @@ __global__ void sig_convert_kernel(int64_t n_face, int NS, int NP, const double*
 
 cudaError_t launch_sig_convert(stdg_ctx* c, const double* in, double* out, int dir) {
     const int64_t n = c->n_face * c->s;
-    sig_convert_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(c->n_face, c->s, c->Nphi, c->d_L, in, out, dir);
+    sig_convert_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(c->n_face, c->s, c->Nphi, c->d_L, in, out, dir); note_launch(c);
     return cudaGetLastError();
 }
 
@@ -325,9 +325,14 @@ __global__ void to_fp32_kernel(int64_t n, const double* __restrict__ a, float* _
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = (float)a[i];
 }
 
+cudaError_t launch_cast32(stdg_ctx* c, const double* a, float* b, int64_t n) {
+    to_fp32_kernel<<<4096, 256, 0, c->stream>>>(n, a, b); note_launch(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_fp32(stdg_ctx* c) {
     const int64_t nD = c->n_face * 2 * c->dim * c->Nphi * c->Nphi;
-    to_fp32_kernel<<<4096, 256, 0, c->stream>>>(nD, c->d_D, c->d_D32);
+    to_fp32_kernel<<<4096, 256, 0, c->stream>>>(nD, c->d_D, c->d_D32); note_launch(c);
     return cudaGetLastError();
 }
 
@@ -515,7 +520,7 @@ static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* m
     if (mass) {
         const int64_t rows = c->n_elem * c->dim * NG;
         mass_kernel<NP, R><<<(unsigned)std::min<int64_t>((rows + 127) / 128, 152 * 64), 128, 0, c->stream>>>(
-            c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y);
+            c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
     }
     if (!face) return cudaGetLastError();
     const FaceSmem L = face_smem(DIM, NP, NG);
@@ -524,7 +529,7 @@ static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* m
     cudaFuncSetAttribute(face_apply_kernel<DIM, NP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int64_t blocks = (c->n_face + wpb - 1) / wpb;
     face_apply_kernel<DIM, NP, R><<<(unsigned)std::min<int64_t>(blocks, 1 << 30), 32 * wpb, smem, c->stream>>>(
-        c->n_face, NG, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale);
+        c->n_face, NG, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale); note_launch(c);
     return cudaGetLastError();
 }
 
@@ -677,7 +682,7 @@ template <int NP>
 static void rhs_mass_stdg(stdg_ctx* c, const double* vtr, double* b) {
     const int64_t rows = c->n_elem * c->dim;
     rhs_mass_stdg_kernel<NP><<<(unsigned)std::min<int64_t>((rows + 127) / 128, 152 * 64), 128, 0, c->stream>>>(
-        c->n_elem, c->dim, c->Ng, c->d_rt, c->d_rhoJ, vtr, b);
+        c->n_elem, c->dim, c->Ng, c->d_rt, c->d_rhoJ, vtr, b); note_launch(c);
 }
 
 cudaError_t launch_rhs(stdg_ctx* c, double dt, const double* dparams, int shot, double* b) {
@@ -708,12 +713,12 @@ cudaError_t launch_rhs(stdg_ctx* c, double dt, const double* dparams, int shot, 
         size_t smem = sizeof(double) * 4 * (size_t)(2 * D_ * N_ * N_ + ns * N_);
         cudaFuncSetAttribute(rhs_face_kernel<D_, N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         rhs_face_kernel<D_, N_><<<(unsigned)std::min<int64_t>((c->n_face + 3) / 4, 1 << 30), 128, smem, c->stream>>>(
-            c->n_face, NG, c->d_face_l, c->d_face_r, c->d_D, c->d_rt, dt, sig, b);
+            c->n_face, NG, c->d_face_l, c->d_face_r, c->d_D, c->d_rt, dt, sig, b); note_launch(c);
     }));
     if (c->have_sources) {
         rhs_source_kernel<<<1, 128, 0, c->stream>>>(c->dim, NP, NG, c->d_rt, dparams, (int32_t)c->src_elem[shot],
                                                      c->d_src + shot * (c->dim + NP), c->src_f0, c->src_td, c->src_a1,
-                                                     c->d_gl8, b);
+                                                     c->d_gl8, b); note_launch(c);
     }
     return cudaGetLastError();
 }
@@ -764,7 +769,7 @@ cudaError_t launch_stress_update(stdg_ctx* c, double dt, int shot, const double*
         size_t smem = sizeof(double) * (size_t)wpb * L.total;
         cudaFuncSetAttribute(stress_kernel<D_, N_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         stress_kernel<D_, N_><<<(unsigned)std::min<int64_t>((c->n_face + wpb - 1) / wpb, 1 << 30), 32 * wpb, smem, c->stream>>>(
-            c->n_face, NG, c->d_face_l, c->d_face_r, c->d_D, c->d_lamf, c->d_muf, c->d_rt, dt, x, x_old, sig);
+            c->n_face, NG, c->d_face_l, c->d_face_r, c->d_D, c->d_lamf, c->d_muf, c->d_rt, dt, x, x_old, sig); note_launch(c);
     }));
     return cudaGetLastError();
 }
@@ -786,7 +791,7 @@ __global__ void traces_kernel(int64_t nrows, int NP, int NG, const RefTables* __
 cudaError_t launch_traces(stdg_ctx* c, int shot, const double* x) {
     const int64_t rows = c->n_elem * c->dim;
     traces_kernel<<<(unsigned)std::min<int64_t>((rows * c->Nphi + 255) / 256, 152 * 32), 256, 0, c->stream>>>(
-        rows, c->Nphi, c->Ng, c->d_rt, x, c->d_vtr + shot * c->ntr);
+        rows, c->Nphi, c->Ng, c->d_rt, x, c->d_vtr + shot * c->ntr); note_launch(c);
     return cudaGetLastError();
 }
 
@@ -801,7 +806,7 @@ __global__ void initial_guess_kernel(int64_t nrows, int NP, int NG, const double
 cudaError_t launch_initial_guess(stdg_ctx* c, int shot, double* x) {
     const int64_t rows = c->n_elem * c->dim;
     initial_guess_kernel<<<(unsigned)std::min<int64_t>((rows * c->Ng * c->Nphi + 255) / 256, 152 * 32), 256, 0, c->stream>>>(
-        rows, c->Nphi, c->Ng, c->d_vtr + shot * c->ntr, x);
+        rows, c->Nphi, c->Ng, c->d_vtr + shot * c->ntr, x); note_launch(c);
     return cudaGetLastError();
 }
 
@@ -823,7 +828,7 @@ cudaError_t launch_receivers(stdg_ctx* c, const double* dparams, int shot) {
     if (c->n_rec == 0) return cudaSuccess;
     receivers_kernel<<<1, 256, 0, c->stream>>>(c->n_rec, c->dim, c->Nphi, c->d_rec_elem, c->d_rec_phi, c->d_vtr + shot * c->ntr,
                                                 dparams, c->rec_cap_steps,
-                                                c->d_records + (int64_t)shot * c->rec_cap_steps * c->n_rec * c->dim);
+                                                c->d_records + (int64_t)shot * c->rec_cap_steps * c->n_rec * c->dim); note_launch(c);
     return cudaGetLastError();
 }
 
@@ -874,12 +879,14 @@ __global__ void energy_kernel(int64_t n_elem, int64_t n_face, int NP, const RefT
 
 cudaError_t launch_energy(stdg_ctx* c, int shot, double* d_out) {
     cudaMemsetAsync(d_out, 0, sizeof(double), c->stream);
-    if (c->dim == 2)
+    if (c->dim == 2) {
         energy_kernel<2><<<152 * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
                                                          c->d_lamf, c->d_muf, c->d_sigtr + shot * c->nsig, d_out);
-    else
+    } else {
         energy_kernel<3><<<152 * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
                                                          c->d_lamf, c->d_muf, c->d_sigtr + shot * c->nsig, d_out);
+    }
+    note_launch(c);
     return cudaGetLastError();
 }
 
@@ -1039,13 +1046,13 @@ cudaError_t launch_project_plane_wave(stdg_ctx* c, int shot, int kind, const dou
     double* sig = c->d_sigtr + shot * c->nsig;
     const unsigned ge = (unsigned)((c->n_elem + 127) / 128), gf = (unsigned)((c->n_face + 127) / 128);
     if (d == 2) {
-        project_vel_kernel<2><<<ge, 128, 0, c->stream>>>(c->n_elem, c->d_rt, c->d_X, c->d_detJ, pw, d_rule, nq, vtr);
+        project_vel_kernel<2><<<ge, 128, 0, c->stream>>>(c->n_elem, c->d_rt, c->d_X, c->d_detJ, pw, d_rule, nq, vtr); note_launch(c);
         project_sig_kernel<2><<<gf, 128, 0, c->stream>>>(c->n_face, c->d_rt, c->d_face_l, c->d_face_r, c->d_X, c->d_faceX,
-                                                         c->d_shift, c->d_xc, c->d_hj, c->d_L, pw, d_rule, nq, sig);
+                                                         c->d_shift, c->d_xc, c->d_hj, c->d_L, pw, d_rule, nq, sig); note_launch(c);
     } else {
-        project_vel_kernel<3><<<ge, 128, 0, c->stream>>>(c->n_elem, c->d_rt, c->d_X, c->d_detJ, pw, d_rule, nq, vtr);
+        project_vel_kernel<3><<<ge, 128, 0, c->stream>>>(c->n_elem, c->d_rt, c->d_X, c->d_detJ, pw, d_rule, nq, vtr); note_launch(c);
         project_sig_kernel<3><<<gf, 128, 0, c->stream>>>(c->n_face, c->d_rt, c->d_face_l, c->d_face_r, c->d_X, c->d_faceX,
-                                                         c->d_shift, c->d_xc, c->d_hj, c->d_L, pw, d_rule, nq, sig);
+                                                         c->d_shift, c->d_xc, c->d_hj, c->d_L, pw, d_rule, nq, sig); note_launch(c);
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,325 @@
+// Block-Jacobi preconditioner "Pre1" (Appendix A, Eq. pre1): the exact inverse of each
+// element's diagonal block of the velocity system.
+//
+// The diagonal block has Kronecker form (space (x) time):
+//   A_ii = M_i (x) T + c dt^2 K_i (x) S,   M_i = rho_i |J_i| (I_d (x) M_ref),
+//   K_i[(k,n),(k',n')] = sum_{j in S_i} sum_{l,l'} E_j[k,l,k',l'] (D~_{i,j}[l] D~_{i,j}[l']^T)[n,n'],
+// (T, S time factors as in the operator; c = 1 or 1/4 for Crank-Nicolson).  With the
+// generalised eigen-decomposition K_i V = M_i V Lambda, V^T M_i V = I:
+//   A_ii^{-1} = (V (x) I) blockdiag_q (T + c dt^2 lambda_q S)^{-1} (V^T (x) I).
+// V and Lambda do not depend on dt; only the small N_gamma x N_gamma blocks do.  The
+// symmetric eigenproblem R^{-1} K R^{-T} / (rho|J|) = Q Lambda Q^T (M_ref = R R^T) is
+// solved per element by a cyclic two-sided Jacobi method with round-robin pair ordering
+// (all pairs of a round rotate concurrently), in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "stdg_internal.h"
+
+namespace stdg {
+
+constexpr int kPreThreads = 128;
+constexpr int kMaxN = 3 * kMaxNP;   // d * N_phi <= 60
+
+// smem: C (n x n, stride n+1), Q (n x n, stride n+1), D~ one side (d*NP*NP), pairs, angles
+__global__ void __launch_bounds__(kPreThreads) pre1_setup_kernel(
+    int64_t n_elem, int dim, const RefTables* __restrict__ rtp, const int32_t* __restrict__ elem_face,
+    const int32_t* __restrict__ face_l, const double* __restrict__ D, const double* __restrict__ lamf,
+    const double* __restrict__ muf, const double* __restrict__ rhoJ, const double* __restrict__ Rinv,
+    double* __restrict__ Vout, double* __restrict__ Lout, int* __restrict__ status) {
+    extern __shared__ double sm[];
+    const int NP = rtp->Nphi;
+    const int n = dim * NP;
+    const int ld = n + 1;
+    double* C = sm;                       // n * ld
+    double* Q = C + n * ld;               // n * ld
+    double* Ds = Q + n * ld;              // dim * NP * NP
+    double* Ri = Ds + dim * NP * NP;      // NP * NP
+    double* cs = Ri + NP * NP;            // n/2 + 1
+    double* sn = cs + kMaxN / 2 + 1;
+    int* top = reinterpret_cast<int*>(sn + kMaxN / 2 + 1);   // round-robin tables
+    int* bot = top + kMaxN / 2 + 1;
+    __shared__ double s_off, s_diag;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < NP * NP; t += blockDim.x) Ri[t] = Rinv[t];
+    for (int64_t e = blockIdx.x; e < n_elem; e += gridDim.x) {
+        // ---- K_i
+        for (int t = tid; t < n * ld; t += blockDim.x) C[t] = 0.0;
+        __syncthreads();
+        for (int f = 0; f <= dim; ++f) {
+            const int j = elem_face[e * (dim + 1) + f];
+            const int side = face_l[j] == (int)e ? 0 : 1;
+            const double* Dg = D + ((int64_t)j * 2 + side) * dim * NP * NP;
+            for (int t = tid; t < dim * NP * NP; t += blockDim.x) Ds[t] = Dg[t];
+            const double lam = lamf[j], mu = muf[j];
+            __syncthreads();
+            for (int ent = tid; ent < n * n; ent += blockDim.x) {
+                const int r = ent / n, c = ent % n;
+                const int k = r / NP, nn = r % NP, k2 = c / NP, n2 = c % NP;
+                // P[l][l'][n][n'] = sum_m D~[l][n][m] D~[l'][n'][m]
+                auto P = [&](int l, int l2) {
+                    const double* a = Ds + (l * NP + nn) * NP;
+                    const double* b = Ds + (l2 * NP + n2) * NP;
+                    double s = 0;
+                    for (int m = 0; m < NP; ++m) s += a[m] * b[m];
+                    return s;
+                };
+                double v = lam * P(k, k2) + mu * P(k2, k);
+                if (k == k2)
+                    for (int l = 0; l < dim; ++l) v += mu * P(l, l);
+                C[r * ld + c] += v;
+            }
+            __syncthreads();
+        }
+        // ---- C <- R^{-1} K R^{-T} / (rho |J|), using Q as scratch
+        const double inv = 1.0 / rhoJ[e];
+        for (int ent = tid; ent < n * n; ent += blockDim.x) {
+            const int r = ent / n, c = ent % n;
+            const int k2 = c / NP, n2 = c % NP;
+            double s = 0;
+            for (int q = 0; q <= n2; ++q) s += C[r * ld + k2 * NP + q] * Ri[n2 * NP + q];
+            Q[r * ld + c] = s;
+        }
+        __syncthreads();
+        for (int ent = tid; ent < n * n; ent += blockDim.x) {
+            const int r = ent / n, c = ent % n;
+            const int k = r / NP, nn = r % NP;
+            double s = 0;
+            for (int q = 0; q <= nn; ++q) s += Ri[nn * NP + q] * Q[(k * NP + q) * ld + c];
+            C[r * ld + c] = s * inv;
+        }
+        __syncthreads();
+        // symmetrise and set Q = I
+        for (int ent = tid; ent < n * n; ent += blockDim.x) {
+            const int r = ent / n, c = ent % n;
+            if (r < c) {
+                const double a = 0.5 * (C[r * ld + c] + C[c * ld + r]);
+                C[r * ld + c] = a;
+                C[c * ld + r] = a;
+            }
+            Q[r * ld + c] = r == c ? 1.0 : 0.0;
+        }
+        // ---- cyclic Jacobi, round-robin ordering on an even number of slots
+        const int m2 = (n + 1) / 2;          // pairs per round (a dummy slot when n is odd)
+        const int slots = 2 * m2;
+        if (tid < m2) { top[tid] = 2 * tid; bot[tid] = 2 * tid + 1; }
+        __syncthreads();
+        int sweep = 0;
+        for (; sweep < 30; ++sweep) {
+            if (tid == 0) { s_off = 0.0; s_diag = 0.0; }
+            __syncthreads();
+            double off = 0, dg = 0;
+            for (int ent = tid; ent < n * n; ent += blockDim.x) {
+                const int r = ent / n, c = ent % n;
+                const double a = C[r * ld + c];
+                if (r == c) dg += a * a; else off += a * a;
+            }
+            atomicAdd(&s_off, off);
+            atomicAdd(&s_diag, dg);
+            __syncthreads();
+            if (s_off <= 1e-30 * s_diag || s_diag == 0.0) break;
+            for (int round = 0; round < slots - 1; ++round) {
+                // rotation angles for the pairs of this round
+                if (tid < m2) {
+                    int p = top[tid], q = bot[tid];
+                    if (p > q) { int t = p; p = q; q = t; }
+                    double c = 1.0, s = 0.0;
+                    if (q < n) {
+                        const double apq = C[p * ld + q];
+                        if (apq != 0.0) {
+                            const double app = C[p * ld + p], aqq = C[q * ld + q];
+                            const double theta = (aqq - app) / (2.0 * apq);
+                            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                            c = 1.0 / sqrt(t * t + 1.0);
+                            s = t * c;
+                        }
+                    }
+                    cs[tid] = c;
+                    sn[tid] = s;
+                }
+                __syncthreads();
+                // columns: C <- C J, Q <- Q J
+                for (int ent = tid; ent < n * m2; ent += blockDim.x) {
+                    const int r = ent / m2, k = ent % m2;
+                    int p = top[k], q = bot[k];
+                    if (p > q) { int t = p; p = q; q = t; }
+                    if (q >= n) continue;
+                    const double c = cs[k], s = sn[k];
+                    const double a = C[r * ld + p], b = C[r * ld + q];
+                    C[r * ld + p] = c * a - s * b;
+                    C[r * ld + q] = s * a + c * b;
+                    const double qa = Q[r * ld + p], qb = Q[r * ld + q];
+                    Q[r * ld + p] = c * qa - s * qb;
+                    Q[r * ld + q] = s * qa + c * qb;
+                }
+                __syncthreads();
+                // rows: C <- J^T C
+                for (int ent = tid; ent < n * m2; ent += blockDim.x) {
+                    const int col = ent / m2, k = ent % m2;
+                    int p = top[k], q = bot[k];
+                    if (p > q) { int t = p; p = q; q = t; }
+                    if (q >= n) continue;
+                    const double c = cs[k], s = sn[k];
+                    const double a = C[p * ld + col], b = C[q * ld + col];
+                    C[p * ld + col] = c * a - s * b;
+                    C[q * ld + col] = s * a + c * b;
+                }
+                __syncthreads();
+                // next round-robin arrangement (slot top[0] stays fixed)
+                if (tid == 0) {
+                    const int t_last = top[m2 - 1];
+                    const int b0 = bot[0];
+                    for (int k = m2 - 1; k > 1; --k) top[k] = top[k - 1];
+                    if (m2 > 1) top[1] = b0;
+                    for (int k = 0; k < m2 - 1; ++k) bot[k] = bot[k + 1];
+                    bot[m2 - 1] = t_last;
+                }
+                __syncthreads();
+            }
+        }
+        if (tid == 0 && sweep >= 30) atomicExch(status, 1);
+        // ---- V = (I (x) R^{-T}) Q / sqrt(rho |J|), eigenvalues
+        const double sc = sqrt(inv);
+        double* Vg = Vout + e * (int64_t)n * n;
+        for (int ent = tid; ent < n * n; ent += blockDim.x) {
+            const int r = ent / n, c = ent % n;
+            const int k = r / NP, nn = r % NP;
+            double s = 0;
+            for (int q = nn; q < NP; ++q) s += Ri[q * NP + nn] * Q[(k * NP + q) * ld + c];
+            Vg[ent] = s * sc;
+        }
+        for (int q = tid; q < n; q += blockDim.x) Lout[e * n + q] = C[q * ld + q];
+        __syncthreads();
+    }
+}
+
+// B[e][q] = (T + cdt2 lambda_q S)^{-1}  (N_gamma x N_gamma, Gauss-Jordan)
+template <typename R>
+__global__ void pre1_time_kernel(int64_t nq, int NG, const RefTables* __restrict__ rtp, const double* __restrict__ lam,
+                                 double cdt2, R* __restrict__ B) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    double A[kMaxNG][2 * kMaxNG];
+    const double l = lam[i];
+    for (int a = 0; a < NG; ++a)
+        for (int b = 0; b < NG; ++b) {
+            A[a][b] = rtp->T[a * NG + b] + cdt2 * l * rtp->S[a * NG + b];
+            A[a][NG + b] = a == b ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < NG; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < NG; ++r) if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < 2 * NG; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+        const double d = 1.0 / A[c][c];
+        for (int k = 0; k < 2 * NG; ++k) A[c][k] *= d;
+        for (int r = 0; r < NG; ++r) {
+            if (r == c) continue;
+            const double f = A[r][c];
+            for (int k = 0; k < 2 * NG; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    for (int a = 0; a < NG; ++a)
+        for (int b = 0; b < NG; ++b) B[i * NG * NG + a * NG + b] = (R)A[a][NG + b];
+}
+
+// z_e = V (blockdiag B) V^T r_e for every element; r, z layout [e][k][a][n].  One warp per
+// element; V staged in shared memory with a padded row stride.
+template <typename R>
+__global__ void __launch_bounds__(128) pre1_apply_kernel(int64_t n_elem, int dim, int NP, int NG, const R* __restrict__ V,
+                                                         const R* __restrict__ B, const R* __restrict__ r,
+                                                         const int* __restrict__ ridx, int64_t ld_vec, R* __restrict__ z) {
+    extern __shared__ unsigned char smraw[];
+    R* sm = reinterpret_cast<R*>(smraw);
+    if (ridx) r += (int64_t)(*ridx) * ld_vec;
+    const int n = dim * NP;
+    const int ldv = n + 1;
+    const int per = n * ldv + 2 * n * NG;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    R* sV = sm + warp * per;
+    R* sr = sV + n * ldv;        // [(k,n)][a]
+    R* sw = sr + n * NG;         // [q][a]
+    for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
+        const R* Vg = V + e * (int64_t)n * n;
+        for (int t = lane; t < n * n; t += 32) sV[(t / n) * ldv + t % n] = Vg[t];
+        const R* re = r + e * (int64_t)n * NG;
+        for (int t = lane; t < n * NG; t += 32) {
+            const int k = t / (NG * NP), a = (t / NP) % NG, nn = t % NP;
+            sr[(k * NP + nn) * NG + a] = re[t];
+        }
+        __syncwarp();
+        for (int q = lane; q < n; q += 32) {
+            R u[kMaxNG];
+            for (int a = 0; a < NG; ++a) u[a] = 0;
+            for (int row = 0; row < n; ++row) {
+                const R v = sV[row * ldv + q];
+                for (int a = 0; a < NG; ++a) u[a] += v * sr[row * NG + a];
+            }
+            const R* Bq = B + (e * n + q) * NG * NG;
+            for (int a = 0; a < NG; ++a) {
+                R s = 0;
+                for (int b = 0; b < NG; ++b) s += Bq[a * NG + b] * u[b];
+                sw[q * NG + a] = s;
+            }
+        }
+        __syncwarp();
+        R* ze = z + e * (int64_t)n * NG;
+        for (int row = lane; row < n; row += 32) {
+            R acc[kMaxNG];
+            for (int a = 0; a < NG; ++a) acc[a] = 0;
+            for (int q = 0; q < n; ++q) {
+                const R v = sV[row * ldv + q];
+                for (int a = 0; a < NG; ++a) acc[a] += v * sw[q * NG + a];
+            }
+            const int k = row / NP, nn = row % NP;
+            for (int a = 0; a < NG; ++a) ze[(k * NG + a) * NP + nn] = acc[a];
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* d_elem_face, int* d_status) {
+    const int n = c->dim * c->Nphi;
+    const size_t smem = sizeof(double) * ((size_t)2 * n * (n + 1) + (size_t)c->dim * c->Nphi * c->Nphi + c->Nphi * c->Nphi +
+                                          2 * (kMaxN / 2 + 1)) +
+                        sizeof(int) * 2 * (kMaxN / 2 + 1);
+    cudaFuncSetAttribute(pre1_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = (int)std::min<int64_t>(c->n_elem, 152 * 16);
+    pre1_setup_kernel<<<grid, kPreThreads, smem, c->stream>>>(c->n_elem, c->dim, c->d_rt, d_elem_face, c->d_face_l, c->d_D,
+                                                              c->d_lamf, c->d_muf, c->d_rhoJ, d_Rinv, c->d_preV, c->d_preLam,
+                                                              d_status); note_launch(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre1_time(stdg_ctx* c, double dt) {
+    const double cfac = c->opt.scheme == STDG_SCHEME_CN ? 0.25 : 1.0;
+    const int64_t nq = c->n_elem * c->dim * c->Nphi;
+    pre1_time_kernel<double><<<(unsigned)((nq + 127) / 128), 128, 0, c->stream>>>(nq, c->Ng, c->d_rt, c->d_preLam,
+                                                                               cfac * dt * dt, c->d_preB); note_launch(c);
+    if (c->d_preB32) {
+        pre1_time_kernel<float><<<(unsigned)((nq + 127) / 128), 128, 0, c->stream>>>(nq, c->Ng, c->d_rt, c->d_preLam,
+                                                                                  cfac * dt * dt, c->d_preB32); note_launch(c);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t pre1_apply_t(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld) {
+    const int n = c->dim * c->Nphi;
+    const int wpb = 4;
+    const size_t smem = sizeof(R) * (size_t)wpb * (n * (n + 1) + 2 * n * c->Ng);
+    cudaFuncSetAttribute(pre1_apply_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
+    pre1_apply_kernel<R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_elem, c->dim, c->Nphi, c->Ng, V, B, r, ridx, ld, z); note_launch(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld) {
+    return pre1_apply_t<double>(c, c->d_preV, c->d_preB, r, z, ridx, ld);
+}
+
+cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld) {
+    return pre1_apply_t<float>(c, c->d_preV32, c->d_preB32, r, z, ridx, ld);
+}
+
+}  // namespace stdg

@@ -42,6 +42,7 @@ struct DevScalars {
     // statistics, reset by the host before a batch of steps
     int st_total, st_max, st_refine, st_notconv;
     double st_final_rel, st_iters_sum;
+    unsigned long long launches;      // kernel executions since the last reset
 };
 
 struct Workspace {
@@ -50,8 +51,9 @@ struct Workspace {
     DevScalars* sc = nullptr;
     double* partials = nullptr;   // (kMaxRestart + 2) * kRedBlocks
     double* dparams = nullptr;    // t^n, dt, step index
-    double *V = nullptr, *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;      // FP64
+    double *V = nullptr, *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *t = nullptr;   // FP64
     float *V32 = nullptr, *w32 = nullptr, *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *z32 = nullptr, *t32 = nullptr;
     cudaStream_t side[6] = {};
     int depth = 0;
     cudaGraph_t graph = nullptr;
@@ -103,16 +105,16 @@ __global__ void zero_if_kernel(int64_t n, double* x, const int* flag) {
 }
 
 // ---------------------------------------------------------------------------------
-// CG kernels (R = vector type, scalars FP64)
+// (Preconditioned) CG kernels (R = vector type, scalars FP64).  Without a preconditioner
+// z aliases r and rz = rr.
 // ---------------------------------------------------------------------------------
 template <typename R>
-__global__ void cg_init_kernel(int64_t n, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ r,
-                               R* __restrict__ p, double* __restrict__ part) {
+__global__ void cg_res_kernel(int64_t n, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ r,
+                              double* __restrict__ part) {
     double rr = 0, bb = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const R ri = b[i] - Ax[i];
         r[i] = ri;
-        p[i] = ri;
         rr += (double)ri * (double)ri;
         bb += (double)b[i] * (double)b[i];
     }
@@ -121,14 +123,16 @@ __global__ void cg_init_kernel(int64_t n, const R* __restrict__ b, const R* __re
     if (threadIdx.x == 0) { part[blockIdx.x] = s1; part[kRedBlocks + blockIdx.x] = s2; }
 }
 
-// bnorm_given < 0: use ||b|| from the partials
+// bnorm_given < 0: use ||b|| from the partials; partials: [0] rr, [1] bb, [2] rz
 __global__ void cg_init_final_kernel(DevScalars* sc, const double* part, double rel_tol, int max_iters,
                                      double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h) {
     double rr = sum_partials(part, kRedBlocks);
     double bb = sum_partials(part + kRedBlocks, kRedBlocks);
+    double rz = sum_partials(part + 2 * kRedBlocks, kRedBlocks);
     if (threadIdx.x == 0) {
         const int active = gate_ir ? sc->ir_flag : 1;
         sc->rr = rr;
+        sc->pq = rz;                       // holds r.z between iterations
         sc->bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(bb);
         sc->tol_abs = rel_tol * sc->bnorm;
         sc->iters = 0;
@@ -140,12 +144,14 @@ __global__ void cg_init_final_kernel(DevScalars* sc, const double* part, double 
     }
 }
 
+template <typename R>
+__global__ void copy_kernel(int64_t n, const R* __restrict__ a, R* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = a[i];
+}
+
 __global__ void cg_alpha_kernel(DevScalars* sc, const double* part) {
     double pq = sum_partials(part, kRedBlocks);
-    if (threadIdx.x == 0) {
-        sc->pq = pq;
-        sc->alpha = pq != 0.0 ? sc->rr / pq : 0.0;
-    }
+    if (threadIdx.x == 0) sc->alpha = pq != 0.0 ? sc->pq / pq : 0.0;
 }
 
 template <typename R>
@@ -163,10 +169,13 @@ __global__ void cg_update_kernel(int64_t n, const DevScalars* __restrict__ sc, R
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// partials: [0] rr, [2] rz (r.z after the preconditioner)
 __global__ void cg_beta_kernel(DevScalars* sc, const double* part, cudaGraphConditionalHandle h, int use_h) {
     double rr = sum_partials(part, kRedBlocks);
+    double rz = sum_partials(part + 2 * kRedBlocks, kRedBlocks);
     if (threadIdx.x == 0) {
-        sc->beta = sc->rr != 0.0 ? rr / sc->rr : 0.0;
+        sc->beta = sc->pq != 0.0 ? rz / sc->pq : 0.0;
+        sc->pq = rz;
         sc->rr = rr;
         sc->iters += 1;
         sc->converged = sqrt(rr) <= sc->tol_abs;
@@ -176,10 +185,10 @@ __global__ void cg_beta_kernel(DevScalars* sc, const double* part, cudaGraphCond
 }
 
 template <typename R>
-__global__ void cg_p_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ r, R* __restrict__ p) {
+__global__ void cg_p_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ z, R* __restrict__ p) {
     const double b = sc->beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = (R)((double)r[i] + b * (double)p[i]);
+        p[i] = (R)((double)z[i] + b * (double)p[i]);
 }
 
 // ---------------------------------------------------------------------------------
@@ -364,6 +373,26 @@ __global__ void gm_update_x_kernel(int64_t n, const DevScalars* __restrict__ sc,
     }
 }
 
+// t = sum_{k<j} y_k V_k (right preconditioning: x += P^{-1} t afterwards)
+template <typename R>
+__global__ void gm_combine_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, R* __restrict__ t) {
+    const int J = sc->j;
+    __shared__ double y[kMaxRestart];
+    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = sc->y[k];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0;
+        for (int k = 0; k < J; ++k) v += y[k] * (double)V[(int64_t)k * n + i];
+        t[i] = (R)v;
+    }
+}
+
+template <typename R>
+__global__ void axpy_kernel(int64_t n, R* __restrict__ x, const R* __restrict__ z) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (R)((double)x[i] + (double)z[i]);
+}
+
 __global__ void gm_cycle_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int use_h) {
     if (threadIdx.x != 0) return;
     sc->j = 0;
@@ -452,6 +481,11 @@ __global__ void solve_stats_kernel(DevScalars* sc, int mode) {
     sc->st_iters_sum += (double)it;
 }
 
+// adds a loop body's (or a step's straight-line) kernel count, itself included
+__global__ void count_kernel(DevScalars* sc, long k) {
+    if (threadIdx.x == 0) sc->launches += (unsigned long long)k;
+}
+
 __global__ void step_begin_kernel(double* dparams, double dt) {
     if (threadIdx.x == 0) dparams[1] = dt;
 }
@@ -479,7 +513,7 @@ struct Flow {
                 err = cudaMemcpyAsync(&f, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
                 if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
                 if (err != cudaSuccess || !f) break;
-                body(cudaGraphConditionalHandle(0), 0);
+                run_body(body, cudaGraphConditionalHandle(0), 0);
             }
             return;
         }
@@ -504,7 +538,7 @@ struct Flow {
         err = cudaStreamBeginCaptureToGraph(s2, body_g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (err == cudaSuccess) {
             c->stream = s2;
-            body(h, 1);
+            run_body(body, h, 1);
             c->stream = s;
             cudaGraph_t tmp;
             cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
@@ -514,39 +548,55 @@ struct Flow {
         if (err == cudaSuccess) err = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
     }
     void check(cudaError_t e) { if (err == cudaSuccess && e != cudaSuccess) err = e; }
+
+    // one loop body in its own launch-count scope, closed by a count kernel
+    template <class Body>
+    void run_body(Body& body, cudaGraphConditionalHandle h, int use) {
+        c->scopes.push_back(0);
+        body(h, use);
+        const long k = c->scopes.back() + 1;
+        c->scopes.pop_back();
+        count_kernel<<<1, 32, 0, c->stream>>>(ws->sc, k);
+    }
 };
 
 static unsigned vec_blocks(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, kRedBlocks); }
 
-// ---- CG on vectors of type R; apply(xptr, yptr) computes y = A x ----------------------
-template <typename R, class Apply>
-static void solve_cg(Flow& F, Apply apply, const R* b, R* x, R* r, R* p, R* q, double rel_tol, int max_iters,
-                     double bnorm_given, int gate_ir) {
+// ---- (P)CG on vectors of type R; apply(x, y): y = A x; prec(r, z): z = P^{-1} r or null --------
+template <typename R, class Apply, class Prec>
+static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b, R* x, R* r, R* p, R* q, R* z,
+                     double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
     const int64_t n = ws->n;
+    R* zz = use_prec ? z : r;
     F.loop(&ws->sc->flag_inner,
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(apply(x, q));
-               cg_init_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, q, r, p, ws->partials);
+               cg_res_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, q, r, ws->partials); note_launch(c);
+               if (use_prec) F.check(prec(r, zz));
+               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, r, zz, ws->partials + 2 * kRedBlocks); note_launch(c);
                cg_init_final_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, rel_tol, max_iters, bnorm_given,
-                                                                      gate_ir, h, use);
+                                                                      gate_ir, h, use); note_launch(c);
+               copy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, zz, p); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(apply(p, q));
-               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, p, q, ws->partials);
-               cg_alpha_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials);
-               cg_update_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, x, r, p, q, ws->partials);
-               cg_beta_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, h, use);
-               cg_p_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, r, p);
+               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, p, q, ws->partials); note_launch(c);
+               cg_alpha_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials); note_launch(c);
+               cg_update_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, x, r, p, q, ws->partials); note_launch(c);
+               if (use_prec) F.check(prec(r, zz));
+               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, r, zz, ws->partials + 2 * kRedBlocks); note_launch(c);
+               cg_beta_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, h, use); note_launch(c);
+               cg_p_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, zz, p); note_launch(c);
                F.check(cudaGetLastError());
            });
 }
 
 // ---- GMRES(m) on vectors of type R -----------------------------------------------------
-template <typename R, class Apply, class ApplyIdx>
-static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, const R* b, R* x, R* V, R* w, double rel_tol,
-                        int max_iters, double bnorm_given, int gate_ir) {
+template <typename R, class Apply, class ApplyIdx, class Prec>
+static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, bool use_prec, const R* b, R* x, R* V, R* w,
+                        R* zbuf, R* tbuf, double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
     const int64_t n = ws->n;
@@ -554,33 +604,44 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, const R* b, R*
     DevScalars* sc = ws->sc;
     F.loop(&sc->flag_outer,
            [&](cudaGraphConditionalHandle h, int use) {
-               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials);
-               gm_init_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, rel_tol, max_iters, m, bnorm_given, gate_ir, h, use);
+               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials); note_launch(c);
+               gm_init_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, rel_tol, max_iters, m, bnorm_given, gate_ir, h, use); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h_outer, int use_outer) {
                // restart cycle: true residual, then Arnoldi
                F.check(apply(x, w));
-               gm_res_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, w, V, ws->partials);
+               gm_res_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, w, V, ws->partials); note_launch(c);
                F.loop(&sc->flag_inner,
                       [&](cudaGraphConditionalHandle h, int use) {
-                          gm_cycle_start_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, h, use);
-                          gm_scale0_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V);
+                          gm_cycle_start_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, h, use); note_launch(c);
+                          gm_scale0_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V); note_launch(c);
                       },
                       [&](cudaGraphConditionalHandle h, int use) {
-                          F.check(apply_idx(V, &sc->j, w));
-                          for (int pass = 0; pass < 2; ++pass) {
-                              gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials);
-                              gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, pass);
-                              gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials, pass);
+                          if (use_prec) {   // right preconditioning: w = A P^{-1} v_j
+                              F.check(prec(V, zbuf, &sc->j, n));
+                              F.check(apply(zbuf, w));
+                          } else {
+                              F.check(apply_idx(V, &sc->j, w));
                           }
-                          gm_norm_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials);
-                          gm_next_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, w, V);
-                          gm_givens_kernel<<<1, 32, 0, c->stream>>>(sc, h, use);
+                          for (int pass = 0; pass < 2; ++pass) {
+                              gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials); note_launch(c);
+                              gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, pass); note_launch(c);
+                              gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials, pass); note_launch(c);
+                          }
+                          gm_norm_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials); note_launch(c);
+                          gm_next_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, w, V); note_launch(c);
+                          gm_givens_kernel<<<1, 32, 0, c->stream>>>(sc, h, use); note_launch(c);
                           F.check(cudaGetLastError());
                       });
-               gm_solve_kernel<<<1, 32, 0, c->stream>>>(sc);
-               gm_update_x_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, x);
-               gm_cycle_end_kernel<<<1, 32, 0, c->stream>>>(sc, h_outer, use_outer);
+               gm_solve_kernel<<<1, 32, 0, c->stream>>>(sc); note_launch(c);
+               if (use_prec) {   // x += P^{-1} (V y)
+                   gm_combine_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, tbuf); note_launch(c);
+                   F.check(prec(tbuf, zbuf, nullptr, 0));
+                   axpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, zbuf); note_launch(c);
+               } else {
+                   gm_update_x_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, x); note_launch(c);
+               }
+               gm_cycle_end_kernel<<<1, 32, 0, c->stream>>>(sc, h_outer, use_outer); note_launch(c);
                F.check(cudaGetLastError());
            });
 }
@@ -591,44 +652,54 @@ static void record_solve(Flow& F, double dt, double* b, double* x) {
     Workspace* ws = F.ws;
     const int64_t n = ws->n;
     const bool cn = c->opt.scheme == STDG_SCHEME_CN;
+    const bool pre = c->opt.preconditioner != 0;
     auto A64 = [&](const double* xx, double* yy) { return launch_apply(c, dt, xx, yy, 1.0); };
     auto A64i = [&](const double* V, const int* idx, double* yy) { return launch_apply(c, dt, V, yy, 1.0, idx, n); };
     auto A32 = [&](const float* xx, float* yy) { return launch_apply32(c, dt, xx, yy, 1.0); };
     auto A32i = [&](const float* V, const int* idx, float* yy) { return launch_apply32(c, dt, V, yy, 1.0, idx, n); };
+    auto P64 = [&](const double* r, double* z, const int* idx, int64_t ld) { return launch_pre1_apply(c, r, z, idx, ld); };
+    auto P32 = [&](const float* r, float* z, const int* idx, int64_t ld) { return launch_pre1_apply32(c, r, z, idx, ld); };
+    auto P64c = [&](const double* r, double* z) { return launch_pre1_apply(c, r, z, nullptr, 0); };
+    auto P32c = [&](const float* r, float* z) { return launch_pre1_apply32(c, r, z, nullptr, 0); };
     const double tol = c->opt.rel_tol;
     const int maxit = c->opt.max_iters;
     if (c->opt.precision == STDG_FP64) {
-        if (cn) solve_cg<double>(F, A64, b, x, ws->r, ws->p, ws->q, tol, maxit, -1.0, 0);
-        else solve_gmres<double>(F, A64, A64i, b, x, ws->V, ws->w, tol, maxit, -1.0, 0);
-        zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x);
-        solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, cn ? 1 : 0);
+        if (cn) solve_cg<double>(F, A64, P64c, pre, b, x, ws->r, ws->p, ws->q, ws->z, tol, maxit, -1.0, 0);
+        else solve_gmres<double>(F, A64, A64i, P64, pre, b, x, ws->V, ws->w, ws->z, ws->t, tol, maxit, -1.0, 0);
+        zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x); note_launch(c);
+        solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, cn ? 1 : 0); note_launch(c);
         return;
     }
     // mixed: FP64 refinement, FP32 inner solve with zero initial guess and unit RHS
     F.loop(&ws->sc->ir_flag,
            [&](cudaGraphConditionalHandle h, int use) {
-               dot_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials);
-               ir_init_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, tol, 64, h, use);
+               dot_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials); note_launch(c);
+               ir_init_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, tol, 64, h, use); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(A64(x, ws->w));
-               gm_res_kernel<double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, ws->w, ws->r, ws->partials);
-               ir_check_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, maxit);
-               ir_convert_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->r, ws->b32, ws->x32);
-               if (cn) solve_cg<float>(F, A32, ws->b32, ws->x32, ws->r32, ws->p32, ws->q32, c->opt.inner_tol, maxit, 1.0, 1);
-               else solve_gmres<float>(F, A32, A32i, ws->b32, ws->x32, ws->V32, ws->w32, c->opt.inner_tol, maxit, 1.0, 1);
-               ir_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->x32, x);
-               ir_end_kernel<<<1, 32, 0, c->stream>>>(ws->sc, h, use);
+               gm_res_kernel<double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, ws->w, ws->r, ws->partials); note_launch(c);
+               ir_check_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, maxit); note_launch(c);
+               ir_convert_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->r, ws->b32, ws->x32); note_launch(c);
+               if (cn)
+                   solve_cg<float>(F, A32, P32c, pre, ws->b32, ws->x32, ws->r32, ws->p32, ws->q32, ws->z32, c->opt.inner_tol,
+                                   maxit, 1.0, 1);
+               else
+                   solve_gmres<float>(F, A32, A32i, P32, pre, ws->b32, ws->x32, ws->V32, ws->w32, ws->z32, ws->t32,
+                                      c->opt.inner_tol, maxit, 1.0, 1);
+               ir_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->x32, x); note_launch(c);
+               ir_end_kernel<<<1, 32, 0, c->stream>>>(ws->sc, h, use); note_launch(c);
                F.check(cudaGetLastError());
            });
-    zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x);
-    solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, 2);
+    zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x); note_launch(c);
+    solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, 2); note_launch(c);
 }
 
 static void record_step(Flow& F, double dt) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
-    step_begin_kernel<<<1, 32, 0, c->stream>>>(ws->dparams, dt);
+    c->scopes.assign(1, 0);
+    step_begin_kernel<<<1, 32, 0, c->stream>>>(ws->dparams, dt); note_launch(c);
     for (int shot = 0; shot < c->n_shots && F.err == cudaSuccess; ++shot) {
         F.check(launch_rhs(c, dt, ws->dparams, shot, c->d_b));
         F.check(launch_initial_guess(c, shot, c->d_x));
@@ -637,7 +708,10 @@ static void record_step(Flow& F, double dt) {
         F.check(launch_traces(c, shot, c->d_x));
         F.check(launch_receivers(c, ws->dparams, shot));
     }
-    step_end_kernel<<<1, 32, 0, c->stream>>>(ws->dparams, dt);
+    step_end_kernel<<<1, 32, 0, c->stream>>>(ws->dparams, dt); note_launch(c);
+    const long k = c->scopes.back() + 1;
+    c->scopes.clear();
+    count_kernel<<<1, 32, 0, c->stream>>>(ws->sc, k);
     F.check(cudaGetLastError());
 }
 
@@ -657,13 +731,16 @@ int solver_setup(stdg_ctx* c) {
     ALLOC(ws->dparams, sizeof(double) * 4);
     ALLOC(ws->w, sizeof(double) * n);
     ALLOC(ws->r, sizeof(double) * n);
+    const bool pre = c->opt.preconditioner != 0;
     if (cn && !mixed) { ALLOC(ws->p, sizeof(double) * n); ALLOC(ws->q, sizeof(double) * n); }
     if (!cn && !mixed) ALLOC(ws->V, sizeof(double) * n * (ws->m + 1));
+    if (pre && !mixed) { ALLOC(ws->z, sizeof(double) * n); if (!cn) ALLOC(ws->t, sizeof(double) * n); }
     if (mixed) {
         ALLOC(ws->b32, sizeof(float) * n);
         ALLOC(ws->x32, sizeof(float) * n);
         if (cn) { ALLOC(ws->r32, sizeof(float) * n); ALLOC(ws->p32, sizeof(float) * n); ALLOC(ws->q32, sizeof(float) * n); }
         else { ALLOC(ws->V32, sizeof(float) * n * (ws->m + 1)); ALLOC(ws->w32, sizeof(float) * n); }
+        if (pre) { ALLOC(ws->z32, sizeof(float) * n); if (!cn) ALLOC(ws->t32, sizeof(float) * n); }
     }
 #undef ALLOC
     cudaMemsetAsync(ws->sc, 0, sizeof(DevScalars), c->stream);
@@ -700,6 +777,11 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
     // statistics reset (outside any graph)
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_total, 0, sizeof(int) * 4, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_final_rel, 0, sizeof(double) * 2, c->stream));
+    STDG_CUDA(c, cudaMemsetAsync(&ws->sc->launches, 0, sizeof(unsigned long long), c->stream));
+    if (c->opt.preconditioner && c->pre_dt != dt) {
+        STDG_CUDA(c, launch_pre1_time(c, dt));
+        c->pre_dt = dt;
+    }
     const double t0 = c->t;
     STDG_CUDA(c, cudaMemcpyAsync(ws->dparams, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     {
@@ -747,6 +829,7 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
         st->final_rel_res = h.st_final_rel;
         st->status = h.st_notconv ? STDG_ENOTCONV : STDG_OK;
     }
+    c->last_launches = (int64_t)h.launches;
     if (h.st_notconv) STDG_FAIL(c, STDG_ENOTCONV, "Krylov solve reached max_iters");
     return STDG_OK;
 }

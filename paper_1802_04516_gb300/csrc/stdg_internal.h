@@ -22,6 +22,7 @@ struct RefTables {
     double coef[kMaxNP * kMaxNP]; // phi_k(xi) = sum_a coef[a*Nphi + k] xi^a
     double Mref[kMaxNP * kMaxNP]; // int_{ref simplex} phi_k phi_m
     double MrefInv[kMaxNP * kMaxNP];
+    double MrefLinv[kMaxNP * kMaxNP];   // R^{-1} with M_ref = R R^T (R lower triangular)
     double tnodes[kMaxNG], W[kMaxNG], g0[kMaxNG], g1[kMaxNG];
     double T[kMaxNG * kMaxNG];    // gamma(1) gamma(1)^T - K
     double Tinv[kMaxNG * kMaxNG];
@@ -122,13 +123,28 @@ struct stdg_ctx {
     double *d_records = nullptr;       // [shot][cap_steps][rec][dim]
     int64_t rec_cap_steps = 0, rec_steps = 0;
 
+    // ---- block-Jacobi preconditioner (precond.cu)
+    double *d_preV = nullptr, *d_preLam = nullptr, *d_preB = nullptr;
+    float *d_preV32 = nullptr, *d_preB32 = nullptr;
+    int32_t* d_elem_face = nullptr;
+    double pre_dt = -1.0;    // slab size the time blocks d_preB were built for
+
     // ---- solver workspace (solver.cu)
     void* ws = nullptr;
 
     // bookkeeping
+    std::vector<long> scopes;
+    int64_t last_launches = 0;   // kernel executions of the last stdg_step call    // kernels recorded per open loop-body scope (launch counting)
     size_t bytes = 0;
     std::vector<void*> allocs;
 };
+
+// Launch counting: every kernel launch of the library adds one to the innermost open
+// scope; a loop body ends with a kernel that adds its scope's count to a device counter,
+// so the total number of kernel executions is known even inside CUDA-graph while loops.
+inline void note_launch(stdg_ctx* c, long k = 1) {
+    if (!c->scopes.empty()) c->scopes.back() += k;
+}
 
 // Error helpers
 #define STDG_FAIL(ctx, code, msg) do { (ctx)->err = (msg); return (code); } while (0)
@@ -160,6 +176,12 @@ cudaError_t launch_energy(stdg_ctx* c, int shot, double* d_out);
 cudaError_t launch_project_plane_wave(stdg_ctx* c, int shot, int kind, const double* n, const double* pol,
                                       double amp, double t, const double* d_rule, int nq);
 cudaError_t launch_initial_guess(stdg_ctx* c, int shot, double* x);
+
+// precond.cu
+cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* d_elem_face, int* d_status);
+cudaError_t launch_pre1_time(stdg_ctx* c, double dt);
+cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld);
+cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld);
 
 // solver.cu
 int solver_setup(stdg_ctx* c);

@@ -17,6 +17,7 @@ def test_library_builds_and_exports_header_symbols():
 
 def test_options_struct_layout():
     from paper_1802_04516_gb300.binding import stdg_options, stdg_stats
-    # int p, p_gamma, scheme, precision; double rel_tol; int max_iters, gmres_restart; double inner_tol; int use_graph
+    # int p, p_gamma, scheme, precision; double rel_tol; int max_iters, gmres_restart; double inner_tol;
+    # int use_graph, preconditioner
     assert ctypes.sizeof(stdg_options) == 48
     assert ctypes.sizeof(stdg_stats) == 32
