@@ -155,6 +155,21 @@ int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);
  * velocity layout, one shot, FP64, host pointers).  Requires preconditioner = 1. */
 int stdg_apply_preconditioner(stdg_ctx* ctx, double dt, const double* r, double* z);
 
+/* Residual of the velocity system without allocating: r_dev = b_dev - A x_dev for slab
+ * size dt (A as in stdg_apply_operator, FP64, one shot, canonical layout) and
+ * out_dev[0] = ||r|| / ||b|| (||r|| when b = 0), out_dev[1] = ||r||.  All four pointers
+ * are device memory owned by the caller.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc -- code running while a stream is captured into a
+ * CUDA graph, pipelines that cannot afford the device-wide synchronisation of cudaFree,
+ * or processes whose device memory is already reserved by another allocator.  The only
+ * other memory used is a 1 MiB scratch array compiled into the library (held by every GPU
+ * that loads it until exit); velocity vectors longer than 2^28 values are rejected with
+ * STDG_EINVAL.  The first call on a device looks up that array's device address, so make
+ * it before any stream capture.  Calls share the array: calls that overlap on the GPU race
+ * and must be ordered by the caller.  Asynchronous on the context stream. */
+int stdg_residual_noalloc(stdg_ctx* ctx, double dt, const double* x_dev, const double* b_dev,
+                          double* r_dev, double* out_dev);
+
 /* Average device time of `n` launches of the operator's face kernel (fp32 != 0: the
  * FP32 one) on the context stream, measured with CUDA events: *ms_out. */
 int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
     "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
+    "stdg_residual_noalloc": (C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
 }
 
 _lib = None
