@@ -103,10 +103,10 @@ def peaks():
         return {}
 
 
-def build_solver(w, precision, stream, shot_offset=0.0):
+def build_solver(w, precision, stream, shot_offset=0.0, restart=10, inner_tol=1e-2, use_graph=True):
     from paper_1802_04516_gb300.binding import Solver
-    s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=30,
-               inner_tol=1e-3 if precision != "fp64" else 1e-4, use_graph=True, stream=stream, preconditioner=1)
+    s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=restart,
+               inner_tol=inner_tol, use_graph=use_graph, stream=stream, preconditioner=1)
     s.set_mesh(w.xyz, w.elem_vert, w.period)
     s.set_material(w.lam, w.mu, w.rho)
     xs = np.array(w.shots_xs) + np.array([shot_offset, 0.0])
@@ -241,6 +241,10 @@ def main():
     ap.add_argument("--ny", type=int, default=224, help="cells in y (224 = the 200,704-triangle mesh)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--restart", type=int, default=10, help="GMRES restart length")
+    ap.add_argument("--inner-tol", type=float, default=1e-2, help="relative tolerance of the FP32 inner solve")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the solver loops from the host instead of CUDA-graph while nodes (for kernel profilers)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -265,7 +269,8 @@ def main():
     stream = torch.cuda.Stream()
     pk = peaks()
     with torch.cuda.stream(stream):
-        s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=0.01 * rank)
+        s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=0.01 * rank, restart=args.restart,
+                         inner_tol=args.inner_tol, use_graph=not args.host_loop)
         n_face = s.n_face
         dofs = dofs_per_slab(w, n_face)
         sampler = ClockSampler(local)
@@ -278,7 +283,8 @@ def main():
         e2e_value = dofs * max(1, args.steps // 2) / (e2e_ms * 1e-3) * world
         fp64 = None
         if not args.no_fp64 and args.fp64_steps > 0:
-            s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=0.01 * rank)
+            s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=0.01 * rank, restart=args.restart,
+                               use_graph=not args.host_loop)
             ms64, it64, _, _ = time_steps(torch, s64, w, args.fp64_steps, 1, stream, dist)
             fp64 = {"value": world * dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
                     "krylov_iters_per_step": it64, "roofline": face_kernel_roofline(s64, w, False, n_face, pk)}
@@ -294,7 +300,8 @@ def main():
         "config": {"workload": "c2_layered_slivers_p3: %d triangles (448x224x2, 1%% slivers), p=p_gamma=3, "
                                "1 Ricker shot/GPU, 16 receivers, dt=%.4g (10x CFL)" % (w.n_elem, w.dt),
                    "dofs_per_slab": dofs, "n_face": n_face, "preconditioner": "block Jacobi (Pre1)",
-                   "gmres_restart": 30, "l2": "working set (blocks, Krylov basis) > 129 MB L2; no flush",
+                   "gmres_restart": args.restart, "inner_tol": args.inner_tol,
+                   "control": "host loop" if args.host_loop else "CUDA graph per step (device while loops)", "l2": "working set (blocks, Krylov basis) > 129 MB L2; no flush",
                    "parallelism": "independent shot per GPU"},
         "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"], "refinements_last": st["refinements"],
         "gpu_launches": launches,

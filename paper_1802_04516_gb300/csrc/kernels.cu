@@ -523,6 +523,8 @@ static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* m
             c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
     }
     if (!face) return cudaGetLastError();
+    cudaError_t fe;
+    if (launch_face_fast<R>(c, D, lamf, muf, x, xidx, ld, y, scale, &fe)) return fe;
     const FaceSmem L = face_smem(DIM, NP, NG);
     const int wpb = 4;
     size_t smem = sizeof(R) * (kMaxNG * kMaxNG + (size_t)wpb * L.total);

@@ -1,0 +1,259 @@
+// Face kernel of the Schur velocity operator with compile-time sizes (dimension d,
+// N_phi, N_gamma) for the production shapes; other shapes use the generic kernel in
+// kernels.cu.  Same arithmetic as the generic kernel (Eq. velocity.sys with Q~ = -D^T
+// and the orthonormalised dual basis):
+//   g = sum_side D~_side^T v_side,  t = E_j : g,  h = scale * S t,  y_side += D~_side h.
+// One warp per face.  The face's D~ blocks are staged in shared memory twice, as D~ and
+// as its transpose, each row padded to a multiple of 16 bytes, so that every inner
+// product of the gather (rows of D~^T against rows of v) and of the scatter (rows of D~
+// against rows of h) runs on 128-bit shared-memory loads; all loop bounds and index
+// decompositions are compile-time constants.
+#include <algorithm>
+
+#include "stdg_internal.h"
+
+namespace stdg {
+
+template <typename R> struct Vec;
+template <> struct Vec<float> { using T = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using T = double2; static constexpr int W = 2; };
+
+template <typename R>
+__device__ __forceinline__ R dotv(const R* __restrict__ a, const R* __restrict__ b, int nv);
+template <>
+__device__ __forceinline__ float dotv<float>(const float* __restrict__ a, const float* __restrict__ b, int nv) {
+    float s = 0.f;
+    const float4* A = reinterpret_cast<const float4*>(a);
+    const float4* B = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < nv) {
+            const float4 x = A[i], y = B[i];
+            s = fmaf(x.x, y.x, s);
+            s = fmaf(x.y, y.y, s);
+            s = fmaf(x.z, y.z, s);
+            s = fmaf(x.w, y.w, s);
+        }
+    }
+    return s;
+}
+template <>
+__device__ __forceinline__ double dotv<double>(const double* __restrict__ a, const double* __restrict__ b, int nv) {
+    double s = 0.0;
+    const double2* A = reinterpret_cast<const double2*>(a);
+    const double2* B = reinterpret_cast<const double2*>(b);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i < nv) {
+            const double2 x = A[i], y = B[i];
+            s = fma(x.x, y.x, s);
+            s = fma(x.y, y.y, s);
+        }
+    }
+    return s;
+}
+
+constexpr int round_up(int v, int w) { return (v + w - 1) / w * w; }
+
+template <int DIM, int NP, int NG, typename R>
+struct FaceFast {
+    static constexpr int NS = DIM == 2 ? 3 : 6;
+    static constexpr int W = Vec<R>::W;
+    static constexpr int NPP = (NP + W - 1) / W * W;     // padded row length
+    static constexpr int NV = NPP / W;                   // vectors per row
+    static constexpr int RD = 2 * DIM * NP;              // rows of D~ (s,l,n) and of D~^T (s,l,m)
+    static constexpr int NVS = DIM * NG * NP;            // values per element
+    static constexpr int SZ_D = RD * NPP;
+    static constexpr int SZ_V = 2 * DIM * NG * NPP;      // rows (s,k,b)
+    static constexpr int SZ_G = round_up(DIM * DIM * NG * NP, W);   // [k][l][b][m]
+    static constexpr int SZ_T = round_up(NS * NG * NP, W);          // [c][b][m]
+    static constexpr int SZ_H = NS * NG * NPP;           // rows (c,b)
+    static constexpr int PER_WARP = 2 * SZ_D + SZ_V + SZ_G + SZ_T + SZ_H;
+};
+
+template <int DIM>
+__device__ __forceinline__ int symc(int a, int b) {
+    if (a == b) return a;
+    if (DIM == 2) return 2;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return (lo == 0 && hi == 1) ? 3 : (lo == 1 ? 4 : 5);
+}
+
+template <int DIM, int NP, int NG, typename R>
+struct FaceReg {
+    static constexpr int NS = DIM == 2 ? 3 : 6;
+    static constexpr int W = Vec<R>::W;
+    static constexpr int NPP = (NP + W - 1) / W * W;     // padded row length (16-byte multiple)
+    static constexpr int NVS = DIM * NG * NP;            // values per element
+    static constexpr int SZ_V = 2 * DIM * NG * NPP;      // rows (s,k,b) of the neighbours' values
+    static constexpr int SZ_G = round_up(DIM * DIM * NG * NP, W);   // g[k][l][b][m]
+    static constexpr int SZ_T = round_up(NS * NG * NP, W);          // t[c][b][m]
+    static constexpr int SZ_H = NS * NG * NPP;           // rows (c,b) of h
+    static constexpr int PER_WARP = SZ_V + SZ_G + SZ_T + SZ_H;
+};
+
+// Register-blocked face kernel.  Gather lanes own a column (l, m) of D~_s (both sides, N_phi
+// values each, in registers); scatter lanes own a row (s, n) of D~_s (all l, m).  The rows
+// of v and h they multiply are read by all lanes at once from shared memory (broadcast), so
+// almost every instruction of the inner products is an FMA.
+template <int DIM, int NP, int NG, typename R>
+__global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+                                                              const int32_t* __restrict__ fr, const R* __restrict__ D,
+                                                              const R* __restrict__ lamf, const R* __restrict__ muf,
+                                                              const RefTables* __restrict__ rtp, const R* __restrict__ x,
+                                                              const int* __restrict__ xidx, int64_t ld, R* __restrict__ y,
+                                                              R scale) {
+    using F = FaceReg<DIM, NP, NG, R>;
+    constexpr int NS = F::NS, NPP = F::NPP, NVS = F::NVS;
+    static_assert(DIM * NP <= 32 && 2 * NP <= 32, "register-blocked face kernel needs d*N_phi <= 32");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* sm = reinterpret_cast<R*>(smraw);
+    if (xidx) x += (int64_t)(*xidx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    __shared__ R sS[NG * NG];
+    for (int t = threadIdx.x; t < NG * NG; t += blockDim.x) sS[t] = (R)rtp->S[t];
+    R* sV = sm + warp * F::PER_WARP;   // [s][k][b][n] rows padded
+    R* sG = sV + F::SZ_V;              // [k][l][b][m]
+    R* sT = sG + F::SZ_G;              // [c][b][m]
+    R* sH = sT + F::SZ_T;              // [c][b][m] rows padded
+    for (int t = lane; t < F::PER_WARP; t += 32) sV[t] = (R)0;   // padding stays zero
+    __syncthreads();
+    const bool gl = lane < DIM * NP;          // gather lane: column (gl_l, gl_m)
+    const int gl_l = gl ? lane / NP : 0, gl_m = gl ? lane % NP : 0;
+    const bool sc = lane < 2 * NP;            // scatter lane: row (sc_s, sc_n)
+    const int sc_s = sc ? lane / NP : 0, sc_n = sc ? lane % NP : 0;
+    constexpr int DFACE = 2 * DIM * NP * NP;
+    for (int64_t f = blockIdx.x * (int64_t)wpb + warp; f < n_face; f += (int64_t)gridDim.x * wpb) {
+        const int el = fl[f], er = fr[f];
+        const R* Df = D + f * (int64_t)DFACE;
+        // ---- registers: gather column and scatter row of D~
+        R Dg[2][NP], Ds[DIM][NP];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int n = 0; n < NP; ++n) Dg[s][n] = gl ? Df[((s * DIM + gl_l) * NP + n) * NP + gl_m] : (R)0;
+#pragma unroll
+        for (int l = 0; l < DIM; ++l)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) Ds[l][m] = sc ? Df[((sc_s * DIM + l) * NP + sc_n) * NP + m] : (R)0;
+        // ---- neighbours' values, rows (s,k,b) padded
+        const R* xl = x + (int64_t)el * NVS;
+        const R* xr = x + (int64_t)(er >= 0 ? er : el) * NVS;
+#pragma unroll
+        for (int e0 = 0; e0 < NVS; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < NVS) {
+                const int row = e / NP, n = e % NP;
+                sV[row * NPP + n] = xl[e];
+                sV[(DIM * NG + row) * NPP + n] = er >= 0 ? xr[e] : (R)0;
+            }
+        }
+        __syncwarp();
+        // ---- gather: g[k][l][b][m] = sum_s sum_n D~_s[l][n][m] v_s[k][b][n]
+#pragma unroll
+        for (int kb = 0; kb < DIM * NG; ++kb) {
+            R acc = 0;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const R* vr = sV + (s * DIM * NG + kb) * NPP;
+#pragma unroll
+                for (int n = 0; n < NP; ++n) acc = fma(Dg[s][n], vr[n], acc);
+            }
+            if (gl) {
+                const int k = kb / NG, b = kb % NG;
+                sG[((k * DIM + gl_l) * NG + b) * NP + gl_m] = acc;
+            }
+        }
+        __syncwarp();
+        // ---- t = E_j : g
+        const R lam = lamf[f], mu = muf[f];
+        constexpr int NT_OUT = NS * NG * NP;
+#pragma unroll
+        for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < NT_OUT) {
+                const int c = e / (NG * NP);
+                const int bm = e % (NG * NP);
+                int a, bb;
+                if (c < DIM) { a = c; bb = c; }
+                else if (DIM == 2) { a = 0; bb = 1; }
+                else { a = c == 3 ? 0 : (c == 4 ? 1 : 0); bb = c == 3 ? 1 : 2; }
+                R val = mu * (sG[(a * DIM + bb) * NG * NP + bm] + sG[(bb * DIM + a) * NG * NP + bm]);
+                if (a == bb) {
+                    R tr = 0;
+#pragma unroll
+                    for (int q = 0; q < DIM; ++q) tr += sG[(q * DIM + q) * NG * NP + bm];
+                    val += lam * tr;
+                }
+                sT[e] = val;
+            }
+        }
+        __syncwarp();
+        // ---- h = scale * S t  (rows (c,b), padded)
+#pragma unroll
+        for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < NT_OUT) {
+                const int c = e / (NG * NP), b = (e / NP) % NG, m = e % NP;
+                R acc = 0;
+#pragma unroll
+                for (int b2 = 0; b2 < NG; ++b2) acc += sS[b * NG + b2] * sT[(c * NG + b2) * NP + m];
+                sH[(c * NG + b) * NPP + m] = scale * acc;
+            }
+        }
+        __syncwarp();
+        // ---- scatter: y_s[k][b][n] += sum_l sum_m D~_s[l][n][m] h[(k,l)][b][m]
+        const int es = sc_s == 0 ? el : er;
+        const bool write = sc && es >= 0;
+#pragma unroll
+        for (int kb = 0; kb < DIM * NG; ++kb) {
+            const int k = kb / NG, b = kb % NG;
+            R acc = 0;
+#pragma unroll
+            for (int l = 0; l < DIM; ++l) {
+                const R* hr = sH + (symc<DIM>(k, l) * NG + b) * NPP;
+#pragma unroll
+                for (int m = 0; m < NP; ++m) acc = fma(Ds[l][m], hr[m], acc);
+            }
+            if (write) atomicAdd(&y[(int64_t)es * NVS + kb * NP + sc_n], acc);
+        }
+        __syncwarp();
+    }
+}
+
+template <int DIM, int NP, int NG, typename R>
+static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx,
+                               int64_t ld, R* y, double scale) {
+    using F = FaceReg<DIM, NP, NG, R>;
+    const int wpb = 4;
+    const size_t smem = sizeof(R) * (size_t)wpb * F::PER_WARP;
+    cudaFuncSetAttribute(face_apply_fast_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 1 << 30);
+    face_apply_fast_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
+        c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale);
+    note_launch(c);
+    return cudaGetLastError();
+}
+
+// Specialised shapes: (2,10,4) space-time p = 3 in 2D, (2,6,3) p = 2 in 2D, (3,10,3) p = 2 in
+// 3D, (2,3,1) Crank-Nicolson p = 1 in 2D.  Returns false when no specialisation exists.
+template <typename R>
+bool launch_face_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx, int64_t ld, R* y,
+                      double scale, cudaError_t* err) {
+    const int d = c->dim, np = c->Nphi, ng = c->Ng;
+    // FP64 stays on the shared-memory kernel: at 1/64 of the FP32 rate the FP64 pipe, not
+    // issue, bounds it, and the register-blocked variant's occupancy is lower.
+    if (sizeof(R) == 8) return false;
+    if (d == 2 && np == 10 && ng == 4) { *err = launch_fast<2, 10, 4, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
+    if (d == 2 && np == 6 && ng == 3) { *err = launch_fast<2, 6, 3, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
+    if (d == 3 && np == 10 && ng == 3) { *err = launch_fast<3, 10, 3, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
+    if (d == 2 && np == 3 && ng == 1) { *err = launch_fast<2, 3, 1, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
+    return false;
+}
+
+template bool launch_face_fast<float>(stdg_ctx*, const float*, const float*, const float*, const float*, const int*, int64_t,
+                                      float*, double, cudaError_t*);
+template bool launch_face_fast<double>(stdg_ctx*, const double*, const double*, const double*, const double*, const int*,
+                                       int64_t, double*, double, cudaError_t*);
+
+}  // namespace stdg

@@ -278,6 +278,98 @@ __global__ void __launch_bounds__(128) pre1_apply_kernel(int64_t n_elem, int dim
     }
 }
 
+// Register-blocked variant for d*N_phi <= 32: lane q holds column q of V (for u = V^T r),
+// lane `row` holds row `row` of V (for z = V w); the rows of r and w are read from shared
+// memory by all lanes at once (broadcast), so the inner loops are FMAs.
+template <int DIM, int NP, int NG, typename R>
+__global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, const R* __restrict__ V, const R* __restrict__ B,
+                                                             const R* __restrict__ r, const int* __restrict__ ridx,
+                                                             int64_t ld_vec, R* __restrict__ z) {
+    constexpr int N = DIM * NP;
+    static_assert(N <= 32, "register-blocked block-Jacobi apply needs d*N_phi <= 32");
+    __shared__ R s_r[4][N * NG], s_w[4][N * NG];
+    if (ridx) r += (int64_t)(*ridx) * ld_vec;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    R* sr = s_r[warp];
+    R* sw = s_w[warp];
+    const bool act = lane < N;
+    const int q = act ? lane : 0;
+    for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
+        const R* Ve = V + e * (int64_t)(N * N);
+        const R* re = r + e * (int64_t)(N * NG);
+        // r rows (k,n) with the NG time values contiguous
+#pragma unroll
+        for (int t0 = 0; t0 < N * NG; t0 += 32) {
+            const int t = t0 + lane;
+            if (t < N * NG) {
+                const int k = t / (NG * NP), a = (t / NP) % NG, n = t % NP;
+                sr[(k * NP + n) * NG + a] = re[t];
+            }
+        }
+        R Vc[N];
+#pragma unroll
+        for (int row = 0; row < N; ++row) Vc[row] = act ? Ve[row * N + q] : (R)0;
+        __syncwarp();
+        // u[q][a] = sum_row V[row][q] r[row][a];  w[q] = B_q u[q]
+        R u[NG];
+#pragma unroll
+        for (int a = 0; a < NG; ++a) u[a] = 0;
+#pragma unroll
+        for (int row = 0; row < N; ++row)
+#pragma unroll
+            for (int a = 0; a < NG; ++a) u[a] = fma(Vc[row], sr[row * NG + a], u[a]);
+        if (act) {
+            const R* Bq = B + (e * N + q) * (int64_t)(NG * NG);
+#pragma unroll
+            for (int a = 0; a < NG; ++a) {
+                R s = 0;
+#pragma unroll
+                for (int b = 0; b < NG; ++b) s = fma(Bq[a * NG + b], u[b], s);
+                sw[q * NG + a] = s;
+            }
+        }
+        R Vr[N];
+#pragma unroll
+        for (int qq = 0; qq < N; ++qq) Vr[qq] = act ? Ve[q * N + qq] : (R)0;
+        __syncwarp();
+        // z[row][a] = sum_q V[row][q] w[q][a], row = lane
+        R acc[NG];
+#pragma unroll
+        for (int a = 0; a < NG; ++a) acc[a] = 0;
+#pragma unroll
+        for (int qq = 0; qq < N; ++qq)
+#pragma unroll
+            for (int a = 0; a < NG; ++a) acc[a] = fma(Vr[qq], sw[qq * NG + a], acc[a]);
+        if (act) {
+            const int k = q / NP, n = q % NP;
+            R* ze = z + e * (int64_t)(N * NG);
+#pragma unroll
+            for (int a = 0; a < NG; ++a) ze[(k * NG + a) * NP + n] = acc[a];
+        }
+        __syncwarp();
+    }
+}
+
+template <typename R>
+static bool pre1_apply_fast(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld,
+                            cudaError_t* err) {
+    const int64_t blocks = std::min<int64_t>((c->n_elem + 3) / 4, 1 << 30);
+    const int d = c->dim, np = c->Nphi, ng = c->Ng;
+#define STDG_PRE_FAST(D_, NP_, NG_)                                                                        \
+    if (d == D_ && np == NP_ && ng == NG_) {                                                              \
+        pre1_apply_reg_kernel<D_, NP_, NG_, R><<<(unsigned)blocks, 128, 0, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z); \
+        note_launch(c);                                                                                    \
+        *err = cudaGetLastError();                                                                         \
+        return true;                                                                                       \
+    }
+    STDG_PRE_FAST(2, 10, 4)
+    STDG_PRE_FAST(2, 6, 3)
+    STDG_PRE_FAST(3, 10, 3)
+    STDG_PRE_FAST(2, 3, 1)
+#undef STDG_PRE_FAST
+    return false;
+}
+
 cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* d_elem_face, int* d_status) {
     const int n = c->dim * c->Nphi;
     const size_t smem = sizeof(double) * ((size_t)2 * n * (n + 1) + (size_t)c->dim * c->Nphi * c->Nphi + c->Nphi * c->Nphi +
@@ -305,6 +397,8 @@ cudaError_t launch_pre1_time(stdg_ctx* c, double dt) {
 
 template <typename R>
 static cudaError_t pre1_apply_t(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld) {
+    cudaError_t fe;
+    if (pre1_apply_fast<R>(c, V, B, r, z, ridx, ld, &fe)) return fe;
     const int n = c->dim * c->Nphi;
     const int wpb = 4;
     const size_t smem = sizeof(R) * (size_t)wpb * (n * (n + 1) + 2 * n * c->Ng);

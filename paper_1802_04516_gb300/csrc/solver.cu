@@ -24,8 +24,9 @@
 namespace stdg {
 
 constexpr int kMaxRestart = 64;
-constexpr int kRedBlocks = 304;     // 2 x 152 SMs
+constexpr int kRedBlocks = 1216;    // 8 x 152 SMs
 constexpr int kRedThreads = 256;
+constexpr int kDotChunk = 16;       // basis vectors per pass of the multi-dot kernels
 
 struct DevScalars {
     // current Krylov level
@@ -79,6 +80,29 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;   // valid in thread 0
 }
 
+// Per-thread dot-product accumulator: FP64 for FP64 vectors; for FP32 vectors an error-free
+// (TwoProduct + TwoSum) pair of floats, so FP32 inner products carry FP64-level accuracy
+// without FP64 arithmetic (GB300's FP64 rate is 1/64 of FP32).
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float pe = fmaf(a, b, -p);
+        const float t = s + p;
+        const float z = t - s;
+        const float te = (s - (t - z)) + (p - z);
+        s = t;
+        c += te + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // sum of partials[0..nb) in a single block; result in thread 0
 __device__ __forceinline__ double sum_partials(const double* p, int nb) {
     double v = 0;
@@ -92,10 +116,10 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
 
 template <typename A, typename B>
 __global__ void dot_partial_kernel(int64_t n, const A* __restrict__ a, const B* __restrict__ b, double* __restrict__ out) {
-    double acc = 0;
+    Acc<A> acc;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)a[i] * (double)b[i];
-    double s = block_sum(acc);
+        acc.add(a[i], b[i]);
+    double s = block_sum(acc.value());
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
@@ -197,13 +221,13 @@ __global__ void cg_p_kernel(int64_t n, const DevScalars* __restrict__ sc, const 
 template <typename R>
 __global__ void gm_res_kernel(int64_t n, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ v0,
                               double* __restrict__ part) {
-    double rr = 0;
+    Acc<R> rr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const R ri = b[i] - Ax[i];
         v0[i] = ri;
-        rr += (double)ri * (double)ri;
+        rr.add(ri, ri);
     }
-    double s = block_sum(rr);
+    double s = block_sum(rr.value());
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
@@ -254,18 +278,57 @@ template <typename R>
 __global__ void gm_mdot_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, const R* __restrict__ w,
                                double* __restrict__ part) {
     const int J = sc->j;
-    for (int k0 = 0; k0 <= J; k0 += 8) {
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const int kn = min(8, J + 1 - k0);
+    for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
+        Acc<R> acc[kDotChunk];
+        const int kn = min(kDotChunk, J + 1 - k0);
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            const double wi = (double)w[i];
+            const R wi = w[i];
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-                if (kk < kn) acc[kk] += (double)V[(int64_t)(k0 + kk) * n + i] * wi;
+            for (int kk = 0; kk < kDotChunk; ++kk)
+                if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * n + i], wi);
         }
-        for (int kk = 0; kk < kn; ++kk) {
-            double s = block_sum(acc[kk]);
-            if (threadIdx.x == 0) part[(k0 + kk) * kRedBlocks + blockIdx.x] = s;
+#pragma unroll
+        for (int kk = 0; kk < kDotChunk; ++kk) {   // constant bound keeps acc[] in registers
+            if (kk < kn) {                            // kn is uniform over the block
+                double s = block_sum(acc[kk].value());
+                if (threadIdx.x == 0) part[(k0 + kk) * kRedBlocks + blockIdx.x] = s;
+            }
+        }
+    }
+}
+
+// Second Gram-Schmidt pass fused with the first subtraction:
+// w <- w - sum_k h1[k] V_k, then partials of V_k . w for the re-orthogonalisation.
+template <typename R>
+__global__ void gm_orth_fused_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, R* __restrict__ w,
+                                     double* __restrict__ part) {
+    const int J = sc->j;
+    __shared__ double h[kMaxRestart + 2];
+    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = sc->hpass[k];
+    __syncthreads();
+    for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
+        Acc<R> acc[kDotChunk];
+        const int kn = min(kDotChunk, J + 1 - k0);
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            R wi;
+            if (k0 == 0) {   // first chunk: form and store the projected w (in the vector precision)
+                R v = w[i];
+                for (int k = 0; k <= J; ++k) v = fma(-(R)h[k], V[(int64_t)k * n + i], v);
+                wi = v;
+                w[i] = wi;
+            } else {
+                wi = w[i];
+            }
+#pragma unroll
+            for (int kk = 0; kk < kDotChunk; ++kk)
+                if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * n + i], wi);
+        }
+#pragma unroll
+        for (int kk = 0; kk < kDotChunk; ++kk) {   // constant bound keeps acc[] in registers
+            if (kk < kn) {                            // kn is uniform over the block
+                double s = block_sum(acc[kk].value());
+                if (threadIdx.x == 0) part[(k0 + kk) * kRedBlocks + blockIdx.x] = s;
+            }
         }
     }
 }
@@ -290,16 +353,15 @@ __global__ void gm_maxpy_kernel(int64_t n, const DevScalars* __restrict__ sc, co
     __shared__ double h[kMaxRestart + 2];
     for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = sc->hpass[k];
     __syncthreads();
-    double nn = 0;
+    Acc<R> nn;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = (double)w[i];
-        for (int k = 0; k <= J; ++k) v -= h[k] * (double)V[(int64_t)k * n + i];
-        const R vr = (R)v;
-        w[i] = vr;
-        nn += (double)vr * (double)vr;
+        R v = w[i];
+        for (int k = 0; k <= J; ++k) v = fma(-(R)h[k], V[(int64_t)k * n + i], v);
+        w[i] = v;
+        nn.add(v, v);
     }
     if (want_norm) {
-        double s = block_sum(nn);
+        double s = block_sum(nn.value());
         if (threadIdx.x == 0) part[blockIdx.x] = s;
     }
 }
@@ -623,11 +685,12 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
                           } else {
                               F.check(apply_idx(V, &sc->j, w));
                           }
-                          for (int pass = 0; pass < 2; ++pass) {
-                              gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials); note_launch(c);
-                              gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, pass); note_launch(c);
-                              gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials, pass); note_launch(c);
-                          }
+                          // classical Gram-Schmidt twice, in three passes over the basis
+                          gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials); note_launch(c);
+                          gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, 0); note_launch(c);
+                          gm_orth_fused_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials); note_launch(c);
+                          gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, 1); note_launch(c);
+                          gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials, 1); note_launch(c);
                           gm_norm_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials); note_launch(c);
                           gm_next_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, w, V); note_launch(c);
                           gm_givens_kernel<<<1, 32, 0, c->stream>>>(sc, h, use); note_launch(c);

@@ -177,6 +177,11 @@ cudaError_t launch_project_plane_wave(stdg_ctx* c, int shot, int kind, const dou
                                       double amp, double t, const double* d_rule, int nq);
 cudaError_t launch_initial_guess(stdg_ctx* c, int shot, double* x);
 
+// operator_fast.cu: compile-time-shape face kernel; false if the shape is not specialised
+template <typename R>
+bool launch_face_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx, int64_t ld, R* y,
+                      double scale, cudaError_t* err);
+
 // precond.cu
 cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* d_elem_face, int* d_status);
 cudaError_t launch_pre1_time(stdg_ctx* c, double dt);
