@@ -184,6 +184,10 @@ int stdg_create(stdg_ctx** out, int dim, const stdg_options* opt, void* cuda_str
         stdg_destroy(c);
         return STDG_ECUDA;
     }
+    if (dev_alloc(c, (void**)&c->d_err, sizeof(int)) != STDG_OK || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        stdg_destroy(c);
+        return STDG_ECUDA;
+    }
     double gl[16];
     gauss_legendre01(8, gl, gl + 8);
     if (dev_alloc(c, (void**)&c->d_gl8, sizeof(gl)) != STDG_OK ||
@@ -216,9 +220,10 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     solver_free(c);
     void* keep_rt = c->d_rt;
     void* keep_gl = c->d_gl8;
+    void* keep_err = c->d_err;
     for (void* p : c->allocs)
-        if (p != keep_rt && p != keep_gl) cudaFree(p);
-    c->allocs.assign({keep_rt, keep_gl});
+        if (p != keep_rt && p != keep_gl && p != keep_err) cudaFree(p);
+    c->allocs.assign({keep_rt, keep_gl, keep_err});
     c->d_face_l = c->d_face_r = nullptr;
     c->d_elem_face = nullptr;
     c->d_preV = c->d_preLam = c->d_preB = nullptr;

@@ -9,6 +9,7 @@
 // against rows of h) runs on 128-bit shared-memory loads; all loop bounds and index
 // decompositions are compile-time constants.
 #include <algorithm>
+#include <cstdint>
 
 #include "stdg_internal.h"
 
@@ -53,7 +54,7 @@ __device__ __forceinline__ double dotv<double>(const double* __restrict__ a, con
     return s;
 }
 
-constexpr int round_up(int v, int w) { return (v + w - 1) / w * w; }
+__host__ __device__ constexpr int round_up(int v, int w) { return (v + w - 1) / w * w; }
 
 template <int DIM, int NP, int NG, typename R>
 struct FaceFast {
@@ -221,9 +222,227 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
     }
 }
 
+// ---------------------------------------------------------------------------------
+// TMA-pipelined variant: the next face's D~ block and its two elements' value rows are
+// copied into shared memory by cp.async.bulk (one elected lane, completion on a per-warp
+// mbarrier) while the warp computes the current face.  Register/broadcast arithmetic as
+// above.  Every wait on an mbarrier is bounded; on timeout the kernel records the error
+// in *err and the warp stops.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// true when the phase with the given parity has completed; gives up after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long limit) {
+    for (long i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int DIM, int NP, int NG, typename R>
+struct FaceTma {
+    static constexpr int NS = DIM == 2 ? 3 : 6;
+    static constexpr int NVS = DIM * NG * NP;
+    static constexpr int DFACE = 2 * DIM * NP * NP;
+    static constexpr bool XBULK = (NVS * sizeof(R)) % 16 == 0;        // element rows copyable by TMA
+    static constexpr int STAGE = round_up(DFACE, 16 / (int)sizeof(R)) + 2 * round_up(NVS, 16 / (int)sizeof(R));
+    static constexpr int SZ_G = round_up(DIM * DIM * NG * NP, 4);
+    static constexpr int SZ_T = round_up(NS * NG * NP, 4);
+    static constexpr int SZ_H = round_up(NS * NG * NP, 4);
+    static constexpr int PER_WARP = round_up(2 * STAGE + SZ_G + SZ_T + SZ_H, 16 / (int)sizeof(R));
+};
+
+template <int DIM, int NP, int NG, typename R>
+__global__ void __launch_bounds__(128) face_apply_tma_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+                                                             const int32_t* __restrict__ fr, const R* __restrict__ D,
+                                                             const R* __restrict__ lamf, const R* __restrict__ muf,
+                                                             const RefTables* __restrict__ rtp, const R* __restrict__ x,
+                                                             const int* __restrict__ xidx, int64_t ld, R* __restrict__ y,
+                                                             R scale, int* __restrict__ err) {
+    using F = FaceTma<DIM, NP, NG, R>;
+    constexpr int NS = F::NS, NVS = F::NVS, DFACE = F::DFACE;
+    constexpr int XOFF = round_up(DFACE, 16 / (int)sizeof(R));
+    constexpr int XR = round_up(NVS, 16 / (int)sizeof(R));
+    static_assert(DIM * NP <= 32 && 2 * NP <= 32, "register-blocked face kernel needs d*N_phi <= 32");
+    static_assert((DFACE * sizeof(R)) % 16 == 0, "D~ block must be a multiple of 16 bytes");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[4][2];
+    __shared__ R sS[NG * NG];
+    if (xidx) x += (int64_t)(*xidx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < NG * NG; t += blockDim.x) sS[t] = (R)rtp->S[t];
+    R* base = reinterpret_cast<R*>(smraw) + warp * F::PER_WARP;
+    auto stage = [&](int s_) { return s_ ? base + F::STAGE : base; };
+    R* sG = base + 2 * F::STAGE;
+    R* sT = sG + F::SZ_G;
+    R* sH = sT + F::SZ_T;
+    for (int t = lane; t < 2 * F::STAGE; t += 32) base[t] = (R)0;   // the r-side rows of boundary faces stay finite
+    const uint32_t bar0 = smem_u32(&bars[warp][0]), bar1 = smem_u32(&bars[warp][1]);
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool gl = lane < DIM * NP;
+    const int gl_l = gl ? lane / NP : 0, gl_m = gl ? lane % NP : 0;
+    const bool sc = lane < 2 * NP;
+    const int sc_s = sc ? lane / NP : 0, sc_n = sc ? lane % NP : 0;
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    constexpr long kPollLimit = 1L << 24;
+
+    auto issue = [&](int64_t f, int st) {   // lane 0 only
+        const int el = fl[f], er = fr[f];
+        const uint32_t bar = st ? bar1 : bar0;
+        uint32_t bytes = DFACE * sizeof(R);
+        if (F::XBULK) bytes += (er >= 0 ? 2 : 1) * NVS * sizeof(R);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(smem_u32(stage(st)), D + f * (int64_t)DFACE, DFACE * sizeof(R), bar);
+        if (F::XBULK) {
+            bulk_g2s(smem_u32(stage(st) + XOFF), x + (int64_t)el * NVS, NVS * sizeof(R), bar);
+            if (er >= 0) bulk_g2s(smem_u32(stage(st) + XOFF + XR), x + (int64_t)er * NVS, NVS * sizeof(R), bar);
+        }
+    };
+
+    int64_t f = blockIdx.x * (int64_t)wpb + warp;
+    if (f < n_face && lane == 0) issue(f, 0);
+    uint32_t ph0 = 0, ph1 = 0;
+    int st = 0;
+    for (; f < n_face; f += stride) {
+        const int64_t fn = f + stride;
+        if (fn < n_face && lane == 0) issue(fn, st ^ 1);
+        if (!mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit)) {
+            if (lane == 0) atomicExch(err, 1);
+            // drain the copy issued for fn before leaving (bounded as well)
+            if (fn < n_face) mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit);
+            break;
+        }
+        if (st) ph1 ^= 1u; else ph0 ^= 1u;
+        const R* sD = stage(st);
+        const R* sV = stage(st) + XOFF;   // rows (s,k,b), NP values each, side r at +XR
+        const int el = fl[f], er = fr[f];
+        if (!F::XBULK) {   // element rows by plain loads
+            R* w = stage(st) + XOFF;
+#pragma unroll
+            for (int e0 = 0; e0 < NVS; e0 += 32) {
+                const int e = e0 + lane;
+                if (e < NVS) {
+                    w[e] = x[(int64_t)el * NVS + e];
+                    w[XR + e] = er >= 0 ? x[(int64_t)er * NVS + e] : (R)0;
+                }
+            }
+            __syncwarp();
+        }
+        R Dg[2][NP], Ds[DIM][NP];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int n = 0; n < NP; ++n) Dg[s][n] = sD[((s * DIM + gl_l) * NP + n) * NP + gl_m];
+#pragma unroll
+        for (int l = 0; l < DIM; ++l)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) Ds[l][m] = sD[((sc_s * DIM + l) * NP + sc_n) * NP + m];
+        // gather (side r contributes zero on a boundary face: its D~ block is zero)
+#pragma unroll
+        for (int kb = 0; kb < DIM * NG; ++kb) {
+            R acc = 0;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const R* vr = sV + s * XR + kb * NP;
+#pragma unroll
+                for (int n = 0; n < NP; ++n) acc = fma(Dg[s][n], vr[n], acc);
+            }
+            if (gl) sG[((kb / NG * DIM + gl_l) * NG + kb % NG) * NP + gl_m] = acc;
+        }
+        __syncwarp();
+        const R lam = lamf[f], mu = muf[f];
+        constexpr int NT_OUT = NS * NG * NP;
+#pragma unroll
+        for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < NT_OUT) {
+                const int c = e / (NG * NP);
+                const int bm = e % (NG * NP);
+                int a, bb;
+                if (c < DIM) { a = c; bb = c; }
+                else if (DIM == 2) { a = 0; bb = 1; }
+                else { a = c == 3 ? 0 : (c == 4 ? 1 : 0); bb = c == 3 ? 1 : 2; }
+                R val = mu * (sG[(a * DIM + bb) * NG * NP + bm] + sG[(bb * DIM + a) * NG * NP + bm]);
+                if (a == bb) {
+                    R tr = 0;
+#pragma unroll
+                    for (int q = 0; q < DIM; ++q) tr += sG[(q * DIM + q) * NG * NP + bm];
+                    val += lam * tr;
+                }
+                sT[e] = val;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < NT_OUT) {
+                const int c = e / (NG * NP), b = (e / NP) % NG, m = e % NP;
+                R acc = 0;
+#pragma unroll
+                for (int b2 = 0; b2 < NG; ++b2) acc += sS[b * NG + b2] * sT[(c * NG + b2) * NP + m];
+                sH[e] = scale * acc;   // rows (c,b), NP values
+            }
+        }
+        __syncwarp();
+        const int es = sc_s == 0 ? el : er;
+        const bool write = sc && es >= 0;
+#pragma unroll
+        for (int kb = 0; kb < DIM * NG; ++kb) {
+            const int k = kb / NG, b = kb % NG;
+            R acc = 0;
+#pragma unroll
+            for (int l = 0; l < DIM; ++l) {
+                const R* hr = sH + (symc<DIM>(k, l) * NG + b) * NP;
+#pragma unroll
+                for (int m = 0; m < NP; ++m) acc = fma(Ds[l][m], hr[m], acc);
+            }
+            if (write) atomicAdd(&y[(int64_t)es * NVS + kb * NP + sc_n], acc);
+        }
+        __syncwarp();   // stage st is free for the copy issued in the next iteration
+        st ^= 1;
+    }
+}
+
 template <int DIM, int NP, int NG, typename R>
 static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx,
                                int64_t ld, R* y, double scale) {
+    using T = FaceTma<DIM, NP, NG, R>;
+    const bool aligned = (reinterpret_cast<uintptr_t>(D) % 16 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
+                         ((ld * (int64_t)sizeof(R)) % 16 == 0);
+    if (aligned && c->d_err) {
+        const int wpb = 4;
+        const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
+        cudaFuncSetAttribute(face_apply_tma_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 152 * 16);
+        face_apply_tma_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
+            c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, c->d_err);
+        note_launch(c);
+        return cudaGetLastError();
+    }
     using F = FaceReg<DIM, NP, NG, R>;
     const int wpb = 4;
     const size_t smem = sizeof(R) * (size_t)wpb * F::PER_WARP;

@@ -48,7 +48,7 @@ struct DevScalars {
 
 struct Workspace {
     int m = 30;
-    int64_t n = 0;
+    int64_t n = 0, ldv = 0;
     DevScalars* sc = nullptr;
     double* partials = nullptr;   // (kMaxRestart + 2) * kRedBlocks
     double* dparams = nullptr;    // t^n, dt, step index
@@ -101,6 +101,32 @@ template <> struct Acc<float> {
         c += te + pe;
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// 16-byte vector access: VW = 4 floats or 2 doubles per load/store.  Streaming kernels walk
+// n / VW vectors with a grid-stride loop and give the n % VW tail to one thread; every
+// pointer they vectorise is 16-byte aligned (separate allocations, or basis columns at a
+// leading dimension that is a multiple of 64 elements).
+template <typename R> struct VL;
+template <> struct VL<float> {
+    static constexpr int W = 4;
+    __device__ __forceinline__ static void ld(const float* p, float (&o)[4]) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct VL<double> {
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void ld(const double* p, double (&o)[2]) {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
 };
 
 // sum of partials[0..nb) in a single block; result in thread 0
@@ -220,13 +246,20 @@ __global__ void cg_p_kernel(int64_t n, const DevScalars* __restrict__ sc, const 
 // ---------------------------------------------------------------------------------
 template <typename R>
 __global__ void gm_res_kernel(int64_t n, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ v0,
-                              double* __restrict__ part) {
+                             double* __restrict__ part) {
+    constexpr int W = VL<R>::W;
+    const int64_t nv = n / W;
     Acc<R> rr;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R ri = b[i] - Ax[i];
-        v0[i] = ri;
-        rr.add(ri, ri);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R bb[W], aa[W];
+        VL<R>::ld(b + g * W, bb);
+        VL<R>::ld(Ax + g * W, aa);
+#pragma unroll
+        for (int u = 0; u < W; ++u) { bb[u] -= aa[u]; rr.add(bb[u], bb[u]); }
+        VL<R>::st(v0 + g * W, bb);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) { const R ri = b[i] - Ax[i]; v0[i] = ri; rr.add(ri, ri); }
     double s = block_sum(rr.value());
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -268,25 +301,48 @@ __global__ void gm_cycle_start_kernel(DevScalars* sc, const double* part, cudaGr
 template <typename R>
 __global__ void gm_scale0_kernel(int64_t n, const DevScalars* __restrict__ sc, R* __restrict__ v0) {
     if (!sc->flag_inner) return;
-    const double s = 1.0 / sc->gbeta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v0[i] = (R)((double)v0[i] * s);
+    constexpr int W = VL<R>::W;
+    const R s = (R)(1.0 / sc->gbeta);
+    const int64_t nv = n / W;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R a[W];
+        VL<R>::ld(v0 + g * W, a);
+#pragma unroll
+        for (int u = 0; u < W; ++u) a[u] *= s;
+        VL<R>::st(v0 + g * W, a);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) v0[i] *= s;
 }
 
-// partials[k][blk] = sum_i V_k[i] w[i], k = 0..j
+// partials[k][blk] = sum_i V_k[i] w[i], k = 0..j  (basis columns at stride ldv)
 template <typename R>
-__global__ void gm_mdot_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, const R* __restrict__ w,
-                               double* __restrict__ part) {
+__global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc,
+                                                      const R* __restrict__ V, const R* __restrict__ w,
+                                                      double* __restrict__ part) {
+    constexpr int W = VL<R>::W;
     const int J = sc->j;
+    const int64_t nv = n / W;
     for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
         Acc<R> acc[kDotChunk];
         const int kn = min(kDotChunk, J + 1 - k0);
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            const R wi = w[i];
+        for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+            R wv[W];
+            VL<R>::ld(w + g * W, wv);
 #pragma unroll
             for (int kk = 0; kk < kDotChunk; ++kk)
-                if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * n + i], wi);
+                if (kk < kn) {
+                    R vv[W];
+                    VL<R>::ld(V + (int64_t)(k0 + kk) * ldv + g * W, vv);
+#pragma unroll
+                    for (int u = 0; u < W; ++u) acc[kk].add(vv[u], wv[u]);
+                }
         }
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            for (int64_t i = nv * W; i < n; ++i)
+#pragma unroll
+                for (int kk = 0; kk < kDotChunk; ++kk)
+                    if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * ldv + i], w[i]);
 #pragma unroll
         for (int kk = 0; kk < kDotChunk; ++kk) {   // constant bound keeps acc[] in registers
             if (kk < kn) {                            // kn is uniform over the block
@@ -300,32 +356,53 @@ __global__ void gm_mdot_kernel(int64_t n, const DevScalars* __restrict__ sc, con
 // Second Gram-Schmidt pass fused with the first subtraction:
 // w <- w - sum_k h1[k] V_k, then partials of V_k . w for the re-orthogonalisation.
 template <typename R>
-__global__ void gm_orth_fused_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, R* __restrict__ w,
-                                     double* __restrict__ part) {
+__global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc,
+                                                            const R* __restrict__ V, R* __restrict__ w,
+                                                            double* __restrict__ part) {
+    constexpr int W = VL<R>::W;
     const int J = sc->j;
-    __shared__ double h[kMaxRestart + 2];
-    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = sc->hpass[k];
+    __shared__ R h[kMaxRestart + 2];
+    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)sc->hpass[k];
     __syncthreads();
+    const int64_t nv = n / W;
     for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
         Acc<R> acc[kDotChunk];
         const int kn = min(kDotChunk, J + 1 - k0);
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            R wi;
+        for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+            R wv[W];
+            VL<R>::ld(w + g * W, wv);
             if (k0 == 0) {   // first chunk: form and store the projected w (in the vector precision)
-                R v = w[i];
-                for (int k = 0; k <= J; ++k) v = fma(-(R)h[k], V[(int64_t)k * n + i], v);
-                wi = v;
-                w[i] = wi;
-            } else {
-                wi = w[i];
+                for (int k = 0; k <= J; ++k) {
+                    R vv[W];
+                    VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
+#pragma unroll
+                    for (int u = 0; u < W; ++u) wv[u] = fma(-h[k], vv[u], wv[u]);
+                }
+                VL<R>::st(w + g * W, wv);
             }
 #pragma unroll
             for (int kk = 0; kk < kDotChunk; ++kk)
-                if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * n + i], wi);
-        }
+                if (kk < kn) {
+                    R vv[W];
+                    VL<R>::ld(V + (int64_t)(k0 + kk) * ldv + g * W, vv);
 #pragma unroll
-        for (int kk = 0; kk < kDotChunk; ++kk) {   // constant bound keeps acc[] in registers
-            if (kk < kn) {                            // kn is uniform over the block
+                    for (int u = 0; u < W; ++u) acc[kk].add(vv[u], wv[u]);
+                }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            for (int64_t i = nv * W; i < n; ++i) {
+                R wi = w[i];
+                if (k0 == 0) {
+                    for (int k = 0; k <= J; ++k) wi = fma(-h[k], V[(int64_t)k * ldv + i], wi);
+                    w[i] = wi;
+                }
+#pragma unroll
+                for (int kk = 0; kk < kDotChunk; ++kk)
+                    if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * ldv + i], wi);
+            }
+#pragma unroll
+        for (int kk = 0; kk < kDotChunk; ++kk) {
+            if (kk < kn) {
                 double s = block_sum(acc[kk].value());
                 if (threadIdx.x == 0) part[(k0 + kk) * kRedBlocks + blockIdx.x] = s;
             }
@@ -347,19 +424,36 @@ __global__ void gm_mdot_final_kernel(DevScalars* sc, const double* part, int pas
 
 // w -= sum_k hpass[k] V_k; optionally partial ||w||^2
 template <typename R>
-__global__ void gm_maxpy_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, R* __restrict__ w,
-                                double* __restrict__ part, int want_norm) {
+__global__ void __launch_bounds__(256) gm_maxpy_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc,
+                                                       const R* __restrict__ V, R* __restrict__ w, double* __restrict__ part,
+                                                       int want_norm) {
+    constexpr int W = VL<R>::W;
     const int J = sc->j;
-    __shared__ double h[kMaxRestart + 2];
-    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = sc->hpass[k];
+    __shared__ R h[kMaxRestart + 2];
+    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)sc->hpass[k];
     __syncthreads();
+    const int64_t nv = n / W;
     Acc<R> nn;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        R v = w[i];
-        for (int k = 0; k <= J; ++k) v = fma(-(R)h[k], V[(int64_t)k * n + i], v);
-        w[i] = v;
-        nn.add(v, v);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R wv[W];
+        VL<R>::ld(w + g * W, wv);
+        for (int k = 0; k <= J; ++k) {
+            R vv[W];
+            VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
+#pragma unroll
+            for (int u = 0; u < W; ++u) wv[u] = fma(-h[k], vv[u], wv[u]);
+        }
+        VL<R>::st(w + g * W, wv);
+#pragma unroll
+        for (int u = 0; u < W; ++u) nn.add(wv[u], wv[u]);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) {
+            R wi = w[i];
+            for (int k = 0; k <= J; ++k) wi = fma(-h[k], V[(int64_t)k * ldv + i], wi);
+            w[i] = wi;
+            nn.add(wi, wi);
+        }
     if (want_norm) {
         double s = block_sum(nn.value());
         if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -372,13 +466,23 @@ __global__ void gm_norm_final_kernel(DevScalars* sc, const double* part) {
 }
 
 template <typename R>
-__global__ void gm_next_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ w, R* __restrict__ V) {
+__global__ void gm_next_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc, const R* __restrict__ w,
+                               R* __restrict__ V) {
+    constexpr int W = VL<R>::W;
     const int J = sc->j;
-    const double h = sc->hcol[J + 1];
-    const double s = h > 0.0 ? 1.0 / h : 0.0;
-    R* vn = V + (int64_t)(J + 1) * n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        vn[i] = (R)((double)w[i] * s);
+    const double hh = sc->hcol[J + 1];
+    const R s = (R)(hh > 0.0 ? 1.0 / hh : 0.0);
+    R* vn = V + (int64_t)(J + 1) * ldv;
+    const int64_t nv = n / W;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R a[W];
+        VL<R>::ld(w + g * W, a);
+#pragma unroll
+        for (int u = 0; u < W; ++u) a[u] *= s;
+        VL<R>::st(vn + g * W, a);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) vn[i] = w[i] * s;
 }
 
 __global__ void gm_givens_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int use_h) {
@@ -422,37 +526,78 @@ __global__ void gm_solve_kernel(DevScalars* sc) {
 }
 
 template <typename R>
-__global__ void gm_update_x_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, R* __restrict__ x) {
+__global__ void gm_update_x_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc, const R* __restrict__ V,
+                                   R* __restrict__ x) {
+    constexpr int W = VL<R>::W;
     const int J = sc->j;
     if (J == 0) return;
-    __shared__ double y[kMaxRestart];
-    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = sc->y[k];
+    __shared__ R y[kMaxRestart];
+    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = (R)sc->y[k];
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = (double)x[i];
-        for (int k = 0; k < J; ++k) v += y[k] * (double)V[(int64_t)k * n + i];
-        x[i] = (R)v;
+    const int64_t nv = n / W;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R a[W];
+        VL<R>::ld(x + g * W, a);
+        for (int k = 0; k < J; ++k) {
+            R vv[W];
+            VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
+#pragma unroll
+            for (int u = 0; u < W; ++u) a[u] = fma(y[k], vv[u], a[u]);
+        }
+        VL<R>::st(x + g * W, a);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) {
+            R a = x[i];
+            for (int k = 0; k < J; ++k) a = fma(y[k], V[(int64_t)k * ldv + i], a);
+            x[i] = a;
+        }
 }
 
 // t = sum_{k<j} y_k V_k (right preconditioning: x += P^{-1} t afterwards)
 template <typename R>
-__global__ void gm_combine_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ V, R* __restrict__ t) {
+__global__ void gm_combine_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc, const R* __restrict__ V,
+                                  R* __restrict__ t) {
+    constexpr int W = VL<R>::W;
     const int J = sc->j;
-    __shared__ double y[kMaxRestart];
-    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = sc->y[k];
+    __shared__ R y[kMaxRestart];
+    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = (R)sc->y[k];
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = 0;
-        for (int k = 0; k < J; ++k) v += y[k] * (double)V[(int64_t)k * n + i];
-        t[i] = (R)v;
+    const int64_t nv = n / W;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R a[W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) a[u] = 0;
+        for (int k = 0; k < J; ++k) {
+            R vv[W];
+            VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
+#pragma unroll
+            for (int u = 0; u < W; ++u) a[u] = fma(y[k], vv[u], a[u]);
+        }
+        VL<R>::st(t + g * W, a);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) {
+            R a = 0;
+            for (int k = 0; k < J; ++k) a = fma(y[k], V[(int64_t)k * ldv + i], a);
+            t[i] = a;
+        }
 }
 
 template <typename R>
 __global__ void axpy_kernel(int64_t n, R* __restrict__ x, const R* __restrict__ z) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = (R)((double)x[i] + (double)z[i]);
+    constexpr int W = VL<R>::W;
+    const int64_t nv = n / W;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
+        R a[W], b[W];
+        VL<R>::ld(x + g * W, a);
+        VL<R>::ld(z + g * W, b);
+#pragma unroll
+        for (int u = 0; u < W; ++u) a[u] += b[u];
+        VL<R>::st(x + g * W, a);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int64_t i = nv * W; i < n; ++i) x[i] += z[i];
 }
 
 __global__ void gm_cycle_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int use_h) {
@@ -661,7 +806,7 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
                         R* zbuf, R* tbuf, double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
-    const int64_t n = ws->n;
+    const int64_t n = ws->n, ldv = ws->ldv;
     const int m = ws->m;
     DevScalars* sc = ws->sc;
     F.loop(&sc->flag_outer,
@@ -680,29 +825,29 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
                       },
                       [&](cudaGraphConditionalHandle h, int use) {
                           if (use_prec) {   // right preconditioning: w = A P^{-1} v_j
-                              F.check(prec(V, zbuf, &sc->j, n));
+                              F.check(prec(V, zbuf, &sc->j, ldv));
                               F.check(apply(zbuf, w));
                           } else {
                               F.check(apply_idx(V, &sc->j, w));
                           }
                           // classical Gram-Schmidt twice, in three passes over the basis
-                          gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials); note_launch(c);
+                          gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, w, ws->partials); note_launch(c);
                           gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, 0); note_launch(c);
-                          gm_orth_fused_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials); note_launch(c);
+                          gm_orth_fused_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, w, ws->partials); note_launch(c);
                           gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, 1); note_launch(c);
-                          gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, w, ws->partials, 1); note_launch(c);
+                          gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, w, ws->partials, 1); note_launch(c);
                           gm_norm_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials); note_launch(c);
-                          gm_next_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, w, V); note_launch(c);
+                          gm_next_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, w, V); note_launch(c);
                           gm_givens_kernel<<<1, 32, 0, c->stream>>>(sc, h, use); note_launch(c);
                           F.check(cudaGetLastError());
                       });
                gm_solve_kernel<<<1, 32, 0, c->stream>>>(sc); note_launch(c);
                if (use_prec) {   // x += P^{-1} (V y)
-                   gm_combine_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, tbuf); note_launch(c);
+                   gm_combine_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, tbuf); note_launch(c);
                    F.check(prec(tbuf, zbuf, nullptr, 0));
                    axpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, zbuf); note_launch(c);
                } else {
-                   gm_update_x_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V, x); note_launch(c);
+                   gm_update_x_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, x); note_launch(c);
                }
                gm_cycle_end_kernel<<<1, 32, 0, c->stream>>>(sc, h_outer, use_outer); note_launch(c);
                F.check(cudaGetLastError());
@@ -717,9 +862,10 @@ static void record_solve(Flow& F, double dt, double* b, double* x) {
     const bool cn = c->opt.scheme == STDG_SCHEME_CN;
     const bool pre = c->opt.preconditioner != 0;
     auto A64 = [&](const double* xx, double* yy) { return launch_apply(c, dt, xx, yy, 1.0); };
-    auto A64i = [&](const double* V, const int* idx, double* yy) { return launch_apply(c, dt, V, yy, 1.0, idx, n); };
+    const int64_t ldv = ws->ldv;
+    auto A64i = [&](const double* V, const int* idx, double* yy) { return launch_apply(c, dt, V, yy, 1.0, idx, ldv); };
     auto A32 = [&](const float* xx, float* yy) { return launch_apply32(c, dt, xx, yy, 1.0); };
-    auto A32i = [&](const float* V, const int* idx, float* yy) { return launch_apply32(c, dt, V, yy, 1.0, idx, n); };
+    auto A32i = [&](const float* V, const int* idx, float* yy) { return launch_apply32(c, dt, V, yy, 1.0, idx, ldv); };
     auto P64 = [&](const double* r, double* z, const int* idx, int64_t ld) { return launch_pre1_apply(c, r, z, idx, ld); };
     auto P32 = [&](const float* r, float* z, const int* idx, int64_t ld) { return launch_pre1_apply32(c, r, z, idx, ld); };
     auto P64c = [&](const double* r, double* z) { return launch_pre1_apply(c, r, z, nullptr, 0); };
@@ -796,13 +942,14 @@ int solver_setup(stdg_ctx* c) {
     ALLOC(ws->r, sizeof(double) * n);
     const bool pre = c->opt.preconditioner != 0;
     if (cn && !mixed) { ALLOC(ws->p, sizeof(double) * n); ALLOC(ws->q, sizeof(double) * n); }
-    if (!cn && !mixed) ALLOC(ws->V, sizeof(double) * n * (ws->m + 1));
+    ws->ldv = (n + 63) / 64 * 64;   // 16-byte aligned basis columns for vector loads
+    if (!cn && !mixed) ALLOC(ws->V, sizeof(double) * ws->ldv * (ws->m + 1));
     if (pre && !mixed) { ALLOC(ws->z, sizeof(double) * n); if (!cn) ALLOC(ws->t, sizeof(double) * n); }
     if (mixed) {
         ALLOC(ws->b32, sizeof(float) * n);
         ALLOC(ws->x32, sizeof(float) * n);
         if (cn) { ALLOC(ws->r32, sizeof(float) * n); ALLOC(ws->p32, sizeof(float) * n); ALLOC(ws->q32, sizeof(float) * n); }
-        else { ALLOC(ws->V32, sizeof(float) * n * (ws->m + 1)); ALLOC(ws->w32, sizeof(float) * n); }
+        else { ALLOC(ws->V32, sizeof(float) * ws->ldv * (ws->m + 1)); ALLOC(ws->w32, sizeof(float) * n); }
         if (pre) { ALLOC(ws->z32, sizeof(float) * n); if (!cn) ALLOC(ws->t32, sizeof(float) * n); }
     }
 #undef ALLOC
@@ -893,6 +1040,11 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
         st->status = h.st_notconv ? STDG_ENOTCONV : STDG_OK;
     }
     c->last_launches = (int64_t)h.launches;
+    if (c->d_err) {
+        int e = 0;
+        STDG_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) STDG_FAIL(c, STDG_ECUDA, "a device-side wait gave up (bounded mbarrier wait)");
+    }
     if (h.st_notconv) STDG_FAIL(c, STDG_ENOTCONV, "Krylov solve reached max_iters");
     return STDG_OK;
 }

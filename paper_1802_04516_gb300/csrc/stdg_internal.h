@@ -129,6 +129,9 @@ struct stdg_ctx {
     int32_t* d_elem_face = nullptr;
     double pre_dt = -1.0;    // slab size the time blocks d_preB were built for
 
+    // ---- device error word: set by kernels whose bounded waits ran out (checked after each call)
+    int* d_err = nullptr;
+
     // ---- solver workspace (solver.cu)
     void* ws = nullptr;
 

@@ -195,3 +195,20 @@ def test_preconditioned_gmres_converges_on_slivers():
     st = s.step(w.dt, 2)
     assert st["status"] == 0 and st["final_rel_res"] <= 1e-8
     assert st["iters_max"] < 3000
+
+
+@pytest.mark.parametrize("name,make", [OP_CASES[i] for i in (0, 2, 3, 4)], ids=[OP_CASES[i][0] for i in (0, 2, 3, 4)])
+def test_fp32_operator_matches_oracle(name, make):
+    # the FP32 operator (orthonormalised blocks rounded to FP32, FP32 arithmetic) used by the
+    # inner solves of the mixed-precision path: FP32-level agreement with the FP64 oracle
+    torch = need_gpu()
+    w = make()
+    sim = oracle_sim(w)
+    s = gpu_solver(w, with_sources=False, with_receivers=False)
+    x = np.random.default_rng(9).normal(size=sim.A.shape[0])
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yd = torch.zeros_like(xd)
+    torch.cuda.synchronize()
+    s.apply_operator_device(w.dt, xd.data_ptr(), yd.data_ptr(), fp32=True)
+    torch.cuda.synchronize()
+    assert rel_l2(yd.cpu().numpy().astype(np.float64), sim.A @ x) < 2e-5
