@@ -24,12 +24,14 @@ int dev_alloc(stdg_ctx* c, void** p, size_t bytes) {
     return STDG_OK;
 }
 
-static void dev_free(stdg_ctx* c, void* p) {
+void dev_release(stdg_ctx* c, void* p) {
     if (!p) return;
     auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
     if (it != c->allocs.end()) c->allocs.erase(it);
     cudaFree(p);
 }
+
+static void dev_free(stdg_ctx* c, void* p) { dev_release(c, p); }
 
 void dev_free_all(stdg_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
@@ -77,7 +79,7 @@ static int alloc_state(stdg_ctx* c, int n_shots) {
     c->n_shots = n_shots;
     c->rec_steps = 0;
     solver_invalidate_graph(c);
-    return STDG_OK;
+    return solver_setup(c);   // stacked Krylov workspace sized for n_shots
 }
 
 static int ensure_fp32(stdg_ctx* c) {
@@ -274,9 +276,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     ALLOC(c->d_lamf32, sizeof(float) * nf);
     ALLOC(c->d_muf32, sizeof(float) * nf);
     ALLOC(c->d_rhoJ32, sizeof(float) * n_elem);
-    ALLOC(c->d_b, sizeof(double) * c->nvel);
     ALLOC(c->d_sigtmp, sizeof(double) * c->nsig);
-    ALLOC(c->d_x, sizeof(double) * c->nvel);
     UP(c->d_face_l, c->hm.face_l.data(), sizeof(int32_t) * nf);
     UP(c->d_elem_face, c->hm.elem_face.data(), sizeof(int32_t) * n_elem * nv);
     UP(c->d_face_r, c->hm.face_r.data(), sizeof(int32_t) * nf);
@@ -317,7 +317,6 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
 #undef UP
     c->have_mesh = true;
     if ((rc = alloc_state(c, 1)) != STDG_OK) return rc;
-    if ((rc = solver_setup(c)) != STDG_OK) return rc;
     if (c->opt.precision != STDG_FP64 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
     STDG_CUDA(c, cudaStreamSynchronize(c->stream));
     return STDG_OK;

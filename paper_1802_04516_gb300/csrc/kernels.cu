@@ -340,8 +340,9 @@ cudaError_t launch_to_fp32(stdg_ctx* c) {
 // Operator: element mass term and face (Schur) term.
 // ---------------------------------------------------------------------------------
 // y[e][k][a][n] = rho_i |J_i| sum_b T[a][b] sum_n' Mref[n][n'] v[e][k][b][n']
+// n_elem = elements x shots of the (shot-major) vectors, n_elem_base = elements of the mesh
 template <int NP, typename R>
-__global__ void mass_kernel(int64_t n_elem, int dim, int NG, const RefTables* __restrict__ rtp,
+__global__ void mass_kernel(int64_t n_elem, int64_t n_elem_base, int dim, int NG, const RefTables* __restrict__ rtp,
                             const R* __restrict__ rhoJ, const R* __restrict__ v, const int* __restrict__ vidx,
                             int64_t ld, R* __restrict__ y) {
     if (vidx) v += (int64_t)(*vidx) * ld;
@@ -365,7 +366,7 @@ __global__ void mass_kernel(int64_t n_elem, int dim, int NG, const RefTables* __
 #pragma unroll
             for (int n = 0; n < NP; ++n) tv[n] += tab * ve[b * NP + n];
         }
-        const R s = rhoJ[e];
+        const R s = rhoJ[e % n_elem_base];
         R* ye = y + row * NP;
 #pragma unroll
         for (int n = 0; n < NP; ++n) {
@@ -437,24 +438,36 @@ __device__ __forceinline__ void face_bracket(int NG, int lane, const R* sD, cons
     __syncwarp();
 }
 
-// Load the D~ blocks and the neighbours' values of face f into the warp's smem.
+// Load the D~ blocks of face f into the warp's smem.
 template <int DIM, int NP, typename R>
-__device__ __forceinline__ void face_load(int64_t f, int NG, int lane, int el, int er, const R* __restrict__ D,
-                                          const R* __restrict__ x, R* sD, R* sv, const R* __restrict__ x2 = nullptr) {
+__device__ __forceinline__ void face_load_D(int64_t f, int lane, const R* __restrict__ D, R* sD) {
     const int nD = 2 * DIM * NP * NP;
     const R* Dg = D + f * nD;
     for (int t = lane; t < nD; t += 32) sD[t] = Dg[t];
+}
+
+// Load the neighbours' values of face f (midpoint average with x2 for Crank-Nicolson).
+template <int DIM, int NP, typename R>
+__device__ __forceinline__ void face_load_v(int NG, int lane, int el, int er, const R* __restrict__ x, R* sv,
+                                            const R* __restrict__ x2 = nullptr) {
     const int nvs = DIM * NG * NP;
     for (int t = lane; t < nvs; t += 32) {
         R a = x[(int64_t)el * nvs + t];
         R b = er >= 0 ? x[(int64_t)er * nvs + t] : (R)0;
-        if (x2) {   // Crank-Nicolson midpoint average
+        if (x2) {
             a = (R)0.5 * (a + x2[(int64_t)el * nvs + t]);
             b = er >= 0 ? (R)0.5 * (b + x2[(int64_t)er * nvs + t]) : (R)0;
         }
         sv[t] = a;
         sv[nvs + t] = b;
     }
+}
+
+template <int DIM, int NP, typename R>
+__device__ __forceinline__ void face_load(int64_t f, int NG, int lane, int el, int er, const R* __restrict__ D,
+                                          const R* __restrict__ x, R* sD, R* sv, const R* __restrict__ x2 = nullptr) {
+    face_load_D<DIM, NP, R>(f, lane, D, sD);
+    face_load_v<DIM, NP, R>(NG, lane, el, er, x, sv, x2);
     __syncwarp();
 }
 
@@ -465,7 +478,7 @@ __global__ void __launch_bounds__(128) face_apply_kernel(int64_t n_face, int NG,
                                                          const R* __restrict__ lamf,
                                                          const R* __restrict__ muf, const RefTables* __restrict__ rtp,
                                                          const R* __restrict__ x, const int* __restrict__ xidx, int64_t ld,
-                                                         R* __restrict__ y, R scale) {
+                                                         R* __restrict__ y, R scale, int nshots, int64_t nvec) {
     if (xidx) x += (int64_t)(*xidx) * ld;
     extern __shared__ unsigned char smraw[];
     R* sm = reinterpret_cast<R*>(smraw);
@@ -482,56 +495,64 @@ __global__ void __launch_bounds__(128) face_apply_kernel(int64_t n_face, int NG,
     const int nvs = DIM * ng_np;
     for (int64_t f = blockIdx.x * (int64_t)wpb + warp; f < n_face; f += (int64_t)gridDim.x * wpb) {
         const int el = fl[f], er = fr[f];
-        face_load<DIM, NP, R>(f, NG, lane, el, er, D, x, sD, sv);
-        face_bracket<DIM, NP, R>(NG, lane, sD, sv, sg, st, lamf[f], muf[f]);
-        // time factor S and scale: h = scale * S t
-        for (int ent = lane; ent < NS * ng_np; ent += 32) {
-            const int c = ent / ng_np, b = (ent / NP) % NG, m = ent % NP;
-            R acc = 0;
-            for (int b2 = 0; b2 < NG; ++b2) acc += sS[b * NG + b2] * st[(c * NG + b2) * NP + m];
-            sh[ent] = scale * acc;
-        }
-        __syncwarp();
-        const int nside = er >= 0 ? 2 : 1;
-        for (int ent = lane; ent < nside * nvs; ent += 32) {
-            const int side = ent / nvs;
-            const int r = ent % nvs;
-            const int k = r / ng_np, b = (r / NP) % NG, n = r % NP;
-            R acc = 0;
-#pragma unroll
-            for (int l = 0; l < DIM; ++l) {
-                const R* Dp = sD + ((side * DIM + l) * NP + n) * NP;
-                const R* hp = sh + (sym_c<DIM>(k, l) * NG + b) * NP;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc += Dp[m] * hp[m];
+        const R lam = lamf[f], mu = muf[f];
+        face_load_D<DIM, NP, R>(f, lane, D, sD);   // once per face, reused by every shot
+        for (int s = 0; s < nshots; ++s) {
+            const R* xs = x + (int64_t)s * nvec;
+            R* ys = y + (int64_t)s * nvec;
+            face_load_v<DIM, NP, R>(NG, lane, el, er, xs, sv);
+            __syncwarp();
+            face_bracket<DIM, NP, R>(NG, lane, sD, sv, sg, st, lam, mu);
+            // time factor S and scale: h = scale * S t
+            for (int ent = lane; ent < NS * ng_np; ent += 32) {
+                const int c = ent / ng_np, b = (ent / NP) % NG, m = ent % NP;
+                R acc = 0;
+                for (int b2 = 0; b2 < NG; ++b2) acc += sS[b * NG + b2] * st[(c * NG + b2) * NP + m];
+                sh[ent] = scale * acc;
             }
-            const int e = side == 0 ? el : er;
-            atomicAdd(&y[(int64_t)e * nvs + r], acc);
+            __syncwarp();
+            const int nside = er >= 0 ? 2 : 1;
+            for (int ent = lane; ent < nside * nvs; ent += 32) {
+                const int side = ent / nvs;
+                const int r = ent % nvs;
+                const int k = r / ng_np, b = (r / NP) % NG, n = r % NP;
+                R acc = 0;
+#pragma unroll
+                for (int l = 0; l < DIM; ++l) {
+                    const R* Dp = sD + ((side * DIM + l) * NP + n) * NP;
+                    const R* hp = sh + (sym_c<DIM>(k, l) * NG + b) * NP;
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) acc += Dp[m] * hp[m];
+                }
+                const int e = side == 0 ? el : er;
+                atomicAdd(&ys[(int64_t)e * nvs + r], acc);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
 template <int DIM, int NP, typename R>
 static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* rhoJ,
                               const R* x, R* y, double scale, bool mass, bool face = true,
-                              const int* xidx = nullptr, int64_t ld = 0) {
+                              const int* xidx = nullptr, int64_t ld = 0, int nshots = 1) {
     const int NG = c->Ng;
     if (mass) {
-        const int64_t rows = c->n_elem * c->dim * NG;
+        const int64_t rows = c->n_elem * nshots * c->dim * NG;
         mass_kernel<NP, R><<<(unsigned)std::min<int64_t>((rows + 127) / 128, 152 * 64), 128, 0, c->stream>>>(
-            c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
+            c->n_elem * nshots, c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
     }
     if (!face) return cudaGetLastError();
     cudaError_t fe;
-    if (launch_face_fast<R>(c, D, lamf, muf, x, xidx, ld, y, scale, &fe)) return fe;
+    if (launch_face_fast<R>(c, D, lamf, muf, x, xidx, ld, y, scale, &fe, nshots)) return fe;
     const FaceSmem L = face_smem(DIM, NP, NG);
     const int wpb = 4;
     size_t smem = sizeof(R) * (kMaxNG * kMaxNG + (size_t)wpb * L.total);
     cudaFuncSetAttribute(face_apply_kernel<DIM, NP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int64_t blocks = (c->n_face + wpb - 1) / wpb;
     face_apply_kernel<DIM, NP, R><<<(unsigned)std::min<int64_t>(blocks, 1 << 30), 32 * wpb, smem, c->stream>>>(
-        c->n_face, NG, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale); note_launch(c);
+        c->n_face, NG, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, nshots, c->nvel);
+    note_launch(c);
     return cudaGetLastError();
 }
 
@@ -557,15 +578,17 @@ static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* m
 
 static double schur_c(const stdg_ctx* c) { return c->opt.scheme == STDG_SCHEME_CN ? 0.25 : 1.0; }
 
-cudaError_t launch_apply(stdg_ctx* c, double dt, const double* x, double* y, double cfac, const int* xidx, int64_t ld) {
+cudaError_t launch_apply(stdg_ctx* c, double dt, const double* x, double* y, double cfac, const int* xidx, int64_t ld,
+                         int nshots) {
     const double scale = cfac * schur_c(c) * dt * dt;
-    STDG_DISPATCH(c->dim, c->Nphi, return (apply_tmpl<D_, N_, double>(c, c->d_D, c->d_lamf, c->d_muf, c->d_rhoJ, x, y, scale, true, true, xidx, ld)));
+    STDG_DISPATCH(c->dim, c->Nphi, return (apply_tmpl<D_, N_, double>(c, c->d_D, c->d_lamf, c->d_muf, c->d_rhoJ, x, y, scale, true, true, xidx, ld, nshots)));
     return cudaSuccess;
 }
 
-cudaError_t launch_apply32(stdg_ctx* c, double dt, const float* x, float* y, double cfac, const int* xidx, int64_t ld) {
+cudaError_t launch_apply32(stdg_ctx* c, double dt, const float* x, float* y, double cfac, const int* xidx, int64_t ld,
+                           int nshots) {
     const double scale = cfac * schur_c(c) * dt * dt;
-    STDG_DISPATCH(c->dim, c->Nphi, return (apply_tmpl<D_, N_, float>(c, c->d_D32, c->d_lamf32, c->d_muf32, c->d_rhoJ32, x, y, scale, true, true, xidx, ld)));
+    STDG_DISPATCH(c->dim, c->Nphi, return (apply_tmpl<D_, N_, float>(c, c->d_D32, c->d_lamf32, c->d_muf32, c->d_rhoJ32, x, y, scale, true, true, xidx, ld, nshots)));
     return cudaSuccess;
 }
 

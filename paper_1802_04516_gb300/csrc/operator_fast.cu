@@ -101,10 +101,11 @@ template <int DIM, int NP, int NG, typename R>
 __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, const int32_t* __restrict__ fl,
                                                               const int32_t* __restrict__ fr, const R* __restrict__ D,
                                                               const R* __restrict__ lamf, const R* __restrict__ muf,
-                                                              const RefTables* __restrict__ rtp, const R* __restrict__ x,
-                                                              const int* __restrict__ xidx, int64_t ld, R* __restrict__ y,
-                                                              R scale) {
+                                                              const RefTables* __restrict__ rtp, const R* __restrict__ x0,
+                                                              const int* __restrict__ xidx, int64_t ld, R* __restrict__ y0,
+                                                              R scale, int nshots, int64_t nvec) {
     using F = FaceReg<DIM, NP, NG, R>;
+    const R* x = x0;
     constexpr int NS = F::NS, NPP = F::NPP, NVS = F::NVS;
     static_assert(DIM * NP <= 32 && 2 * NP <= 32, "register-blocked face kernel needs d*N_phi <= 32");
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -137,9 +138,13 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
         for (int l = 0; l < DIM; ++l)
 #pragma unroll
             for (int m = 0; m < NP; ++m) Ds[l][m] = sc ? Df[((sc_s * DIM + l) * NP + sc_n) * NP + m] : (R)0;
+        const R lam = lamf[f], mu = muf[f];
+        // D~ stays in registers for every shot of the batch
+        for (int shot = 0; shot < nshots; ++shot) {
+        R* y = y0 + (int64_t)shot * nvec;
         // ---- neighbours' values, rows (s,k,b) padded
-        const R* xl = x + (int64_t)el * NVS;
-        const R* xr = x + (int64_t)(er >= 0 ? er : el) * NVS;
+        const R* xl = x + (int64_t)shot * nvec + (int64_t)el * NVS;
+        const R* xr = x + (int64_t)shot * nvec + (int64_t)(er >= 0 ? er : el) * NVS;
 #pragma unroll
         for (int e0 = 0; e0 < NVS; e0 += 32) {
             const int e = e0 + lane;
@@ -167,7 +172,6 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
         }
         __syncwarp();
         // ---- t = E_j : g
-        const R lam = lamf[f], mu = muf[f];
         constexpr int NT_OUT = NS * NG * NP;
 #pragma unroll
         for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
@@ -219,6 +223,7 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
             if (write) atomicAdd(&y[(int64_t)es * NVS + kb * NP + sc_n], acc);
         }
         __syncwarp();
+        }   // shots
     }
 }
 
@@ -429,11 +434,11 @@ __global__ void __launch_bounds__(128) face_apply_tma_kernel(int64_t n_face, con
 
 template <int DIM, int NP, int NG, typename R>
 static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx,
-                               int64_t ld, R* y, double scale) {
+                               int64_t ld, R* y, double scale, int nshots) {
     using T = FaceTma<DIM, NP, NG, R>;
     const bool aligned = (reinterpret_cast<uintptr_t>(D) % 16 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
                          ((ld * (int64_t)sizeof(R)) % 16 == 0);
-    if (aligned && c->d_err) {
+    if (nshots == 1 && aligned && c->d_err) {
         const int wpb = 4;
         const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
         cudaFuncSetAttribute(face_apply_tma_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -449,7 +454,7 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
     cudaFuncSetAttribute(face_apply_fast_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 1 << 30);
     face_apply_fast_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
-        c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale);
+        c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, nshots, c->nvel);
     note_launch(c);
     return cudaGetLastError();
 }
@@ -458,21 +463,21 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
 // 3D, (2,3,1) Crank-Nicolson p = 1 in 2D.  Returns false when no specialisation exists.
 template <typename R>
 bool launch_face_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx, int64_t ld, R* y,
-                      double scale, cudaError_t* err) {
+                      double scale, cudaError_t* err, int nshots) {
     const int d = c->dim, np = c->Nphi, ng = c->Ng;
     // FP64 stays on the shared-memory kernel: at 1/64 of the FP32 rate the FP64 pipe, not
     // issue, bounds it, and the register-blocked variant's occupancy is lower.
     if (sizeof(R) == 8) return false;
-    if (d == 2 && np == 10 && ng == 4) { *err = launch_fast<2, 10, 4, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
-    if (d == 2 && np == 6 && ng == 3) { *err = launch_fast<2, 6, 3, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
-    if (d == 3 && np == 10 && ng == 3) { *err = launch_fast<3, 10, 3, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
-    if (d == 2 && np == 3 && ng == 1) { *err = launch_fast<2, 3, 1, R>(c, D, lamf, muf, x, xidx, ld, y, scale); return true; }
+    if (d == 2 && np == 10 && ng == 4) { *err = launch_fast<2, 10, 4, R>(c, D, lamf, muf, x, xidx, ld, y, scale, nshots); return true; }
+    if (d == 2 && np == 6 && ng == 3) { *err = launch_fast<2, 6, 3, R>(c, D, lamf, muf, x, xidx, ld, y, scale, nshots); return true; }
+    if (d == 3 && np == 10 && ng == 3) { *err = launch_fast<3, 10, 3, R>(c, D, lamf, muf, x, xidx, ld, y, scale, nshots); return true; }
+    if (d == 2 && np == 3 && ng == 1) { *err = launch_fast<2, 3, 1, R>(c, D, lamf, muf, x, xidx, ld, y, scale, nshots); return true; }
     return false;
 }
 
 template bool launch_face_fast<float>(stdg_ctx*, const float*, const float*, const float*, const float*, const int*, int64_t,
-                                      float*, double, cudaError_t*);
+                                      float*, double, cudaError_t*, int);
 template bool launch_face_fast<double>(stdg_ctx*, const double*, const double*, const double*, const double*, const int*,
-                                       int64_t, double*, double, cudaError_t*);
+                                       int64_t, double*, double, cudaError_t*, int);
 
 }  // namespace stdg

@@ -227,8 +227,10 @@ __global__ void pre1_time_kernel(int64_t nq, int NG, const RefTables* __restrict
 // element; V staged in shared memory with a padded row stride.
 template <typename R>
 __global__ void __launch_bounds__(128) pre1_apply_kernel(int64_t n_elem, int dim, int NP, int NG, const R* __restrict__ V,
-                                                         const R* __restrict__ B, const R* __restrict__ r,
-                                                         const int* __restrict__ ridx, int64_t ld_vec, R* __restrict__ z) {
+                                                         const R* __restrict__ B, const R* __restrict__ r0,
+                                                         const int* __restrict__ ridx, int64_t ld_vec, R* __restrict__ z0,
+                                                         int nshots, int64_t nvec) {
+    const R* r = r0;
     extern __shared__ unsigned char smraw[];
     R* sm = reinterpret_cast<R*>(smraw);
     if (ridx) r += (int64_t)(*ridx) * ld_vec;
@@ -242,7 +244,9 @@ __global__ void __launch_bounds__(128) pre1_apply_kernel(int64_t n_elem, int dim
     for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
         const R* Vg = V + e * (int64_t)n * n;
         for (int t = lane; t < n * n; t += 32) sV[(t / n) * ldv + t % n] = Vg[t];
-        const R* re = r + e * (int64_t)n * NG;
+        for (int shot = 0; shot < nshots; ++shot) {
+        const R* re = r + (int64_t)shot * nvec + e * (int64_t)n * NG;
+        R* z = z0 + (int64_t)shot * nvec;
         for (int t = lane; t < n * NG; t += 32) {
             const int k = t / (NG * NP), a = (t / NP) % NG, nn = t % NP;
             sr[(k * NP + nn) * NG + a] = re[t];
@@ -275,6 +279,7 @@ __global__ void __launch_bounds__(128) pre1_apply_kernel(int64_t n_elem, int dim
             for (int a = 0; a < NG; ++a) ze[(k * NG + a) * NP + nn] = acc[a];
         }
         __syncwarp();
+        }   // shots
     }
 }
 
@@ -283,8 +288,9 @@ __global__ void __launch_bounds__(128) pre1_apply_kernel(int64_t n_elem, int dim
 // memory by all lanes at once (broadcast), so the inner loops are FMAs.
 template <int DIM, int NP, int NG, typename R>
 __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, const R* __restrict__ V, const R* __restrict__ B,
-                                                             const R* __restrict__ r, const int* __restrict__ ridx,
-                                                             int64_t ld_vec, R* __restrict__ z) {
+                                                             const R* __restrict__ r0, const int* __restrict__ ridx,
+                                                             int64_t ld_vec, R* __restrict__ z0, int nshots, int64_t nvec) {
+    const R* r = r0;
     constexpr int N = DIM * NP;
     static_assert(N <= 32, "register-blocked block-Jacobi apply needs d*N_phi <= 32");
     __shared__ R s_r[4][N * NG], s_w[4][N * NG];
@@ -296,7 +302,16 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
     const int q = act ? lane : 0;
     for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
         const R* Ve = V + e * (int64_t)(N * N);
-        const R* re = r + e * (int64_t)(N * NG);
+        R Vc[N], Vr[N], Bq[NG * NG];
+#pragma unroll
+        for (int row = 0; row < N; ++row) Vc[row] = act ? Ve[row * N + q] : (R)0;
+#pragma unroll
+        for (int qq = 0; qq < N; ++qq) Vr[qq] = act ? Ve[q * N + qq] : (R)0;
+#pragma unroll
+        for (int t = 0; t < NG * NG; ++t) Bq[t] = act ? B[(e * N + q) * (int64_t)(NG * NG) + t] : (R)0;
+        for (int shot = 0; shot < nshots; ++shot) {   // V and B stay in registers for every shot
+        const R* re = r + (int64_t)shot * nvec + e * (int64_t)(N * NG);
+        R* z = z0 + (int64_t)shot * nvec;
         // r rows (k,n) with the NG time values contiguous
 #pragma unroll
         for (int t0 = 0; t0 < N * NG; t0 += 32) {
@@ -306,9 +321,6 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
                 sr[(k * NP + n) * NG + a] = re[t];
             }
         }
-        R Vc[N];
-#pragma unroll
-        for (int row = 0; row < N; ++row) Vc[row] = act ? Ve[row * N + q] : (R)0;
         __syncwarp();
         // u[q][a] = sum_row V[row][q] r[row][a];  w[q] = B_q u[q]
         R u[NG];
@@ -319,7 +331,6 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
 #pragma unroll
             for (int a = 0; a < NG; ++a) u[a] = fma(Vc[row], sr[row * NG + a], u[a]);
         if (act) {
-            const R* Bq = B + (e * N + q) * (int64_t)(NG * NG);
 #pragma unroll
             for (int a = 0; a < NG; ++a) {
                 R s = 0;
@@ -328,9 +339,6 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
                 sw[q * NG + a] = s;
             }
         }
-        R Vr[N];
-#pragma unroll
-        for (int qq = 0; qq < N; ++qq) Vr[qq] = act ? Ve[q * N + qq] : (R)0;
         __syncwarp();
         // z[row][a] = sum_q V[row][q] w[q][a], row = lane
         R acc[NG];
@@ -347,17 +355,18 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
             for (int a = 0; a < NG; ++a) ze[(k * NG + a) * NP + n] = acc[a];
         }
         __syncwarp();
+        }   // shots
     }
 }
 
 template <typename R>
 static bool pre1_apply_fast(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld,
-                            cudaError_t* err) {
+                            cudaError_t* err, int nshots) {
     const int64_t blocks = std::min<int64_t>((c->n_elem + 3) / 4, 1 << 30);
     const int d = c->dim, np = c->Nphi, ng = c->Ng;
 #define STDG_PRE_FAST(D_, NP_, NG_)                                                                        \
     if (d == D_ && np == NP_ && ng == NG_) {                                                              \
-        pre1_apply_reg_kernel<D_, NP_, NG_, R><<<(unsigned)blocks, 128, 0, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z); \
+        pre1_apply_reg_kernel<D_, NP_, NG_, R><<<(unsigned)blocks, 128, 0, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z, nshots, c->nvel); \
         note_launch(c);                                                                                    \
         *err = cudaGetLastError();                                                                         \
         return true;                                                                                       \
@@ -396,24 +405,26 @@ cudaError_t launch_pre1_time(stdg_ctx* c, double dt) {
 }
 
 template <typename R>
-static cudaError_t pre1_apply_t(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld) {
+static cudaError_t pre1_apply_t(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld,
+                                int nshots) {
     cudaError_t fe;
-    if (pre1_apply_fast<R>(c, V, B, r, z, ridx, ld, &fe)) return fe;
+    if (pre1_apply_fast<R>(c, V, B, r, z, ridx, ld, &fe, nshots)) return fe;
     const int n = c->dim * c->Nphi;
     const int wpb = 4;
     const size_t smem = sizeof(R) * (size_t)wpb * (n * (n + 1) + 2 * n * c->Ng);
     cudaFuncSetAttribute(pre1_apply_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
-    pre1_apply_kernel<R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_elem, c->dim, c->Nphi, c->Ng, V, B, r, ridx, ld, z); note_launch(c);
+    pre1_apply_kernel<R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_elem, c->dim, c->Nphi, c->Ng, V, B, r, ridx, ld, z,
+                                                                          nshots, c->nvel); note_launch(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld) {
-    return pre1_apply_t<double>(c, c->d_preV, c->d_preB, r, z, ridx, ld);
+cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots) {
+    return pre1_apply_t<double>(c, c->d_preV, c->d_preB, r, z, ridx, ld, nshots);
 }
 
-cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld) {
-    return pre1_apply_t<float>(c, c->d_preV32, c->d_preB32, r, z, ridx, ld);
+cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots) {
+    return pre1_apply_t<float>(c, c->d_preV32, c->d_preB32, r, z, ridx, ld, nshots);
 }
 
 }  // namespace stdg

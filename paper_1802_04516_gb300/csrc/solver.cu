@@ -31,6 +31,7 @@ constexpr int kDotChunk = 16;       // basis vectors per pass of the multi-dot k
 struct DevScalars {
     // current Krylov level
     double bnorm, tol_abs;
+    double bmin;          // min over shots of ||b_shot|| (stacked multi-shot solves)
     double rr, pq, alpha, beta;                   // CG
     double gbeta, resid;                          // GMRES
     double hcol[kMaxRestart + 2], hpass[kMaxRestart + 2];
@@ -60,6 +61,7 @@ struct Workspace {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double graph_dt = -1.0;
+    std::vector<void*> owned;   // device buffers of this workspace
 };
 
 static Workspace* W(stdg_ctx* c) { return reinterpret_cast<Workspace*>(c->ws); }
@@ -149,6 +151,30 @@ __global__ void dot_partial_kernel(int64_t n, const A* __restrict__ a, const B* 
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
+// per-shot partial sums of ||b_s||^2: grid (G, nshots), part[s * G + blk]
+__global__ void shot_norm_partial_kernel(int64_t nvec, const double* __restrict__ b, double* __restrict__ part) {
+    const double* bs = b + (int64_t)blockIdx.y * nvec;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(bs[i], bs[i], acc);
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// sc->bmin = min_s ||b_s||: a stacked solve stopped at ||r|| <= tol * bmin meets tol for every shot
+__global__ void shot_min_kernel(DevScalars* sc, const double* part, int G, int nshots) {
+    double mn = 0.0;
+    for (int s = 0; s < nshots; ++s) {
+        double t = sum_partials(part + s * G, G);
+        if (threadIdx.x == 0) {
+            const double nrm = sqrt(t);
+            mn = (s == 0 || nrm < mn) ? nrm : mn;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sc->bmin = mn;
+}
+
 __global__ void zero_if_kernel(int64_t n, double* x, const int* flag) {
     if (!*flag) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = 0;
@@ -175,7 +201,8 @@ __global__ void cg_res_kernel(int64_t n, const R* __restrict__ b, const R* __res
 
 // bnorm_given < 0: use ||b|| from the partials; partials: [0] rr, [1] bb, [2] rz
 __global__ void cg_init_final_kernel(DevScalars* sc, const double* part, double rel_tol, int max_iters,
-                                     double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h) {
+                                     double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h,
+                                     int use_bmin) {
     double rr = sum_partials(part, kRedBlocks);
     double bb = sum_partials(part + kRedBlocks, kRedBlocks);
     double rz = sum_partials(part + 2 * kRedBlocks, kRedBlocks);
@@ -184,7 +211,7 @@ __global__ void cg_init_final_kernel(DevScalars* sc, const double* part, double 
         sc->rr = rr;
         sc->pq = rz;                       // holds r.z between iterations
         sc->bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(bb);
-        sc->tol_abs = rel_tol * sc->bnorm;
+        sc->tol_abs = rel_tol * (use_bmin ? sc->bmin : sc->bnorm);
         sc->iters = 0;
         sc->max_iters = max_iters;
         sc->zero_x = active && sc->bnorm == 0.0;
@@ -266,12 +293,12 @@ __global__ void gm_res_kernel(int64_t n, const R* __restrict__ b, const R* __res
 
 // set up one GMRES solve: ||b|| (from partials, or given), tolerance, counters
 __global__ void gm_init_kernel(DevScalars* sc, const double* part, double rel_tol, int max_iters, int m,
-                               double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h) {
+                               double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h, int use_bmin) {
     double bb = sum_partials(part, kRedBlocks);
     if (threadIdx.x == 0) {
         const int active = gate_ir ? sc->ir_flag : 1;
         sc->bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(bb);
-        sc->tol_abs = rel_tol * sc->bnorm;
+        sc->tol_abs = rel_tol * (use_bmin ? sc->bmin : sc->bnorm);
         sc->iters = 0;
         sc->max_iters = max_iters;
         sc->m = m;
@@ -611,11 +638,11 @@ __global__ void gm_cycle_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h
 // FP64 iterative refinement around the FP32 solver
 // ---------------------------------------------------------------------------------
 __global__ void ir_init_kernel(DevScalars* sc, const double* part, double rel_tol, int ir_max,
-                               cudaGraphConditionalHandle h, int use_h) {
+                               cudaGraphConditionalHandle h, int use_h, int use_bmin) {
     double bb = sum_partials(part, kRedBlocks);
     if (threadIdx.x == 0) {
         sc->ir_bnorm = sqrt(bb);
-        sc->ir_tol_abs = rel_tol * sc->ir_bnorm;
+        sc->ir_tol_abs = rel_tol * (use_bmin ? sc->bmin : sc->ir_bnorm);
         sc->ir_count = 0;
         sc->ir_max = ir_max;
         sc->ir_flag = 1;
@@ -667,20 +694,22 @@ __global__ void ir_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int 
 }
 
 // per-solve statistics; mode 0 = GMRES, 1 = CG, 2 = mixed (refinement level)
-__global__ void solve_stats_kernel(DevScalars* sc, int mode) {
+__global__ void solve_stats_kernel(DevScalars* sc, int mode, int use_bmin) {
     if (threadIdx.x != 0) return;
     int it;
     double rel;
     if (mode == 2) {
         it = sc->st_total;          // accumulated by ir_end over the refinement sweeps
         sc->st_total = 0;
-        rel = sc->ir_bnorm > 0 ? sc->ir_rnorm / sc->ir_bnorm : 0.0;
+        const double bn = use_bmin ? sc->bmin : sc->ir_bnorm;
+        rel = bn > 0 ? sc->ir_rnorm / bn : 0.0;
         sc->st_refine += sc->ir_count;
         if (!sc->ir_conv) sc->st_notconv = 1;
     } else {
         it = sc->iters;
         const double r = mode == 1 ? sqrt(sc->rr) : sc->resid;
-        rel = sc->bnorm > 0 ? r / sc->bnorm : 0.0;
+        const double bn = use_bmin ? sc->bmin : sc->bnorm;
+        rel = bn > 0 ? r / bn : 0.0;
         if (!sc->converged) sc->st_notconv = 1;
     }
     sc->st_final_rel = rel;
@@ -772,7 +801,7 @@ static unsigned vec_blocks(int64_t n) { return (unsigned)std::min<int64_t>((n + 
 // ---- (P)CG on vectors of type R; apply(x, y): y = A x; prec(r, z): z = P^{-1} r or null --------
 template <typename R, class Apply, class Prec>
 static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b, R* x, R* r, R* p, R* q, R* z,
-                     double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
+                     double rel_tol, int max_iters, double bnorm_given, int gate_ir, int use_bmin) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
     const int64_t n = ws->n;
@@ -784,7 +813,7 @@ static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b,
                if (use_prec) F.check(prec(r, zz));
                dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, r, zz, ws->partials + 2 * kRedBlocks); note_launch(c);
                cg_init_final_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, rel_tol, max_iters, bnorm_given,
-                                                                      gate_ir, h, use); note_launch(c);
+                                                                      gate_ir, h, use, use_bmin); note_launch(c);
                copy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, zz, p); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
@@ -803,7 +832,7 @@ static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b,
 // ---- GMRES(m) on vectors of type R -----------------------------------------------------
 template <typename R, class Apply, class ApplyIdx, class Prec>
 static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, bool use_prec, const R* b, R* x, R* V, R* w,
-                        R* zbuf, R* tbuf, double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
+                        R* zbuf, R* tbuf, double rel_tol, int max_iters, double bnorm_given, int gate_ir, int use_bmin) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
     const int64_t n = ws->n, ldv = ws->ldv;
@@ -812,7 +841,8 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
     F.loop(&sc->flag_outer,
            [&](cudaGraphConditionalHandle h, int use) {
                dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials); note_launch(c);
-               gm_init_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, rel_tol, max_iters, m, bnorm_given, gate_ir, h, use); note_launch(c);
+               gm_init_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, rel_tol, max_iters, m, bnorm_given, gate_ir, h, use,
+                                                                use_bmin); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h_outer, int use_outer) {
                // restart cycle: true residual, then Arnoldi
@@ -858,32 +888,39 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
 static void record_solve(Flow& F, double dt, double* b, double* x) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
-    const int64_t n = ws->n;
+    const int64_t n = ws->n;                 // stacked length: n_shots x velocity values
+    const int ns = c->n_shots;
+    const int bm = ns > 1 ? 1 : 0;            // stacked solves stop on min-shot norms
     const bool cn = c->opt.scheme == STDG_SCHEME_CN;
     const bool pre = c->opt.preconditioner != 0;
-    auto A64 = [&](const double* xx, double* yy) { return launch_apply(c, dt, xx, yy, 1.0); };
     const int64_t ldv = ws->ldv;
-    auto A64i = [&](const double* V, const int* idx, double* yy) { return launch_apply(c, dt, V, yy, 1.0, idx, ldv); };
-    auto A32 = [&](const float* xx, float* yy) { return launch_apply32(c, dt, xx, yy, 1.0); };
-    auto A32i = [&](const float* V, const int* idx, float* yy) { return launch_apply32(c, dt, V, yy, 1.0, idx, ldv); };
-    auto P64 = [&](const double* r, double* z, const int* idx, int64_t ld) { return launch_pre1_apply(c, r, z, idx, ld); };
-    auto P32 = [&](const float* r, float* z, const int* idx, int64_t ld) { return launch_pre1_apply32(c, r, z, idx, ld); };
-    auto P64c = [&](const double* r, double* z) { return launch_pre1_apply(c, r, z, nullptr, 0); };
-    auto P32c = [&](const float* r, float* z) { return launch_pre1_apply32(c, r, z, nullptr, 0); };
+    auto A64 = [&](const double* xx, double* yy) { return launch_apply(c, dt, xx, yy, 1.0, nullptr, 0, ns); };
+    auto A64i = [&](const double* V, const int* idx, double* yy) { return launch_apply(c, dt, V, yy, 1.0, idx, ldv, ns); };
+    auto A32 = [&](const float* xx, float* yy) { return launch_apply32(c, dt, xx, yy, 1.0, nullptr, 0, ns); };
+    auto A32i = [&](const float* V, const int* idx, float* yy) { return launch_apply32(c, dt, V, yy, 1.0, idx, ldv, ns); };
+    auto P64 = [&](const double* r, double* z, const int* idx, int64_t ld) { return launch_pre1_apply(c, r, z, idx, ld, ns); };
+    auto P32 = [&](const float* r, float* z, const int* idx, int64_t ld) { return launch_pre1_apply32(c, r, z, idx, ld, ns); };
+    auto P64c = [&](const double* r, double* z) { return launch_pre1_apply(c, r, z, nullptr, 0, ns); };
+    auto P32c = [&](const float* r, float* z) { return launch_pre1_apply32(c, r, z, nullptr, 0, ns); };
     const double tol = c->opt.rel_tol;
     const int maxit = c->opt.max_iters;
+    if (bm) {   // min over shots of ||b_s||
+        const int G = (int)std::min<int64_t>(kRedBlocks, (int64_t)(kMaxRestart + 2) * kRedBlocks / ns);
+        shot_norm_partial_kernel<<<dim3(G, ns), kRedThreads, 0, c->stream>>>(c->nvel, b, ws->partials); note_launch(c);
+        shot_min_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, G, ns); note_launch(c);
+    }
     if (c->opt.precision == STDG_FP64) {
-        if (cn) solve_cg<double>(F, A64, P64c, pre, b, x, ws->r, ws->p, ws->q, ws->z, tol, maxit, -1.0, 0);
-        else solve_gmres<double>(F, A64, A64i, P64, pre, b, x, ws->V, ws->w, ws->z, ws->t, tol, maxit, -1.0, 0);
+        if (cn) solve_cg<double>(F, A64, P64c, pre, b, x, ws->r, ws->p, ws->q, ws->z, tol, maxit, -1.0, 0, bm);
+        else solve_gmres<double>(F, A64, A64i, P64, pre, b, x, ws->V, ws->w, ws->z, ws->t, tol, maxit, -1.0, 0, bm);
         zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x); note_launch(c);
-        solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, cn ? 1 : 0); note_launch(c);
+        solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, cn ? 1 : 0, bm); note_launch(c);
         return;
     }
     // mixed: FP64 refinement, FP32 inner solve with zero initial guess and unit RHS
     F.loop(&ws->sc->ir_flag,
            [&](cudaGraphConditionalHandle h, int use) {
                dot_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials); note_launch(c);
-               ir_init_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, tol, 64, h, use); note_launch(c);
+               ir_init_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, tol, 64, h, use, bm); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(A64(x, ws->w));
@@ -892,29 +929,34 @@ static void record_solve(Flow& F, double dt, double* b, double* x) {
                ir_convert_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->r, ws->b32, ws->x32); note_launch(c);
                if (cn)
                    solve_cg<float>(F, A32, P32c, pre, ws->b32, ws->x32, ws->r32, ws->p32, ws->q32, ws->z32, c->opt.inner_tol,
-                                   maxit, 1.0, 1);
+                                   maxit, 1.0, 1, 0);
                else
                    solve_gmres<float>(F, A32, A32i, P32, pre, ws->b32, ws->x32, ws->V32, ws->w32, ws->z32, ws->t32,
-                                      c->opt.inner_tol, maxit, 1.0, 1);
+                                      c->opt.inner_tol, maxit, 1.0, 1, 0);
                ir_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->x32, x); note_launch(c);
                ir_end_kernel<<<1, 32, 0, c->stream>>>(ws->sc, h, use); note_launch(c);
                F.check(cudaGetLastError());
            });
     zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x); note_launch(c);
-    solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, 2); note_launch(c);
+    solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, 2, bm); note_launch(c);
 }
 
+// One slab for every shot: per-shot right-hand sides and initial guesses, ONE stacked
+// (block-diagonal) solve whose operator and preconditioner kernels load each face's and
+// element's blocks once for all shots, then per-shot stress, traces and receivers.
 static void record_step(Flow& F, double dt) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
     c->scopes.assign(1, 0);
     step_begin_kernel<<<1, 32, 0, c->stream>>>(ws->dparams, dt); note_launch(c);
     for (int shot = 0; shot < c->n_shots && F.err == cudaSuccess; ++shot) {
-        F.check(launch_rhs(c, dt, ws->dparams, shot, c->d_b));
-        F.check(launch_initial_guess(c, shot, c->d_x));
-        record_solve(F, dt, c->d_b, c->d_x);
-        F.check(launch_stress_update(c, dt, shot, c->d_x));
-        F.check(launch_traces(c, shot, c->d_x));
+        F.check(launch_rhs(c, dt, ws->dparams, shot, c->d_b + (int64_t)shot * c->nvel));
+        F.check(launch_initial_guess(c, shot, c->d_x + (int64_t)shot * c->nvel));
+    }
+    record_solve(F, dt, c->d_b, c->d_x);
+    for (int shot = 0; shot < c->n_shots && F.err == cudaSuccess; ++shot) {
+        F.check(launch_stress_update(c, dt, shot, c->d_x + (int64_t)shot * c->nvel));
+        F.check(launch_traces(c, shot, c->d_x + (int64_t)shot * c->nvel));
         F.check(launch_receivers(c, ws->dparams, shot));
     }
     step_end_kernel<<<1, 32, 0, c->stream>>>(ws->dparams, dt); note_launch(c);
@@ -929,20 +971,23 @@ int solver_setup(stdg_ctx* c) {
     Workspace* ws = new Workspace();
     c->ws = ws;
     ws->m = std::max(2, std::min(c->opt.gmres_restart > 0 ? c->opt.gmres_restart : 30, kMaxRestart));
-    ws->n = c->nvel;
+    ws->n = c->nvel * (int64_t)c->n_shots;
     const int64_t n = ws->n;
     const bool cn = c->opt.scheme == STDG_SCHEME_CN;
     const bool mixed = c->opt.precision != STDG_FP64;
+    const bool pre = c->opt.preconditioner != 0;
     int rc;
-#define ALLOC(ptr, bytes) do { if ((rc = dev_alloc(c, (void**)&(ptr), (bytes))) != STDG_OK) return rc; } while (0)
+#define ALLOC(ptr, bytes) do { if ((rc = dev_alloc(c, (void**)&(ptr), (bytes))) != STDG_OK) return rc; \
+                               ws->owned.push_back((void*)(ptr)); } while (0)
     ALLOC(ws->sc, sizeof(DevScalars));
     ALLOC(ws->partials, sizeof(double) * (kMaxRestart + 2) * kRedBlocks);
     ALLOC(ws->dparams, sizeof(double) * 4);
+    ALLOC(c->d_b, sizeof(double) * n);
+    ALLOC(c->d_x, sizeof(double) * n);
     ALLOC(ws->w, sizeof(double) * n);
     ALLOC(ws->r, sizeof(double) * n);
-    const bool pre = c->opt.preconditioner != 0;
-    if (cn && !mixed) { ALLOC(ws->p, sizeof(double) * n); ALLOC(ws->q, sizeof(double) * n); }
     ws->ldv = (n + 63) / 64 * 64;   // 16-byte aligned basis columns for vector loads
+    if (cn && !mixed) { ALLOC(ws->p, sizeof(double) * n); ALLOC(ws->q, sizeof(double) * n); }
     if (!cn && !mixed) ALLOC(ws->V, sizeof(double) * ws->ldv * (ws->m + 1));
     if (pre && !mixed) { ALLOC(ws->z, sizeof(double) * n); if (!cn) ALLOC(ws->t, sizeof(double) * n); }
     if (mixed) {
@@ -965,8 +1010,11 @@ void solver_free(stdg_ctx* c) {
     if (ws->exec) cudaGraphExecDestroy(ws->exec);
     if (ws->graph) cudaGraphDestroy(ws->graph);
     for (auto& s : ws->side) if (s) cudaStreamDestroy(s);
+    cudaStreamSynchronize(c->stream);
+    for (void* p : ws->owned) dev_release(c, p);
+    c->d_b = c->d_x = nullptr;
     delete ws;
-    c->ws = nullptr;   // device buffers are released with the context's other allocations
+    c->ws = nullptr;
 }
 
 void solver_invalidate_graph(stdg_ctx* c) {

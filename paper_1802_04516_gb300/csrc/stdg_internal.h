@@ -157,6 +157,7 @@ inline void note_launch(stdg_ctx* c, long k = 1) {
 
 namespace stdg {
 int dev_alloc(stdg_ctx* c, void** p, size_t bytes);
+void dev_release(stdg_ctx* c, void* p);   // frees one allocation made by dev_alloc
 void dev_free_all(stdg_ctx* c);
 
 // kernels.cu -- launchers (all on c->stream); return cudaGetLastError()
@@ -166,10 +167,11 @@ cudaError_t launch_sig_convert(stdg_ctx* c, const double* in, double* out, int d
 cudaError_t launch_to_fp32(stdg_ctx* c);
 // y = A x (cfac scales the Schur part; 1 for the operator).  With xidx != null the input is
 // x + (*xidx) * ld, the index read on the device (Krylov basis column j).
+// nshots > 1: x and y hold nshots consecutive (shot-major) velocity vectors of c->nvel values.
 cudaError_t launch_apply(stdg_ctx* c, double dt, const double* x, double* y, double cfac,
-                         const int* xidx = nullptr, int64_t ld = 0);
+                         const int* xidx = nullptr, int64_t ld = 0, int nshots = 1);
 cudaError_t launch_apply32(stdg_ctx* c, double dt, const float* x, float* y, double cfac,
-                           const int* xidx = nullptr, int64_t ld = 0);
+                           const int* xidx = nullptr, int64_t ld = 0, int nshots = 1);
 cudaError_t launch_face_only(stdg_ctx* c, double dt, const void* x, void* y, double cfac, int fp32);
 cudaError_t launch_rhs(stdg_ctx* c, double dt, const double* dparams, int shot, double* b);
 cudaError_t launch_stress_update(stdg_ctx* c, double dt, int shot, const double* x);
@@ -183,13 +185,13 @@ cudaError_t launch_initial_guess(stdg_ctx* c, int shot, double* x);
 // operator_fast.cu: compile-time-shape face kernel; false if the shape is not specialised
 template <typename R>
 bool launch_face_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx, int64_t ld, R* y,
-                      double scale, cudaError_t* err);
+                      double scale, cudaError_t* err, int nshots = 1);
 
 // precond.cu
 cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* d_elem_face, int* d_status);
 cudaError_t launch_pre1_time(stdg_ctx* c, double dt);
-cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld);
-cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld);
+cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
+cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots = 1);
 
 // solver.cu
 int solver_setup(stdg_ctx* c);

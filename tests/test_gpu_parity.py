@@ -212,3 +212,24 @@ def test_fp32_operator_matches_oracle(name, make):
     s.apply_operator_device(w.dt, xd.data_ptr(), yd.data_ptr(), fp32=True)
     torch.cuda.synchronize()
     assert rel_l2(yd.cpu().numpy().astype(np.float64), sim.A @ x) < 2e-5
+
+
+@pytest.mark.parametrize("precision,tol,rel_tol", [("fp64", 1e-10, 1e-13), ("mixed", 1e-8, 1e-12)])
+def test_multishot_batch_matches_oracle_per_shot(precision, tol, rel_tol):
+    # all shots of a slab are solved as one stacked system; each shot against its own oracle run
+    need_gpu()
+    w = synth.scaled("c4", ny=8, steps=3, n_shots=3)
+    s = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000)
+    st = s.step(w.dt, 3)
+    assert st["status"] == 0
+    rec = s.read_receivers()
+    assert rec.shape[:2] == (3, 3)
+    for k in range(3):
+        sim = oracle_sim(w)
+        sim.set_source(w.shots_xs[k], w.shots_dir[k], w.f0, w.t_delay, w.a1)
+        sim.set_receivers(w.receivers)
+        sim.step(3)
+        v, sig = s.get_state(k)
+        assert rel_l2(v, sim.v_tr) < tol, (k, rel_l2(v, sim.v_tr))
+        assert stress_field_rel(sig, sim.sig_tr, sim.disc) < tol
+        assert rel_l2(rec[k], np.array(sim.records)) < 10 * tol
