@@ -109,8 +109,12 @@ def build_solver(w, precision, stream, shot_offset=0.0, restart=10, inner_tol=1e
                inner_tol=inner_tol, use_graph=use_graph, stream=stream, preconditioner=1)
     s.set_mesh(w.xyz, w.elem_vert, w.period)
     s.set_material(w.lam, w.mu, w.rho)
-    xs = np.array(w.shots_xs) + np.array([shot_offset, 0.0])
-    s.set_sources(xs, w.shots_dir, w.f0, w.t_delay, w.a1)
+    if w.shots_xs is not None:
+        xs = np.array(w.shots_xs) + np.array([shot_offset, 0.0])
+        s.set_sources(xs, w.shots_dir, w.f0, w.t_delay, w.a1)
+    else:                                   # ragged union: one point source per mesh part, one shot
+        xs = w.extra["part_sources"]
+        s.set_point_sources(xs, np.tile([0.0, 1.0], (xs.shape[0], 1)), w.f0, w.t_delay, w.a1)
     s.set_receivers(w.receivers)
     return s
 
@@ -193,6 +197,54 @@ def face_kernel_roofline(s, w, fp32, n_face, pk):
             "peak_source": "nominal FP64 1.25 TFLOP/s"}
 
 
+def multishot_section(torch, args, stream, dist, world):
+    """The 64-shot batch on the layered sliver mesh at p = 2: all shots of a slab as one
+    stacked mixed-precision solve, against the plain FP64 path run one shot at a time on
+    the same mesh.  Both at 1e-8 relative residual; shot-steps/s and DOF-steps/s."""
+    import synth
+    w = synth.c4_multishot(ny=args.ny, n_shots=args.shots, steps=args.ms_steps)
+    s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
+                     use_graph=not args.host_loop)
+    n_face = s.n_face
+    ms, iters, launches, st = time_steps(torch, s, w, args.ms_steps, 1, stream, dist)
+    s.close()
+    dofs_shot = dofs_per_slab(w, n_face)
+    w1 = synth.c4_multishot(ny=args.ny, n_shots=1, steps=args.ms_steps)
+    w1.shots_xs, w1.shots_dir = w.shots_xs[:1], w.shots_dir[:1]
+    s1 = build_solver(w1, "fp64", stream.cuda_stream, restart=args.restart, use_graph=not args.host_loop)
+    ms1, it1, _, _ = time_steps(torch, s1, w1, args.ms_steps, 1, stream, dist)
+    s1.close()
+    multi = world * w.n_shots * args.ms_steps / (ms * 1e-3)
+    single = world * args.ms_steps / (ms1 * 1e-3)
+    return {"workload": "c4_multishot: %d triangles (layered, 1%% slivers), p=p_gamma=2, %d Ricker shots on a line, "
+                        "dt=%.4g (10x CFL)" % (w.n_elem, w.n_shots, w.dt),
+            "mixed_multishot": {"shot_steps_per_s": multi, "dof_steps_per_s": multi * dofs_shot,
+                                "ms_per_step": ms / args.ms_steps, "krylov_iters_per_step": iters,
+                                "final_rel_res": st["final_rel_res"], "gpu_launches": launches},
+            "fp64_single_shot": {"shot_steps_per_s": single, "dof_steps_per_s": single * dofs_shot,
+                                 "ms_per_step": ms1 / args.ms_steps, "krylov_iters_per_step": it1},
+            "speedup_shot_steps": multi / single, "dofs_per_slab_per_shot": dofs_shot, "steps": args.ms_steps}
+
+
+def ragged_section(torch, args, stream, dist, world):
+    """The ragged batch: 16 meshes of ~5k to ~80k triangles side by side as one disconnected
+    mesh, one source per part, advanced by one mixed-precision solve per slab."""
+    import synth
+    w, spans = synth.ragged_union(steps=args.ms_steps)
+    s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
+                     use_graph=not args.host_loop)
+    n_face = s.n_face
+    ms, iters, launches, st = time_steps(torch, s, w, args.ms_steps, 1, stream, dist)
+    s.close()
+    dofs = dofs_per_slab(w, n_face)
+    return {"workload": "c4_ragged: %d meshes of %d..%d triangles (%d total), p=p_gamma=2, dt=%.4g"
+                        % (len(spans), min(n for _, n in spans), max(n for _, n in spans), w.n_elem, w.dt),
+            "dof_steps_per_s": world * dofs * args.ms_steps / (ms * 1e-3),
+            "mesh_steps_per_s": world * len(spans) * args.ms_steps / (ms * 1e-3),
+            "ms_per_step": ms / args.ms_steps, "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"],
+            "gpu_launches": launches, "steps": args.ms_steps}
+
+
 def cpu_baseline(max_seconds=25.0, ny=12, steps=20):
     """The oracle as it stands (assembly + SuperLU, one core) on a bounded sample of the
     same construction: ny x 2ny cells, steps slabs; DOF-steps/s over the solve phase."""
@@ -243,6 +295,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--restart", type=int, default=10, help="GMRES restart length")
     ap.add_argument("--inner-tol", type=float, default=1e-2, help="relative tolerance of the FP32 inner solve")
+    ap.add_argument("--shots", type=int, default=64, help="shots of the multi-shot batch")
+    ap.add_argument("--ms-steps", type=int, default=2, help="timed slabs of the multi-shot and ragged batches")
+    ap.add_argument("--no-multishot", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solver loops from the host instead of CUDA-graph while nodes (for kernel profilers)")
     args = ap.parse_args()
@@ -289,6 +345,9 @@ def main():
             fp64 = {"value": world * dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
                     "krylov_iters_per_step": it64, "roofline": face_kernel_roofline(s64, w, False, n_face, pk)}
             s64.close()
+        s.close()
+        multishot = None if args.no_multishot else multishot_section(torch, args, stream, dist, world)
+        ragged = None if args.no_ragged else ragged_section(torch, args, stream, dist, world)
     if rank != 0:
         return
     cb = None if args.no_cpu_baseline else cpu_baseline()
@@ -309,6 +368,8 @@ def main():
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "DOF-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "fp64": fp64,
+        "multishot": multishot,
+        "ragged": ragged,
         "cpu_baseline": cb,
     }
     print(json.dumps(line))

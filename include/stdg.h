@@ -114,6 +114,13 @@ int stdg_set_plane_wave(stdg_ctx* ctx, int shot, int kind, const double* n, cons
 int stdg_set_sources(stdg_ctx* ctx, int n_shots, const double* xs, const double* dir,
                      double f0, double t_delay, double a1);
 
+/* Several point sources per shot (same Ricker wavelet): shot k has the sources
+ * xs[k*per_shot + q], dir[k*per_shot + q], q < per_shot.  stdg_set_sources is the case
+ * per_shot = 1.  A disconnected mesh with one source per part advances independent
+ * problems (a ragged batch) in one shot.  Sets n_shots (resets states). */
+int stdg_set_point_sources(stdg_ctx* ctx, int n_shots, int per_shot, const double* xs, const double* dir,
+                           double f0, double t_delay, double a1);
+
 /* Receivers: velocity v_h(x_r, t^{n+1,-}) is recorded after every step. */
 int stdg_set_receivers(stdg_ctx* ctx, int n_rec, const double* xr);
 

@@ -47,6 +47,7 @@ SIGNATURES = {
     "stdg_get_state": (C.c_int, [_P, C.c_int, _D, _D]),
     "stdg_set_plane_wave": (C.c_int, [_P, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double]),
     "stdg_set_sources": (C.c_int, [_P, C.c_int, _D, _D, C.c_double, C.c_double, C.c_double]),
+    "stdg_set_point_sources": (C.c_int, [_P, C.c_int, C.c_int, _D, _D, C.c_double, C.c_double, C.c_double]),
     "stdg_set_receivers": (C.c_int, [_P, C.c_int, _D]),
     "stdg_step": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(stdg_stats)]),
     "stdg_get_time": (C.c_int, [_P, _D]),
@@ -180,6 +181,12 @@ class Solver:
         xs, dr = _f64(np.atleast_2d(xs)), _f64(np.atleast_2d(direction))
         self._chk(self.lib.stdg_set_sources(self.h, xs.shape[0], _d(xs), _d(dr), f0, t_delay, a1))
 
+    def set_point_sources(self, xs, direction, f0, t_delay, a1, n_shots=1):
+        """Several point sources per shot: xs, direction of shape (n_shots * per_shot, dim)."""
+        xs, dr = _f64(np.atleast_2d(xs)), _f64(np.atleast_2d(direction))
+        per = xs.shape[0] // n_shots
+        self._chk(self.lib.stdg_set_point_sources(self.h, n_shots, per, _d(xs), _d(dr), f0, t_delay, a1))
+
     def set_receivers(self, xr):
         xr = _f64(np.atleast_2d(xr))
         self.n_rec = xr.shape[0]
@@ -252,6 +259,9 @@ def solver_from_workload(w, precision="fp64", rel_tol=1e-8, max_iters=5000, gmre
     s.set_material(w.lam, w.mu, w.rho)
     if with_sources and w.shots_xs is not None:
         s.set_sources(w.shots_xs, w.shots_dir, w.f0, w.t_delay, w.a1)
+    elif with_sources and "part_sources" in w.extra:     # ragged batch: one source per mesh part, one shot
+        xs = w.extra["part_sources"]
+        s.set_point_sources(xs, np.tile(np.eye(w.dim)[-1], (xs.shape[0], 1)), w.f0, w.t_delay, w.a1)
     if w.plane_wave is not None:
         pw = w.plane_wave
         s.set_plane_wave(pw["kind"], pw["n"], pw.get("pol"), pw["amp"])

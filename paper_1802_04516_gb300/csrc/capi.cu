@@ -415,19 +415,21 @@ int stdg_set_plane_wave(stdg_ctx* c, int shot, int kind, const double* n, const 
     return STDG_OK;
 }
 
-int stdg_set_sources(stdg_ctx* c, int n_shots, const double* xs, const double* dir, double f0, double t_delay, double a1) {
+int stdg_set_point_sources(stdg_ctx* c, int n_shots, int per_shot, const double* xs, const double* dir, double f0,
+                           double t_delay, double a1) {
     CHECK_CTX(c);
     NEED_ALL(c);
     const int d = c->dim, NP = c->Nphi;
-    if (n_shots < 1 || !xs || !dir) STDG_FAIL(c, STDG_EINVAL, "bad source arguments");
-    if (!all_finite(xs, (int64_t)n_shots * d) || !all_finite(dir, (int64_t)n_shots * d) || !std::isfinite(f0) ||
-        !std::isfinite(t_delay) || !std::isfinite(a1))
+    if (n_shots < 1 || per_shot < 1 || !xs || !dir) STDG_FAIL(c, STDG_EINVAL, "bad source arguments");
+    const int64_t ns = (int64_t)n_shots * per_shot;
+    if (!all_finite(xs, ns * d) || !all_finite(dir, ns * d) || !std::isfinite(f0) || !std::isfinite(t_delay) ||
+        !std::isfinite(a1))
         STDG_FAIL(c, STDG_EINVAL, "non-finite source argument");
     int rc = alloc_state(c, n_shots);
     if (rc != STDG_OK) return rc;
-    std::vector<double> host((size_t)n_shots * (d + NP));
-    c->src_elem.assign(n_shots, 0);
-    for (int s = 0; s < n_shots; ++s) {
+    std::vector<double> host((size_t)ns * (d + NP));
+    c->src_elem.assign(ns, 0);
+    for (int64_t s = 0; s < ns; ++s) {
         double y[3];
         int64_t e = locate_point(c->hm, xs + s * d, y);
         if (e < 0) STDG_FAIL(c, STDG_EINVAL, "source outside the mesh");
@@ -439,12 +441,17 @@ int stdg_set_sources(stdg_ctx* c, int n_shots, const double* xs, const double* d
     c->d_src = nullptr;
     if ((rc = dev_alloc(c, (void**)&c->d_src, sizeof(double) * host.size())) != STDG_OK) return rc;
     STDG_CUDA(c, cudaMemcpy(c->d_src, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice));
+    c->src_per_shot = per_shot;
     c->src_f0 = f0;
     c->src_td = t_delay;
     c->src_a1 = a1;
     c->have_sources = 1;
     solver_invalidate_graph(c);
     return STDG_OK;
+}
+
+int stdg_set_sources(stdg_ctx* c, int n_shots, const double* xs, const double* dir, double f0, double t_delay, double a1) {
+    return stdg_set_point_sources(c, n_shots, 1, xs, dir, f0, t_delay, a1);
 }
 
 int stdg_set_receivers(stdg_ctx* c, int n_rec, const double* xr) {

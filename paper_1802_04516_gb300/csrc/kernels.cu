@@ -740,9 +740,10 @@ cudaError_t launch_rhs(stdg_ctx* c, double dt, const double* dparams, int shot, 
         rhs_face_kernel<D_, N_><<<(unsigned)std::min<int64_t>((c->n_face + 3) / 4, 1 << 30), 128, smem, c->stream>>>(
             c->n_face, NG, c->d_face_l, c->d_face_r, c->d_D, c->d_rt, dt, sig, b); note_launch(c);
     }));
-    if (c->have_sources) {
-        rhs_source_kernel<<<1, 128, 0, c->stream>>>(c->dim, NP, NG, c->d_rt, dparams, (int32_t)c->src_elem[shot],
-                                                     c->d_src + shot * (c->dim + NP), c->src_f0, c->src_td, c->src_a1,
+    for (int q = 0; c->have_sources && q < c->src_per_shot; ++q) {   // sequential: sources may share an element
+        const int64_t sq = (int64_t)shot * c->src_per_shot + q;
+        rhs_source_kernel<<<1, 128, 0, c->stream>>>(c->dim, NP, NG, c->d_rt, dparams, (int32_t)c->src_elem[sq],
+                                                     c->d_src + sq * (c->dim + NP), c->src_f0, c->src_td, c->src_a1,
                                                      c->d_gl8, b); note_launch(c);
     }
     return cudaGetLastError();

@@ -111,8 +111,9 @@ struct stdg_ctx {
 
     // ---- sources / receivers
     int have_sources = 0;
-    std::vector<int64_t> src_elem;     // per shot
-    double *d_src = nullptr;           // per shot: [dim dir][Nphi phi(x_s)]
+    std::vector<int64_t> src_elem;     // [shot][source of the shot]
+    int src_per_shot = 1;
+    double *d_src = nullptr;           // [shot][source]: [dim dir][Nphi phi(x_s)]
     int32_t *d_src_elem = nullptr;
     double src_f0 = 0, src_td = 0, src_a1 = 0;
     double* d_gl8 = nullptr;           // 8-point Gauss-Legendre rule on [0,1]: nodes, weights

@@ -171,3 +171,31 @@ def scaled(name, **kw):
         kw.setdefault("n_rec", 5)
         return c5_adjoint(**kw)
     raise KeyError(name)
+
+
+def ragged_union(ks=range(16), p=2, steps=200, scale=1.0, seed=1300, gap=0.5):
+    """The ragged batch as one input: meshes c4_ragged(k) placed side by side (x-shifted by
+    their width plus ``gap``) as one disconnected mesh, so that one context -- and one launch
+    per kernel -- advances all of them.  All parts share the smallest part's time step.
+    Returns (Workload, list of (first element, element count) per part)."""
+    parts = [c4_ragged(k, p=p, steps=steps, seed=seed, scale=scale) for k in ks]
+    xyz, ev, lam, mu, rho, xs, rec, spans = [], [], [], [], [], [], [], []
+    voff, eoff, xoff = 0, 0, 0.0
+    for w in parts:
+        shift = np.array([xoff, 0.0])
+        xyz.append(w.xyz + shift)
+        ev.append(w.elem_vert + voff)
+        lam.append(w.lam); mu.append(w.mu); rho.append(w.rho)
+        xs.append(w.shots_xs[0] + shift)
+        rec.append(w.receivers + shift)
+        spans.append((eoff, w.n_elem))
+        voff += w.xyz.shape[0]
+        eoff += w.n_elem
+        xoff += 2.0 + gap
+    dt = min(w.dt for w in parts)
+    u = Workload("c4_ragged_union%d_p%d_%dtri" % (len(parts), p, eoff), 2, np.concatenate(xyz),
+                 np.concatenate(ev).astype(np.int32), None, np.concatenate(lam), np.concatenate(mu),
+                 np.concatenate(rho), p=p, p_gamma=p, scheme="stdg", dt=dt, n_steps=steps, h=parts[0].h,
+                 shots_xs=None, shots_dir=None, receivers=np.concatenate(rec),
+                 extra={"part_sources": np.array(xs), "spans": spans})
+    return u, spans

@@ -233,3 +233,27 @@ def test_multishot_batch_matches_oracle_per_shot(precision, tol, rel_tol):
         assert rel_l2(v, sim.v_tr) < tol, (k, rel_l2(v, sim.v_tr))
         assert stress_field_rel(sig, sim.sig_tr, sim.disc) < tol
         assert rel_l2(rec[k], np.array(sim.records)) < 10 * tol
+
+
+@pytest.mark.parametrize("precision,tol,rel_tol", [("fp64", 1e-10, 1e-13), ("mixed", 1e-8, 1e-12)])
+def test_ragged_union_matches_oracle_per_part(precision, tol, rel_tol):
+    # meshes of different sizes placed side by side as one disconnected mesh with one source
+    # per part: one stacked solve per slab, each part against its own oracle run
+    need_gpu()
+    w, spans = synth.ragged_union(ks=[0, 5, 10], steps=3, scale=0.02)
+    s = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000)
+    st = s.step(w.dt, 3)
+    assert st["status"] == 0
+    v, sig = s.get_state(0)
+    parts = [synth.c4_ragged(k, steps=3, seed=1300, scale=0.02) for k in [0, 5, 10]]
+    f0 = 0
+    for (e0, ne), part in zip(spans, parts):
+        assert part.n_elem == ne
+        sim = oracle_sim(part, dt=w.dt)        # the part alone, in its own coordinates
+        sim.set_source(part.shots_xs[0], [0.0, 1.0], w.f0, w.t_delay, w.a1)
+        sim.step(3)
+        nf = sim.sig_tr.shape[0]
+        assert rel_l2(v[e0:e0 + ne], sim.v_tr) < tol
+        assert stress_field_rel(sig[f0:f0 + nf], sim.sig_tr, sim.disc) < tol
+        f0 += nf
+    assert f0 == sig.shape[0]
