@@ -8,6 +8,13 @@
 // a whole time step with no host round trip.  With use_graph = 0 the same kernels run
 // from a host loop that reads the flag after each body (a debugging aid).
 //
+// Several shots (right-hand sides on one mesh) are solved together: their vectors are
+// stacked shot-major, the operator and preconditioner kernels load each face's and
+// element's blocks once for all shots, and every Krylov scalar is kept PER SHOT, so each
+// shot runs its own CG / GMRES recurrence (the same iterates as a solve of that shot
+// alone) and stops at ||r_s|| <= rel_tol ||b_s||.  A shot that has converged is frozen
+// (zero step length) while the others continue; the loops end when every shot has.
+//
 // Solvers
 //   CG        (Crank-Nicolson)  r = b - A x; standard recurrences; FP64 dots.
 //   GMRES(m)  (space-time DG)   restarted, classical Gram-Schmidt with one
@@ -26,21 +33,30 @@ namespace stdg {
 constexpr int kMaxRestart = 64;
 constexpr int kRedBlocks = 1216;    // 8 x 152 SMs
 constexpr int kRedThreads = 256;
+constexpr int kFinThreads = 1024;   // single-block reduction / control kernels
 constexpr int kDotChunk = 16;       // basis vectors per pass of the multi-dot kernels
 
-struct DevScalars {
-    // current Krylov level
+// Krylov state of one shot
+struct ShotScalars {
     double bnorm, tol_abs;
-    double bmin;          // min over shots of ||b_shot|| (stacked multi-shot solves)
     double rr, pq, alpha, beta;                   // CG
     double gbeta, resid;                          // GMRES
     double hcol[kMaxRestart + 2], hpass[kMaxRestart + 2];
     double H[(kMaxRestart + 1) * kMaxRestart];
     double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
-    int j, iters, converged, flag_outer, flag_inner, max_iters, m, zero_x;
+    double red[3];                                // reduced sums handed between warps
+    int jj;            // basis columns this shot uses in the current cycle
+    int active;        // still iterating in the current cycle / CG solve
+    int converged, zero_x;                        // zero_x: b_s = 0, so x_s = 0
     // FP64 refinement level (mixed precision)
     double ir_bnorm, ir_tol_abs, ir_rnorm, ir_scale;
-    int ir_flag, ir_count, ir_max, ir_conv;
+    int ir_conv, ir_zero;
+};
+
+// loop control shared by all shots
+struct DevScalars {
+    int j, iters, flag_outer, flag_inner, max_iters, m;
+    int ir_flag, ir_count, ir_max;
     // statistics, reset by the host before a batch of steps
     int st_total, st_max, st_refine, st_notconv;
     double st_final_rel, st_iters_sum;
@@ -49,9 +65,13 @@ struct DevScalars {
 
 struct Workspace {
     int m = 30;
-    int64_t n = 0, ldv = 0;
+    int ns = 1;                   // shots
+    int64_t nvec = 0;             // values per shot (velocity DOFs)
+    int64_t n = 0, ldv = 0;       // stacked length, basis leading dimension
+    unsigned G = kRedBlocks;      // blocks per shot of the streaming kernels (grid G x ns)
     DevScalars* sc = nullptr;
-    double* partials = nullptr;   // (kMaxRestart + 2) * kRedBlocks
+    ShotScalars* ss = nullptr;    // [ns]
+    double* partials = nullptr;   // [slot][shot][block], (kMaxRestart + 2) slots
     double* dparams = nullptr;    // t^n, dt, step index
     double *V = nullptr, *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *t = nullptr;   // FP64
     float *V32 = nullptr, *w32 = nullptr, *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
@@ -62,6 +82,7 @@ struct Workspace {
     cudaGraphExec_t exec = nullptr;
     double graph_dt = -1.0;
     std::vector<void*> owned;   // device buffers of this workspace
+    dim3 grid() const { return dim3(G, (unsigned)ns); }
 };
 
 static Workspace* W(stdg_ctx* c) { return reinterpret_cast<Workspace*>(c->ws); }
@@ -80,6 +101,19 @@ __device__ __forceinline__ double block_sum(double v) {
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     return s;   // valid in thread 0
+}
+
+// sum of p[0..n) by one warp; valid in every lane
+__device__ __forceinline__ double warp_sum(const double* p, int n) {
+    double v = 0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) v += p[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// partial sums of slot k, shot s: part + (k * ns + s) * G
+__device__ __forceinline__ const double* slot(const double* part, int k, int s, int ns, int G) {
+    return part + ((int64_t)k * ns + s) * G;
 }
 
 // Per-thread dot-product accumulator: FP64 for FP64 vectors; for FP32 vectors an error-free
@@ -105,10 +139,9 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-// 16-byte vector access: VW = 4 floats or 2 doubles per load/store.  Streaming kernels walk
-// n / VW vectors with a grid-stride loop and give the n % VW tail to one thread; every
-// pointer they vectorise is 16-byte aligned (separate allocations, or basis columns at a
-// leading dimension that is a multiple of 64 elements).
+// 16-byte vector access: VW = 4 floats or 2 doubles per load/store.  Every pointer that is
+// vectorised is 16-byte aligned (separate allocations, or basis columns at a leading
+// dimension that is a multiple of 64 elements).
 template <typename R> struct VL;
 template <> struct VL<float> {
     static constexpr int W = 4;
@@ -131,92 +164,102 @@ template <> struct VL<double> {
     }
 };
 
-// sum of partials[0..nb) in a single block; result in thread 0
-__device__ __forceinline__ double sum_partials(const double* p, int nb) {
-    double v = 0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += p[i];
-    return block_sum(v);
+// Streaming over one shot's segment [s*nvec, (s+1)*nvec), s = blockIdx.y, by the
+// gridDim.x blocks of that shot: fv(i) handles the VW values from i (i a multiple of VW),
+// fs(i) one value of the unaligned head or tail (thread 0 of the shot's first block).
+template <typename R, class FV, class FS>
+__device__ __forceinline__ void seg_loop(int64_t nvec, FV&& fv, FS&& fs) {
+    constexpr int VW = VL<R>::W;
+    const int64_t lo = (int64_t)blockIdx.y * nvec, hi = lo + nvec;
+    const int64_t a0 = min(hi, (lo + VW - 1) / VW * VW);
+    const int64_t a1 = max(a0, hi / VW * VW);
+    for (int64_t g = a0 / VW + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a1 / VW;
+         g += (int64_t)gridDim.x * blockDim.x)
+        fv(g * VW);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int64_t i = lo; i < a0; ++i) fs(i);
+        for (int64_t i = a1; i < hi; ++i) fs(i);
+    }
+}
+
+// block's partial sum into slot k of its shot
+__device__ __forceinline__ void put_partial(double* part, int k, double v) {
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) part[((int64_t)k * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
 }
 
 __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, int v) {
     if (use) cudaGraphSetConditional(h, v ? 1u : 0u);
 }
 
+// per-shot dot products a_s . b_s into slot k
 template <typename A, typename B>
-__global__ void dot_partial_kernel(int64_t n, const A* __restrict__ a, const B* __restrict__ b, double* __restrict__ out) {
+__global__ void dot_partial_kernel(int64_t nvec, const A* __restrict__ a, const B* __restrict__ b, double* __restrict__ part,
+                                   int k) {
     Acc<A> acc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc.add(a[i], b[i]);
-    double s = block_sum(acc.value());
-    if (threadIdx.x == 0) out[blockIdx.x] = s;
-}
-
-// per-shot partial sums of ||b_s||^2: grid (G, nshots), part[s * G + blk]
-__global__ void shot_norm_partial_kernel(int64_t nvec, const double* __restrict__ b, double* __restrict__ part) {
-    const double* bs = b + (int64_t)blockIdx.y * nvec;
-    double acc = 0;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x)
-        acc = fma(bs[i], bs[i], acc);
-    double s = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+        acc.add(a[lo + i], b[lo + i]);
+    put_partial(part, k, acc.value());
 }
 
-// sc->bmin = min_s ||b_s||: a stacked solve stopped at ||r|| <= tol * bmin meets tol for every shot
-__global__ void shot_min_kernel(DevScalars* sc, const double* part, int G, int nshots) {
-    double mn = 0.0;
-    for (int s = 0; s < nshots; ++s) {
-        double t = sum_partials(part + s * G, G);
-        if (threadIdx.x == 0) {
-            const double nrm = sqrt(t);
-            mn = (s == 0 || nrm < mn) ? nrm : mn;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) sc->bmin = mn;
-}
-
-__global__ void zero_if_kernel(int64_t n, double* x, const int* flag) {
-    if (!*flag) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = 0;
+// x_s = 0 for the shots whose right-hand side is zero (level 0: Krylov, 1: refinement)
+__global__ void zero_if_kernel(int64_t nvec, double* x, const ShotScalars* ss, int level) {
+    if (!(level ? ss[blockIdx.y].ir_zero : ss[blockIdx.y].zero_x)) return;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x)
+        x[lo + i] = 0;
 }
 
 // ---------------------------------------------------------------------------------
-// (Preconditioned) CG kernels (R = vector type, scalars FP64).  Without a preconditioner
-// z aliases r and rz = rr.
+// (Preconditioned) CG kernels (R = vector type, scalars FP64, one recurrence per shot).
+// Without a preconditioner z aliases r and rz = rr.
 // ---------------------------------------------------------------------------------
 template <typename R>
-__global__ void cg_res_kernel(int64_t n, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ r,
+__global__ void cg_res_kernel(int64_t nvec, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ r,
                               double* __restrict__ part) {
     double rr = 0, bb = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R ri = b[i] - Ax[i];
-        r[i] = ri;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x) {
+        const R ri = b[lo + i] - Ax[lo + i];
+        r[lo + i] = ri;
         rr += (double)ri * (double)ri;
-        bb += (double)b[i] * (double)b[i];
+        bb += (double)b[lo + i] * (double)b[lo + i];
     }
-    double s1 = block_sum(rr);
-    double s2 = block_sum(bb);
-    if (threadIdx.x == 0) { part[blockIdx.x] = s1; part[kRedBlocks + blockIdx.x] = s2; }
+    put_partial(part, 0, rr);
+    put_partial(part, 1, bb);
 }
 
-// bnorm_given < 0: use ||b|| from the partials; partials: [0] rr, [1] bb, [2] rz
-__global__ void cg_init_final_kernel(DevScalars* sc, const double* part, double rel_tol, int max_iters,
-                                     double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h,
-                                     int use_bmin) {
-    double rr = sum_partials(part, kRedBlocks);
-    double bb = sum_partials(part + kRedBlocks, kRedBlocks);
-    double rz = sum_partials(part + 2 * kRedBlocks, kRedBlocks);
+// bnorm_given < 0: use ||b_s|| from the partials; slots: 0 rr, 1 bb, 2 rz
+__global__ void __launch_bounds__(kFinThreads) cg_init_final_kernel(DevScalars* sc, ShotScalars* ss, const double* part,
+                                                                    int ns, int G, double rel_tol, int max_iters,
+                                                                    double bnorm_given, int gate_ir,
+                                                                    cudaGraphConditionalHandle h, int use_h) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < 3 * ns; q += nw) {
+        const double v = warp_sum(slot(part, q % 3, q / 3, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[q / 3].red[q % 3] = v;
+    }
+    __syncthreads();
+    const int active = gate_ir ? sc->ir_flag : 1;
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        t.rr = t.red[0];
+        t.pq = t.red[2];                   // holds r.z between iterations
+        t.bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(t.red[1]);
+        t.tol_abs = rel_tol * t.bnorm;
+        t.zero_x = active && t.bnorm == 0.0;
+        t.converged = !active || sqrt(t.rr) <= t.tol_abs;
+        t.active = !t.converged;
+        t.alpha = t.beta = 0.0;
+        any |= t.active;
+    }
+    any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        const int active = gate_ir ? sc->ir_flag : 1;
-        sc->rr = rr;
-        sc->pq = rz;                       // holds r.z between iterations
-        sc->bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(bb);
-        sc->tol_abs = rel_tol * (use_bmin ? sc->bmin : sc->bnorm);
         sc->iters = 0;
         sc->max_iters = max_iters;
-        sc->zero_x = active && sc->bnorm == 0.0;
-        sc->converged = !active || sqrt(rr) <= sc->tol_abs;
-        sc->flag_inner = !sc->converged && max_iters > 0;
+        sc->flag_inner = any && max_iters > 0;
         set_cond(h, use_h, sc->flag_inner);
     }
 }
@@ -226,198 +269,247 @@ __global__ void copy_kernel(int64_t n, const R* __restrict__ a, R* __restrict__ 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = a[i];
 }
 
-__global__ void cg_alpha_kernel(DevScalars* sc, const double* part) {
-    double pq = sum_partials(part, kRedBlocks);
-    if (threadIdx.x == 0) sc->alpha = pq != 0.0 ? sc->pq / pq : 0.0;
+// alpha_s = (r.z)_s / (p.q)_s for the shots still iterating, 0 for the frozen ones
+__global__ void __launch_bounds__(kFinThreads) cg_alpha_kernel(ShotScalars* ss, const double* part, int ns, int G) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = warp; s < ns; s += nw) {
+        const double pq = warp_sum(slot(part, 0, s, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[s].alpha = ss[s].active && pq != 0.0 ? ss[s].pq / pq : 0.0;
+    }
 }
 
 template <typename R>
-__global__ void cg_update_kernel(int64_t n, const DevScalars* __restrict__ sc, R* __restrict__ x, R* __restrict__ r,
+__global__ void cg_update_kernel(int64_t nvec, const ShotScalars* __restrict__ ss, R* __restrict__ x, R* __restrict__ r,
                                  const R* __restrict__ p, const R* __restrict__ q, double* __restrict__ part) {
-    const double a = sc->alpha;
+    const double a = ss[blockIdx.y].alpha;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
     double rr = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] = (R)((double)x[i] + a * (double)p[i]);
-        const R ri = (R)((double)r[i] - a * (double)q[i]);
-        r[i] = ri;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x) {
+        x[lo + i] = (R)((double)x[lo + i] + a * (double)p[lo + i]);
+        const R ri = (R)((double)r[lo + i] - a * (double)q[lo + i]);
+        r[lo + i] = ri;
         rr += (double)ri * (double)ri;
     }
-    double s = block_sum(rr);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    put_partial(part, 0, rr);
 }
 
-// partials: [0] rr, [2] rz (r.z after the preconditioner)
-__global__ void cg_beta_kernel(DevScalars* sc, const double* part, cudaGraphConditionalHandle h, int use_h) {
-    double rr = sum_partials(part, kRedBlocks);
-    double rz = sum_partials(part + 2 * kRedBlocks, kRedBlocks);
+// slots: 0 rr, 2 rz (r.z after the preconditioner)
+__global__ void __launch_bounds__(kFinThreads) cg_beta_kernel(DevScalars* sc, ShotScalars* ss, const double* part, int ns,
+                                                              int G, cudaGraphConditionalHandle h, int use_h) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < 2 * ns; q += nw) {
+        const int k = q % 2 == 0 ? 0 : 2;
+        const double v = warp_sum(slot(part, k, q / 2, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[q / 2].red[k] = v;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        if (t.active) {
+            const double rz = t.red[2];
+            t.beta = t.pq != 0.0 ? rz / t.pq : 0.0;
+            t.pq = rz;
+            t.rr = t.red[0];
+            t.converged = sqrt(t.rr) <= t.tol_abs;
+            t.active = !t.converged;
+        }
+        if (!t.active) t.beta = 0.0;
+        any |= t.active;
+    }
+    any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        sc->beta = sc->pq != 0.0 ? rz / sc->pq : 0.0;
-        sc->pq = rz;
-        sc->rr = rr;
         sc->iters += 1;
-        sc->converged = sqrt(rr) <= sc->tol_abs;
-        sc->flag_inner = !sc->converged && sc->iters < sc->max_iters;
+        sc->flag_inner = any && sc->iters < sc->max_iters;
         set_cond(h, use_h, sc->flag_inner);
     }
 }
 
 template <typename R>
-__global__ void cg_p_kernel(int64_t n, const DevScalars* __restrict__ sc, const R* __restrict__ z, R* __restrict__ p) {
-    const double b = sc->beta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p[i] = (R)((double)z[i] + b * (double)p[i]);
+__global__ void cg_p_kernel(int64_t nvec, const ShotScalars* __restrict__ ss, const R* __restrict__ z, R* __restrict__ p) {
+    const double b = ss[blockIdx.y].beta;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x)
+        p[lo + i] = (R)((double)z[lo + i] + b * (double)p[lo + i]);
 }
 
 // ---------------------------------------------------------------------------------
-// GMRES kernels
+// GMRES kernels (one Arnoldi process and one Hessenberg matrix per shot)
 // ---------------------------------------------------------------------------------
 template <typename R>
-__global__ void gm_res_kernel(int64_t n, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ v0,
+__global__ void gm_res_kernel(int64_t nvec, const R* __restrict__ b, const R* __restrict__ Ax, R* __restrict__ v0,
                              double* __restrict__ part) {
-    constexpr int W = VL<R>::W;
-    const int64_t nv = n / W;
+    constexpr int VW = VL<R>::W;
     Acc<R> rr;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R bb[W], aa[W];
-        VL<R>::ld(b + g * W, bb);
-        VL<R>::ld(Ax + g * W, aa);
+    seg_loop<R>(nvec,
+        [&](int64_t i) {
+            R bb[VW], aa[VW];
+            VL<R>::ld(b + i, bb);
+            VL<R>::ld(Ax + i, aa);
 #pragma unroll
-        for (int u = 0; u < W; ++u) { bb[u] -= aa[u]; rr.add(bb[u], bb[u]); }
-        VL<R>::st(v0 + g * W, bb);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) { const R ri = b[i] - Ax[i]; v0[i] = ri; rr.add(ri, ri); }
-    double s = block_sum(rr.value());
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+            for (int u = 0; u < VW; ++u) { bb[u] -= aa[u]; rr.add(bb[u], bb[u]); }
+            VL<R>::st(v0 + i, bb);
+        },
+        [&](int64_t i) { const R ri = b[i] - Ax[i]; v0[i] = ri; rr.add(ri, ri); });
+    put_partial(part, 0, rr.value());
 }
 
-// set up one GMRES solve: ||b|| (from partials, or given), tolerance, counters
-__global__ void gm_init_kernel(DevScalars* sc, const double* part, double rel_tol, int max_iters, int m,
-                               double bnorm_given, int gate_ir, cudaGraphConditionalHandle h, int use_h, int use_bmin) {
-    double bb = sum_partials(part, kRedBlocks);
+// set up one GMRES solve: ||b_s|| (from slot 0, or given), tolerances, counters
+__global__ void __launch_bounds__(kFinThreads) gm_init_kernel(DevScalars* sc, ShotScalars* ss, const double* part, int ns,
+                                                              int G, double rel_tol, int max_iters, int m,
+                                                              double bnorm_given, int gate_ir,
+                                                              cudaGraphConditionalHandle h, int use_h) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (bnorm_given < 0)
+        for (int s = warp; s < ns; s += nw) {
+            const double v = warp_sum(slot(part, 0, s, ns, G), G);
+            if ((threadIdx.x & 31) == 0) ss[s].red[0] = v;
+        }
+    __syncthreads();
+    const int active = gate_ir ? sc->ir_flag : 1;
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        t.bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(t.red[0]);
+        t.tol_abs = rel_tol * t.bnorm;
+        t.zero_x = active && t.bnorm == 0.0;
+        t.converged = !active || t.zero_x;
+        t.active = 0;
+        t.jj = 0;
+        any |= !t.converged;
+    }
+    any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        const int active = gate_ir ? sc->ir_flag : 1;
-        sc->bnorm = bnorm_given >= 0 ? bnorm_given : sqrt(bb);
-        sc->tol_abs = rel_tol * (use_bmin ? sc->bmin : sc->bnorm);
         sc->iters = 0;
         sc->max_iters = max_iters;
         sc->m = m;
-        sc->converged = !active;
-        sc->zero_x = active && sc->bnorm == 0.0;
-        sc->flag_outer = active && sc->bnorm != 0.0;
-        if (sc->zero_x) sc->converged = 1;
+        sc->j = 0;
+        sc->flag_outer = any;
         set_cond(h, use_h, sc->flag_outer);
     }
 }
 
-__global__ void gm_cycle_start_kernel(DevScalars* sc, const double* part, cudaGraphConditionalHandle h, int use_h) {
-    double rr = sum_partials(part, kRedBlocks);
+// restart: beta_s = ||r_s|| (the true residual), convergence test, g = beta_s e_1
+__global__ void __launch_bounds__(kFinThreads) gm_cycle_start_kernel(DevScalars* sc, ShotScalars* ss, const double* part,
+                                                                     int ns, int G, cudaGraphConditionalHandle h,
+                                                                     int use_h) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = warp; s < ns; s += nw) {
+        const double v = warp_sum(slot(part, 0, s, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[s].red[0] = v;
+    }
+    __syncthreads();
+    const int m = sc->m;
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        const double beta = sqrt(t.red[0]);
+        t.gbeta = beta;
+        t.resid = beta;
+        t.jj = 0;
+        if (!t.converged) t.converged = beta <= t.tol_abs;
+        t.active = !t.converged;
+        for (int k = 0; k <= m; ++k) t.g[k] = 0.0;
+        t.g[0] = beta;
+        any |= t.active;
+    }
+    any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        const double beta = sqrt(rr);
-        sc->gbeta = beta;
-        sc->resid = beta;
         sc->j = 0;
-        sc->converged = beta <= sc->tol_abs;
-        for (int k = 0; k <= sc->m; ++k) sc->g[k] = 0.0;
-        sc->g[0] = beta;
-        sc->flag_inner = !sc->converged && sc->iters < sc->max_iters;
+        sc->flag_inner = any && sc->iters < sc->max_iters;
         set_cond(h, use_h, sc->flag_inner);
     }
 }
 
 template <typename R>
-__global__ void gm_scale0_kernel(int64_t n, const DevScalars* __restrict__ sc, R* __restrict__ v0) {
+__global__ void gm_scale0_kernel(int64_t nvec, const DevScalars* __restrict__ sc, const ShotScalars* __restrict__ ss,
+                                 R* __restrict__ v0) {
     if (!sc->flag_inner) return;
-    constexpr int W = VL<R>::W;
-    const R s = (R)(1.0 / sc->gbeta);
-    const int64_t nv = n / W;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R a[W];
-        VL<R>::ld(v0 + g * W, a);
+    constexpr int VW = VL<R>::W;
+    const double gb = ss[blockIdx.y].gbeta;
+    const R s = (R)(gb > 0.0 ? 1.0 / gb : 0.0);
+    seg_loop<R>(nvec,
+        [&](int64_t i) {
+            R a[VW];
+            VL<R>::ld(v0 + i, a);
 #pragma unroll
-        for (int u = 0; u < W; ++u) a[u] *= s;
-        VL<R>::st(v0 + g * W, a);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) v0[i] *= s;
+            for (int u = 0; u < VW; ++u) a[u] *= s;
+            VL<R>::st(v0 + i, a);
+        },
+        [&](int64_t i) { v0[i] *= s; });
 }
 
-// partials[k][blk] = sum_i V_k[i] w[i], k = 0..j  (basis columns at stride ldv)
+// slot k, shot s: sum_i V_k[i] w[i] over the shot's segment, k = 0..j (basis columns at stride ldv)
 template <typename R>
-__global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc,
+__global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
                                                       const R* __restrict__ V, const R* __restrict__ w,
                                                       double* __restrict__ part) {
-    constexpr int W = VL<R>::W;
+    constexpr int VW = VL<R>::W;
     const int J = sc->j;
-    const int64_t nv = n / W;
     for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
         Acc<R> acc[kDotChunk];
         const int kn = min(kDotChunk, J + 1 - k0);
-        for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-            R wv[W];
-            VL<R>::ld(w + g * W, wv);
+        seg_loop<R>(nvec,
+            [&](int64_t i) {
+                R wv[VW];
+                VL<R>::ld(w + i, wv);
 #pragma unroll
-            for (int kk = 0; kk < kDotChunk; ++kk)
-                if (kk < kn) {
-                    R vv[W];
-                    VL<R>::ld(V + (int64_t)(k0 + kk) * ldv + g * W, vv);
+                for (int kk = 0; kk < kDotChunk; ++kk)
+                    if (kk < kn) {
+                        R vv[VW];
+                        VL<R>::ld(V + (int64_t)(k0 + kk) * ldv + i, vv);
 #pragma unroll
-                    for (int u = 0; u < W; ++u) acc[kk].add(vv[u], wv[u]);
-                }
-        }
-        if (blockIdx.x == 0 && threadIdx.x == 0)
-            for (int64_t i = nv * W; i < n; ++i)
+                        for (int u = 0; u < VW; ++u) acc[kk].add(vv[u], wv[u]);
+                    }
+            },
+            [&](int64_t i) {
 #pragma unroll
                 for (int kk = 0; kk < kDotChunk; ++kk)
                     if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * ldv + i], w[i]);
+            });
 #pragma unroll
-        for (int kk = 0; kk < kDotChunk; ++kk) {   // constant bound keeps acc[] in registers
-            if (kk < kn) {                            // kn is uniform over the block
-                double s = block_sum(acc[kk].value());
-                if (threadIdx.x == 0) part[(k0 + kk) * kRedBlocks + blockIdx.x] = s;
-            }
-        }
+        for (int kk = 0; kk < kDotChunk; ++kk)   // constant bound keeps acc[] in registers
+            if (kk < kn) put_partial(part, k0 + kk, acc[kk].value());   // kn is uniform over the block
     }
 }
 
 // Second Gram-Schmidt pass fused with the first subtraction:
-// w <- w - sum_k h1[k] V_k, then partials of V_k . w for the re-orthogonalisation.
+// w_s <- w_s - sum_k h1_s[k] V_k, then partials of V_k . w_s for the re-orthogonalisation.
 template <typename R>
-__global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc,
-                                                            const R* __restrict__ V, R* __restrict__ w,
-                                                            double* __restrict__ part) {
-    constexpr int W = VL<R>::W;
+__global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
+                                                            const ShotScalars* __restrict__ ss, const R* __restrict__ V,
+                                                            R* __restrict__ w, double* __restrict__ part) {
+    constexpr int VW = VL<R>::W;
     const int J = sc->j;
     __shared__ R h[kMaxRestart + 2];
-    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)sc->hpass[k];
+    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)ss[blockIdx.y].hpass[k];
     __syncthreads();
-    const int64_t nv = n / W;
     for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
         Acc<R> acc[kDotChunk];
         const int kn = min(kDotChunk, J + 1 - k0);
-        for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-            R wv[W];
-            VL<R>::ld(w + g * W, wv);
-            if (k0 == 0) {   // first chunk: form and store the projected w (in the vector precision)
-                for (int k = 0; k <= J; ++k) {
-                    R vv[W];
-                    VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
+        seg_loop<R>(nvec,
+            [&](int64_t i) {
+                R wv[VW];
+                VL<R>::ld(w + i, wv);
+                if (k0 == 0) {   // first chunk: form and store the projected w (in the vector precision)
+                    for (int k = 0; k <= J; ++k) {
+                        R vv[VW];
+                        VL<R>::ld(V + (int64_t)k * ldv + i, vv);
 #pragma unroll
-                    for (int u = 0; u < W; ++u) wv[u] = fma(-h[k], vv[u], wv[u]);
+                        for (int u = 0; u < VW; ++u) wv[u] = fma(-h[k], vv[u], wv[u]);
+                    }
+                    VL<R>::st(w + i, wv);
                 }
-                VL<R>::st(w + g * W, wv);
-            }
 #pragma unroll
-            for (int kk = 0; kk < kDotChunk; ++kk)
-                if (kk < kn) {
-                    R vv[W];
-                    VL<R>::ld(V + (int64_t)(k0 + kk) * ldv + g * W, vv);
+                for (int kk = 0; kk < kDotChunk; ++kk)
+                    if (kk < kn) {
+                        R vv[VW];
+                        VL<R>::ld(V + (int64_t)(k0 + kk) * ldv + i, vv);
 #pragma unroll
-                    for (int u = 0; u < W; ++u) acc[kk].add(vv[u], wv[u]);
-                }
-        }
-        if (blockIdx.x == 0 && threadIdx.x == 0)
-            for (int64_t i = nv * W; i < n; ++i) {
+                        for (int u = 0; u < VW; ++u) acc[kk].add(vv[u], wv[u]);
+                    }
+            },
+            [&](int64_t i) {
                 R wi = w[i];
                 if (k0 == 0) {
                     for (int k = 0; k <= J; ++k) wi = fma(-h[k], V[(int64_t)k * ldv + i], wi);
@@ -426,262 +518,279 @@ __global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t n, int64_t l
 #pragma unroll
                 for (int kk = 0; kk < kDotChunk; ++kk)
                     if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * ldv + i], wi);
-            }
+            });
 #pragma unroll
-        for (int kk = 0; kk < kDotChunk; ++kk) {
-            if (kk < kn) {
-                double s = block_sum(acc[kk].value());
-                if (threadIdx.x == 0) part[(k0 + kk) * kRedBlocks + blockIdx.x] = s;
-            }
-        }
+        for (int kk = 0; kk < kDotChunk; ++kk)
+            if (kk < kn) put_partial(part, k0 + kk, acc[kk].value());
     }
 }
 
-__global__ void gm_mdot_final_kernel(DevScalars* sc, const double* part, int pass) {
+// hpass_s[k] = reduced slot k (k = 0..j); pass 0 starts the Hessenberg column, pass 1 adds
+__global__ void __launch_bounds__(kFinThreads) gm_mdot_final_kernel(const DevScalars* sc, ShotScalars* ss,
+                                                                    const double* part, int ns, int G, int pass) {
     const int J = sc->j;
-    for (int k = 0; k <= J; ++k) {
-        double s = sum_partials(part + k * kRedBlocks, kRedBlocks);
-        if (threadIdx.x == 0) {
-            sc->hpass[k] = s;
-            sc->hcol[k] = pass == 0 ? s : sc->hcol[k] + s;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < (J + 1) * ns; q += nw) {
+        const int k = q / ns, s = q % ns;
+        const double v = warp_sum(slot(part, k, s, ns, G), G);
+        if ((threadIdx.x & 31) == 0) {
+            ss[s].hpass[k] = v;
+            ss[s].hcol[k] = pass == 0 ? v : ss[s].hcol[k] + v;
         }
-        __syncthreads();
     }
 }
 
-// w -= sum_k hpass[k] V_k; optionally partial ||w||^2
+// w_s -= sum_k hpass_s[k] V_k; partial ||w_s||^2 into slot 0
 template <typename R>
-__global__ void __launch_bounds__(256) gm_maxpy_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc,
-                                                       const R* __restrict__ V, R* __restrict__ w, double* __restrict__ part,
-                                                       int want_norm) {
-    constexpr int W = VL<R>::W;
+__global__ void __launch_bounds__(256) gm_maxpy_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
+                                                       const ShotScalars* __restrict__ ss, const R* __restrict__ V,
+                                                       R* __restrict__ w, double* __restrict__ part) {
+    constexpr int VW = VL<R>::W;
     const int J = sc->j;
     __shared__ R h[kMaxRestart + 2];
-    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)sc->hpass[k];
+    for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)ss[blockIdx.y].hpass[k];
     __syncthreads();
-    const int64_t nv = n / W;
     Acc<R> nn;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R wv[W];
-        VL<R>::ld(w + g * W, wv);
-        for (int k = 0; k <= J; ++k) {
-            R vv[W];
-            VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
+    seg_loop<R>(nvec,
+        [&](int64_t i) {
+            R wv[VW];
+            VL<R>::ld(w + i, wv);
+            for (int k = 0; k <= J; ++k) {
+                R vv[VW];
+                VL<R>::ld(V + (int64_t)k * ldv + i, vv);
 #pragma unroll
-            for (int u = 0; u < W; ++u) wv[u] = fma(-h[k], vv[u], wv[u]);
-        }
-        VL<R>::st(w + g * W, wv);
+                for (int u = 0; u < VW; ++u) wv[u] = fma(-h[k], vv[u], wv[u]);
+            }
+            VL<R>::st(w + i, wv);
 #pragma unroll
-        for (int u = 0; u < W; ++u) nn.add(wv[u], wv[u]);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) {
+            for (int u = 0; u < VW; ++u) nn.add(wv[u], wv[u]);
+        },
+        [&](int64_t i) {
             R wi = w[i];
             for (int k = 0; k <= J; ++k) wi = fma(-h[k], V[(int64_t)k * ldv + i], wi);
             w[i] = wi;
             nn.add(wi, wi);
-        }
-    if (want_norm) {
-        double s = block_sum(nn.value());
-        if (threadIdx.x == 0) part[blockIdx.x] = s;
+        });
+    put_partial(part, 0, nn.value());
+}
+
+__global__ void __launch_bounds__(kFinThreads) gm_norm_final_kernel(const DevScalars* sc, ShotScalars* ss, const double* part,
+                                                                    int ns, int G) {
+    const int J = sc->j;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = warp; s < ns; s += nw) {
+        const double v = warp_sum(slot(part, 0, s, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[s].hcol[J + 1] = sqrt(v);
     }
 }
 
-__global__ void gm_norm_final_kernel(DevScalars* sc, const double* part) {
-    double s = sum_partials(part, kRedBlocks);
-    if (threadIdx.x == 0) sc->hcol[sc->j + 1] = sqrt(s);
-}
-
 template <typename R>
-__global__ void gm_next_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc, const R* __restrict__ w,
-                               R* __restrict__ V) {
-    constexpr int W = VL<R>::W;
+__global__ void gm_next_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
+                               const ShotScalars* __restrict__ ss, const R* __restrict__ w, R* __restrict__ V) {
+    constexpr int VW = VL<R>::W;
     const int J = sc->j;
-    const double hh = sc->hcol[J + 1];
+    const double hh = ss[blockIdx.y].hcol[J + 1];
     const R s = (R)(hh > 0.0 ? 1.0 / hh : 0.0);
     R* vn = V + (int64_t)(J + 1) * ldv;
-    const int64_t nv = n / W;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R a[W];
-        VL<R>::ld(w + g * W, a);
+    seg_loop<R>(nvec,
+        [&](int64_t i) {
+            R a[VW];
+            VL<R>::ld(w + i, a);
 #pragma unroll
-        for (int u = 0; u < W; ++u) a[u] *= s;
-        VL<R>::st(vn + g * W, a);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) vn[i] = w[i] * s;
+            for (int u = 0; u < VW; ++u) a[u] *= s;
+            VL<R>::st(vn + i, a);
+        },
+        [&](int64_t i) { vn[i] = w[i] * s; });
 }
 
-__global__ void gm_givens_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int use_h) {
-    if (threadIdx.x != 0) return;
+// Givens update of every shot still iterating; a shot stops at its residual estimate or on
+// breakdown, and keeps the columns it has (jj)
+__global__ void __launch_bounds__(kFinThreads) gm_givens_kernel(DevScalars* sc, ShotScalars* ss, int ns,
+                                                                cudaGraphConditionalHandle h, int use_h) {
     const int J = sc->j, m = sc->m;
-    double* hc = sc->hcol;
-    for (int i = 0; i < J; ++i) {
-        const double t = sc->cs[i] * hc[i] + sc->sn[i] * hc[i + 1];
-        hc[i + 1] = -sc->sn[i] * hc[i] + sc->cs[i] * hc[i + 1];
-        hc[i] = t;
-    }
-    const double a = hc[J], b = hc[J + 1];
-    const double den = hypot(a, b);
-    double cs = 1.0, sn = 0.0;
-    if (den > 0.0) { cs = a / den; sn = b / den; }
-    sc->cs[J] = cs;
-    sc->sn[J] = sn;
-    hc[J] = den;
-    hc[J + 1] = 0.0;
-    for (int i = 0; i <= J; ++i) sc->H[i * kMaxRestart + J] = hc[i];
-    sc->g[J + 1] = -sn * sc->g[J];
-    sc->g[J] = cs * sc->g[J];
-    sc->resid = fabs(sc->g[J + 1]);
-    sc->iters += 1;
-    sc->j = J + 1;
-    const int done = sc->resid <= sc->tol_abs || den == 0.0;
-    sc->flag_inner = !done && sc->j < m && sc->iters < sc->max_iters;
-    set_cond(h, use_h, sc->flag_inner);
-}
-
-// y = R^{-1} g (upper triangular, size j)
-__global__ void gm_solve_kernel(DevScalars* sc) {
-    if (threadIdx.x != 0) return;
-    const int J = sc->j;
-    for (int i = J - 1; i >= 0; --i) {
-        double s = sc->g[i];
-        for (int k = i + 1; k < J; ++k) s -= sc->H[i * kMaxRestart + k] * sc->y[k];
-        const double d = sc->H[i * kMaxRestart + i];
-        sc->y[i] = d != 0.0 ? s / d : 0.0;
-    }
-}
-
-template <typename R>
-__global__ void gm_update_x_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc, const R* __restrict__ V,
-                                   R* __restrict__ x) {
-    constexpr int W = VL<R>::W;
-    const int J = sc->j;
-    if (J == 0) return;
-    __shared__ R y[kMaxRestart];
-    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = (R)sc->y[k];
-    __syncthreads();
-    const int64_t nv = n / W;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R a[W];
-        VL<R>::ld(x + g * W, a);
-        for (int k = 0; k < J; ++k) {
-            R vv[W];
-            VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
-#pragma unroll
-            for (int u = 0; u < W; ++u) a[u] = fma(y[k], vv[u], a[u]);
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        if (t.active) {
+            double* hc = t.hcol;
+            for (int i = 0; i < J; ++i) {
+                const double u = t.cs[i] * hc[i] + t.sn[i] * hc[i + 1];
+                hc[i + 1] = -t.sn[i] * hc[i] + t.cs[i] * hc[i + 1];
+                hc[i] = u;
+            }
+            const double a = hc[J], b = hc[J + 1];
+            const double den = hypot(a, b);
+            double cs = 1.0, sn = 0.0;
+            if (den > 0.0) { cs = a / den; sn = b / den; }
+            t.cs[J] = cs;
+            t.sn[J] = sn;
+            hc[J] = den;
+            hc[J + 1] = 0.0;
+            for (int i = 0; i <= J; ++i) t.H[i * kMaxRestart + J] = hc[i];
+            t.g[J + 1] = -sn * t.g[J];
+            t.g[J] = cs * t.g[J];
+            t.resid = fabs(t.g[J + 1]);
+            t.jj = J + 1;
+            if (t.resid <= t.tol_abs || den == 0.0) t.active = 0;
         }
-        VL<R>::st(x + g * W, a);
+        any |= t.active;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) {
-            R a = x[i];
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->j = J + 1;
+        sc->flag_inner = any && sc->j < m && sc->iters < sc->max_iters;
+        set_cond(h, use_h, sc->flag_inner);
+    }
+}
+
+// y_s = R_s^{-1} g_s (upper triangular, size jj_s)
+__global__ void gm_solve_kernel(ShotScalars* ss, int ns) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
+        ShotScalars& t = ss[s];
+        const int J = t.jj;
+        for (int i = J - 1; i >= 0; --i) {
+            double v = t.g[i];
+            for (int k = i + 1; k < J; ++k) v -= t.H[i * kMaxRestart + k] * t.y[k];
+            const double d = t.H[i * kMaxRestart + i];
+            t.y[i] = d != 0.0 ? v / d : 0.0;
+        }
+    }
+}
+
+// x_s += sum_{k<jj_s} y_s[k] V_k  (accumulate = 1), or t_s = sum_k y_s[k] V_k (accumulate = 0;
+// right preconditioning applies P^{-1} to t afterwards)
+template <typename R>
+__global__ void gm_combine_kernel(int64_t nvec, int64_t ldv, const ShotScalars* __restrict__ ss, const R* __restrict__ V,
+                                  R* __restrict__ x, int accumulate) {
+    constexpr int VW = VL<R>::W;
+    const int J = ss[blockIdx.y].jj;
+    if (accumulate && J == 0) return;
+    __shared__ R y[kMaxRestart];
+    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = (R)ss[blockIdx.y].y[k];
+    __syncthreads();
+    seg_loop<R>(nvec,
+        [&](int64_t i) {
+            R a[VW];
+            if (accumulate) VL<R>::ld(x + i, a);
+            else {
+#pragma unroll
+                for (int u = 0; u < VW; ++u) a[u] = 0;
+            }
+            for (int k = 0; k < J; ++k) {
+                R vv[VW];
+                VL<R>::ld(V + (int64_t)k * ldv + i, vv);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) a[u] = fma(y[k], vv[u], a[u]);
+            }
+            VL<R>::st(x + i, a);
+        },
+        [&](int64_t i) {
+            R a = accumulate ? x[i] : (R)0;
             for (int k = 0; k < J; ++k) a = fma(y[k], V[(int64_t)k * ldv + i], a);
             x[i] = a;
-        }
-}
-
-// t = sum_{k<j} y_k V_k (right preconditioning: x += P^{-1} t afterwards)
-template <typename R>
-__global__ void gm_combine_kernel(int64_t n, int64_t ldv, const DevScalars* __restrict__ sc, const R* __restrict__ V,
-                                  R* __restrict__ t) {
-    constexpr int W = VL<R>::W;
-    const int J = sc->j;
-    __shared__ R y[kMaxRestart];
-    for (int k = threadIdx.x; k < J; k += blockDim.x) y[k] = (R)sc->y[k];
-    __syncthreads();
-    const int64_t nv = n / W;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R a[W];
-#pragma unroll
-        for (int u = 0; u < W; ++u) a[u] = 0;
-        for (int k = 0; k < J; ++k) {
-            R vv[W];
-            VL<R>::ld(V + (int64_t)k * ldv + g * W, vv);
-#pragma unroll
-            for (int u = 0; u < W; ++u) a[u] = fma(y[k], vv[u], a[u]);
-        }
-        VL<R>::st(t + g * W, a);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) {
-            R a = 0;
-            for (int k = 0; k < J; ++k) a = fma(y[k], V[(int64_t)k * ldv + i], a);
-            t[i] = a;
-        }
+        });
 }
 
 template <typename R>
 __global__ void axpy_kernel(int64_t n, R* __restrict__ x, const R* __restrict__ z) {
-    constexpr int W = VL<R>::W;
-    const int64_t nv = n / W;
+    constexpr int VW = VL<R>::W;
+    const int64_t nv = n / VW;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nv; g += (int64_t)gridDim.x * blockDim.x) {
-        R a[W], b[W];
-        VL<R>::ld(x + g * W, a);
-        VL<R>::ld(z + g * W, b);
+        R a[VW], b[VW];
+        VL<R>::ld(x + g * VW, a);
+        VL<R>::ld(z + g * VW, b);
 #pragma unroll
-        for (int u = 0; u < W; ++u) a[u] += b[u];
-        VL<R>::st(x + g * W, a);
+        for (int u = 0; u < VW; ++u) a[u] += b[u];
+        VL<R>::st(x + g * VW, a);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int64_t i = nv * W; i < n; ++i) x[i] += z[i];
+        for (int64_t i = nv * VW; i < n; ++i) x[i] += z[i];
 }
 
-__global__ void gm_cycle_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int use_h) {
-    if (threadIdx.x != 0) return;
-    sc->j = 0;
-    sc->flag_outer = !sc->converged && sc->iters < sc->max_iters;
-    set_cond(h, use_h, sc->flag_outer);
-}
-
-// ---------------------------------------------------------------------------------
-// FP64 iterative refinement around the FP32 solver
-// ---------------------------------------------------------------------------------
-__global__ void ir_init_kernel(DevScalars* sc, const double* part, double rel_tol, int ir_max,
-                               cudaGraphConditionalHandle h, int use_h, int use_bmin) {
-    double bb = sum_partials(part, kRedBlocks);
+__global__ void __launch_bounds__(kFinThreads) gm_cycle_end_kernel(DevScalars* sc, const ShotScalars* ss, int ns,
+                                                                   cudaGraphConditionalHandle h, int use_h) {
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) any |= !ss[s].converged;
+    any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-        sc->ir_bnorm = sqrt(bb);
-        sc->ir_tol_abs = rel_tol * (use_bmin ? sc->bmin : sc->ir_bnorm);
+        sc->j = 0;
+        sc->flag_outer = any && sc->iters < sc->max_iters;
+        set_cond(h, use_h, sc->flag_outer);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 iterative refinement around the FP32 solver (per shot)
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFinThreads) ir_init_kernel(DevScalars* sc, ShotScalars* ss, const double* part, int ns,
+                                                              int G, double rel_tol, int ir_max,
+                                                              cudaGraphConditionalHandle h, int use_h) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = warp; s < ns; s += nw) {
+        const double v = warp_sum(slot(part, 0, s, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[s].red[0] = v;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        t.ir_bnorm = sqrt(t.red[0]);
+        t.ir_tol_abs = rel_tol * t.ir_bnorm;
+        t.ir_rnorm = t.ir_bnorm;
+        t.ir_zero = t.ir_bnorm == 0.0;
+        t.ir_conv = t.ir_zero;
+        any |= !t.ir_conv;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
         sc->ir_count = 0;
         sc->ir_max = ir_max;
-        sc->ir_flag = 1;
-        sc->ir_conv = 0;
-        sc->zero_x = sc->ir_bnorm == 0.0;
-        if (sc->zero_x) sc->ir_conv = 1;
-        if (sc->zero_x) sc->ir_flag = 0;
+        sc->ir_flag = any;
         set_cond(h, use_h, sc->ir_flag);
     }
 }
 
-__global__ void ir_check_kernel(DevScalars* sc, const double* part, int max_total) {
-    double rr = sum_partials(part, kRedBlocks);
-    if (threadIdx.x == 0) {
-        sc->ir_rnorm = sqrt(rr);
-        const int conv = sc->ir_rnorm <= sc->ir_tol_abs;
-        sc->ir_conv = conv;
-        sc->ir_flag = !conv && sc->ir_count < sc->ir_max && sc->st_total < max_total;
-        sc->ir_scale = sc->ir_rnorm > 0.0 ? 1.0 / sc->ir_rnorm : 0.0;
+__global__ void __launch_bounds__(kFinThreads) ir_check_kernel(DevScalars* sc, ShotScalars* ss, const double* part, int ns,
+                                                               int G, int max_total) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s = warp; s < ns; s += nw) {
+        const double v = warp_sum(slot(part, 0, s, ns, G), G);
+        if ((threadIdx.x & 31) == 0) ss[s].red[0] = v;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        t.ir_rnorm = sqrt(t.red[0]);
+        t.ir_conv = t.ir_zero || t.ir_rnorm <= t.ir_tol_abs;
+        t.ir_scale = !t.ir_conv && t.ir_rnorm > 0.0 ? 1.0 / t.ir_rnorm : 0.0;
+        any |= !t.ir_conv;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) sc->ir_flag = any && sc->ir_count < sc->ir_max && sc->st_total < max_total;
+}
+
+// r32_s = r64_s * scale_s (0 for converged shots); x32 = 0   (when the refinement continues)
+__global__ void ir_convert_kernel(int64_t nvec, const DevScalars* __restrict__ sc, const ShotScalars* __restrict__ ss,
+                                  const double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ x32) {
+    if (!sc->ir_flag) return;
+    const double s = ss[blockIdx.y].ir_scale;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x) {
+        r32[lo + i] = (float)(r64[lo + i] * s);
+        x32[lo + i] = 0.0f;
     }
 }
 
-// r32 = r64 * scale; x32 = 0   (when the refinement continues)
-__global__ void ir_convert_kernel(int64_t n, const DevScalars* __restrict__ sc, const double* __restrict__ r64,
-                                  float* __restrict__ r32, float* __restrict__ x32) {
-    if (!sc->ir_flag) return;
-    const double s = sc->ir_scale;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        r32[i] = (float)(r64[i] * s);
-        x32[i] = 0.0f;
-    }
-}
-
-// x += x32 / scale
-__global__ void ir_update_kernel(int64_t n, const DevScalars* __restrict__ sc, const float* __restrict__ x32, double* __restrict__ x) {
-    if (!sc->ir_flag) return;
-    const double s = sc->ir_rnorm;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += s * (double)x32[i];
+// x_s += |r_s| x32_s
+__global__ void ir_update_kernel(int64_t nvec, const DevScalars* __restrict__ sc, const ShotScalars* __restrict__ ss,
+                                 const float* __restrict__ x32, double* __restrict__ x) {
+    if (!sc->ir_flag || ss[blockIdx.y].ir_conv) return;
+    const double s = ss[blockIdx.y].ir_rnorm;
+    const int64_t lo = (int64_t)blockIdx.y * nvec;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x)
+        x[lo + i] += s * (double)x32[lo + i];
 }
 
 __global__ void ir_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int use_h) {
@@ -693,25 +802,31 @@ __global__ void ir_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int 
     set_cond(h, use_h, sc->ir_flag);
 }
 
-// per-solve statistics; mode 0 = GMRES, 1 = CG, 2 = mixed (refinement level)
-__global__ void solve_stats_kernel(DevScalars* sc, int mode, int use_bmin) {
+// per-solve statistics (worst shot); mode 0 = GMRES, 1 = CG, 2 = mixed (refinement level)
+__global__ void __launch_bounds__(kFinThreads) solve_stats_kernel(DevScalars* sc, const ShotScalars* ss, int ns, int mode) {
+    __shared__ double worst[kFinThreads];
+    double rel = 0.0;
+    int notconv = 0;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const ShotScalars& t = ss[s];
+        double r, bn;
+        if (mode == 2) { r = t.ir_zero ? 0.0 : t.ir_rnorm; bn = t.ir_bnorm; notconv |= !t.ir_conv; }
+        else { r = t.zero_x ? 0.0 : mode == 1 ? sqrt(t.rr) : t.resid; bn = t.bnorm; notconv |= !t.converged; }
+        rel = fmax(rel, bn > 0 ? r / bn : 0.0);
+    }
+    worst[threadIdx.x] = rel;
+    notconv = __syncthreads_or(notconv);
     if (threadIdx.x != 0) return;
+    for (int i = 1; i < (int)blockDim.x; ++i) rel = fmax(rel, worst[i]);
     int it;
-    double rel;
     if (mode == 2) {
         it = sc->st_total;          // accumulated by ir_end over the refinement sweeps
         sc->st_total = 0;
-        const double bn = use_bmin ? sc->bmin : sc->ir_bnorm;
-        rel = bn > 0 ? sc->ir_rnorm / bn : 0.0;
         sc->st_refine += sc->ir_count;
-        if (!sc->ir_conv) sc->st_notconv = 1;
     } else {
         it = sc->iters;
-        const double r = mode == 1 ? sqrt(sc->rr) : sc->resid;
-        const double bn = use_bmin ? sc->bmin : sc->bnorm;
-        rel = bn > 0 ? r / bn : 0.0;
-        if (!sc->converged) sc->st_notconv = 1;
     }
+    if (notconv) sc->st_notconv = 1;
     sc->st_final_rel = rel;
     sc->st_max = max(sc->st_max, it);
     sc->st_iters_sum += (double)it;
@@ -796,35 +911,36 @@ struct Flow {
     }
 };
 
-static unsigned vec_blocks(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, kRedBlocks); }
 
 // ---- (P)CG on vectors of type R; apply(x, y): y = A x; prec(r, z): z = P^{-1} r or null --------
 template <typename R, class Apply, class Prec>
 static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b, R* x, R* r, R* p, R* q, R* z,
-                     double rel_tol, int max_iters, double bnorm_given, int gate_ir, int use_bmin) {
+                     double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
-    const int64_t n = ws->n;
+    const int64_t n = ws->n, nv = ws->nvec;
+    const int ns = ws->ns, G = (int)ws->G;
+    const dim3 grid = ws->grid();
     R* zz = use_prec ? z : r;
     F.loop(&ws->sc->flag_inner,
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(apply(x, q));
-               cg_res_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, q, r, ws->partials); note_launch(c);
+               cg_res_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, b, q, r, ws->partials); note_launch(c);
                if (use_prec) F.check(prec(r, zz));
-               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, r, zz, ws->partials + 2 * kRedBlocks); note_launch(c);
-               cg_init_final_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, rel_tol, max_iters, bnorm_given,
-                                                                      gate_ir, h, use, use_bmin); note_launch(c);
+               dot_partial_kernel<R, R><<<grid, kRedThreads, 0, c->stream>>>(nv, r, zz, ws->partials, 2); note_launch(c);
+               cg_init_final_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ws->partials, ns, G, rel_tol, max_iters,
+                                                                      bnorm_given, gate_ir, h, use); note_launch(c);
                copy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, zz, p); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(apply(p, q));
-               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, p, q, ws->partials); note_launch(c);
-               cg_alpha_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials); note_launch(c);
-               cg_update_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, x, r, p, q, ws->partials); note_launch(c);
+               dot_partial_kernel<R, R><<<grid, kRedThreads, 0, c->stream>>>(nv, p, q, ws->partials, 0); note_launch(c);
+               cg_alpha_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->ss, ws->partials, ns, G); note_launch(c);
+               cg_update_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ws->ss, x, r, p, q, ws->partials); note_launch(c);
                if (use_prec) F.check(prec(r, zz));
-               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, r, zz, ws->partials + 2 * kRedBlocks); note_launch(c);
-               cg_beta_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, h, use); note_launch(c);
-               cg_p_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, zz, p); note_launch(c);
+               dot_partial_kernel<R, R><<<grid, kRedThreads, 0, c->stream>>>(nv, r, zz, ws->partials, 2); note_launch(c);
+               cg_beta_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ws->partials, ns, G, h, use); note_launch(c);
+               cg_p_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ws->ss, zz, p); note_launch(c);
                F.check(cudaGetLastError());
            });
 }
@@ -832,26 +948,32 @@ static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b,
 // ---- GMRES(m) on vectors of type R -----------------------------------------------------
 template <typename R, class Apply, class ApplyIdx, class Prec>
 static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, bool use_prec, const R* b, R* x, R* V, R* w,
-                        R* zbuf, R* tbuf, double rel_tol, int max_iters, double bnorm_given, int gate_ir, int use_bmin) {
+                        R* zbuf, R* tbuf, double rel_tol, int max_iters, double bnorm_given, int gate_ir) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
-    const int64_t n = ws->n, ldv = ws->ldv;
+    const int64_t n = ws->n, nv = ws->nvec, ldv = ws->ldv;
     const int m = ws->m;
+    const int ns = ws->ns, G = (int)ws->G;
+    const dim3 grid = ws->grid();
     DevScalars* sc = ws->sc;
+    ShotScalars* ss = ws->ss;
+    double* part = ws->partials;
     F.loop(&sc->flag_outer,
            [&](cudaGraphConditionalHandle h, int use) {
-               dot_partial_kernel<R, R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials); note_launch(c);
-               gm_init_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, rel_tol, max_iters, m, bnorm_given, gate_ir, h, use,
-                                                                use_bmin); note_launch(c);
+               if (bnorm_given < 0) {
+                   dot_partial_kernel<R, R><<<grid, kRedThreads, 0, c->stream>>>(nv, b, b, part, 0); note_launch(c);
+               }
+               gm_init_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, part, ns, G, rel_tol, max_iters, m, bnorm_given,
+                                                                gate_ir, h, use); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h_outer, int use_outer) {
                // restart cycle: true residual, then Arnoldi
                F.check(apply(x, w));
-               gm_res_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, w, V, ws->partials); note_launch(c);
+               gm_res_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, b, w, V, part); note_launch(c);
                F.loop(&sc->flag_inner,
                       [&](cudaGraphConditionalHandle h, int use) {
-                          gm_cycle_start_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, h, use); note_launch(c);
-                          gm_scale0_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, sc, V); note_launch(c);
+                          gm_cycle_start_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, part, ns, G, h, use); note_launch(c);
+                          gm_scale0_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, sc, ss, V); note_launch(c);
                       },
                       [&](cudaGraphConditionalHandle h, int use) {
                           if (use_prec) {   // right preconditioning: w = A P^{-1} v_j
@@ -861,36 +983,36 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
                               F.check(apply_idx(V, &sc->j, w));
                           }
                           // classical Gram-Schmidt twice, in three passes over the basis
-                          gm_mdot_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, w, ws->partials); note_launch(c);
-                          gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, 0); note_launch(c);
-                          gm_orth_fused_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, w, ws->partials); note_launch(c);
-                          gm_mdot_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials, 1); note_launch(c);
-                          gm_maxpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, w, ws->partials, 1); note_launch(c);
-                          gm_norm_final_kernel<<<1, kRedThreads, 0, c->stream>>>(sc, ws->partials); note_launch(c);
-                          gm_next_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, w, V); note_launch(c);
-                          gm_givens_kernel<<<1, 32, 0, c->stream>>>(sc, h, use); note_launch(c);
+                          gm_mdot_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, sc, V, w, part); note_launch(c);
+                          gm_mdot_final_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, part, ns, G, 0); note_launch(c);
+                          gm_orth_fused_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, sc, ss, V, w, part); note_launch(c);
+                          gm_mdot_final_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, part, ns, G, 1); note_launch(c);
+                          gm_maxpy_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, sc, ss, V, w, part); note_launch(c);
+                          gm_norm_final_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, part, ns, G); note_launch(c);
+                          gm_next_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, sc, ss, w, V); note_launch(c);
+                          gm_givens_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, ns, h, use); note_launch(c);
                           F.check(cudaGetLastError());
                       });
-               gm_solve_kernel<<<1, 32, 0, c->stream>>>(sc); note_launch(c);
+               gm_solve_kernel<<<(ns + 127) / 128, 128, 0, c->stream>>>(ss, ns); note_launch(c);
                if (use_prec) {   // x += P^{-1} (V y)
-                   gm_combine_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, tbuf); note_launch(c);
+                   gm_combine_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, ss, V, tbuf, 0); note_launch(c);
                    F.check(prec(tbuf, zbuf, nullptr, 0));
                    axpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, zbuf); note_launch(c);
                } else {
-                   gm_update_x_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ldv, sc, V, x); note_launch(c);
+                   gm_combine_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, ss, V, x, 1); note_launch(c);
                }
-               gm_cycle_end_kernel<<<1, 32, 0, c->stream>>>(sc, h_outer, use_outer); note_launch(c);
+               gm_cycle_end_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, ns, h_outer, use_outer); note_launch(c);
                F.check(cudaGetLastError());
            });
 }
 
-// ---- one shot, one slab ----------------------------------------------------------------
+// ---- all shots, one slab -----------------------------------------------------------------
 static void record_solve(Flow& F, double dt, double* b, double* x) {
     stdg_ctx* c = F.c;
     Workspace* ws = F.ws;
-    const int64_t n = ws->n;                 // stacked length: n_shots x velocity values
-    const int ns = c->n_shots;
-    const int bm = ns > 1 ? 1 : 0;            // stacked solves stop on min-shot norms
+    const int64_t nv = ws->nvec;
+    const int ns = ws->ns, G = (int)ws->G;
+    const dim3 grid = ws->grid();
     const bool cn = c->opt.scheme == STDG_SCHEME_CN;
     const bool pre = c->opt.preconditioner != 0;
     const int64_t ldv = ws->ldv;
@@ -904,41 +1026,36 @@ static void record_solve(Flow& F, double dt, double* b, double* x) {
     auto P32c = [&](const float* r, float* z) { return launch_pre1_apply32(c, r, z, nullptr, 0, ns); };
     const double tol = c->opt.rel_tol;
     const int maxit = c->opt.max_iters;
-    if (bm) {   // min over shots of ||b_s||
-        const int G = (int)std::min<int64_t>(kRedBlocks, (int64_t)(kMaxRestart + 2) * kRedBlocks / ns);
-        shot_norm_partial_kernel<<<dim3(G, ns), kRedThreads, 0, c->stream>>>(c->nvel, b, ws->partials); note_launch(c);
-        shot_min_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, G, ns); note_launch(c);
-    }
     if (c->opt.precision == STDG_FP64) {
-        if (cn) solve_cg<double>(F, A64, P64c, pre, b, x, ws->r, ws->p, ws->q, ws->z, tol, maxit, -1.0, 0, bm);
-        else solve_gmres<double>(F, A64, A64i, P64, pre, b, x, ws->V, ws->w, ws->z, ws->t, tol, maxit, -1.0, 0, bm);
-        zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x); note_launch(c);
-        solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, cn ? 1 : 0, bm); note_launch(c);
+        if (cn) solve_cg<double>(F, A64, P64c, pre, b, x, ws->r, ws->p, ws->q, ws->z, tol, maxit, -1.0, 0);
+        else solve_gmres<double>(F, A64, A64i, P64, pre, b, x, ws->V, ws->w, ws->z, ws->t, tol, maxit, -1.0, 0);
+        zero_if_kernel<<<grid, kRedThreads, 0, c->stream>>>(nv, x, ws->ss, 0); note_launch(c);
+        solve_stats_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ns, cn ? 1 : 0); note_launch(c);
         return;
     }
-    // mixed: FP64 refinement, FP32 inner solve with zero initial guess and unit RHS
+    // mixed: FP64 refinement, FP32 inner solve with zero initial guess and unit RHS per shot
     F.loop(&ws->sc->ir_flag,
            [&](cudaGraphConditionalHandle h, int use) {
-               dot_partial_kernel<double, double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, b, ws->partials); note_launch(c);
-               ir_init_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, tol, 64, h, use, bm); note_launch(c);
+               dot_partial_kernel<double, double><<<grid, kRedThreads, 0, c->stream>>>(nv, b, b, ws->partials, 0); note_launch(c);
+               ir_init_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ws->partials, ns, G, tol, 64, h, use); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(A64(x, ws->w));
-               gm_res_kernel<double><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, b, ws->w, ws->r, ws->partials); note_launch(c);
-               ir_check_kernel<<<1, kRedThreads, 0, c->stream>>>(ws->sc, ws->partials, maxit); note_launch(c);
-               ir_convert_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->r, ws->b32, ws->x32); note_launch(c);
+               gm_res_kernel<double><<<grid, kRedThreads, 0, c->stream>>>(nv, b, ws->w, ws->r, ws->partials); note_launch(c);
+               ir_check_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ws->partials, ns, G, maxit); note_launch(c);
+               ir_convert_kernel<<<grid, kRedThreads, 0, c->stream>>>(nv, ws->sc, ws->ss, ws->r, ws->b32, ws->x32); note_launch(c);
                if (cn)
                    solve_cg<float>(F, A32, P32c, pre, ws->b32, ws->x32, ws->r32, ws->p32, ws->q32, ws->z32, c->opt.inner_tol,
-                                   maxit, 1.0, 1, 0);
+                                   maxit, 1.0, 1);
                else
                    solve_gmres<float>(F, A32, A32i, P32, pre, ws->b32, ws->x32, ws->V32, ws->w32, ws->z32, ws->t32,
-                                      c->opt.inner_tol, maxit, 1.0, 1, 0);
-               ir_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, ws->sc, ws->x32, x); note_launch(c);
+                                      c->opt.inner_tol, maxit, 1.0, 1);
+               ir_update_kernel<<<grid, kRedThreads, 0, c->stream>>>(nv, ws->sc, ws->ss, ws->x32, x); note_launch(c);
                ir_end_kernel<<<1, 32, 0, c->stream>>>(ws->sc, h, use); note_launch(c);
                F.check(cudaGetLastError());
            });
-    zero_if_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, &ws->sc->zero_x); note_launch(c);
-    solve_stats_kernel<<<1, 32, 0, c->stream>>>(ws->sc, 2, bm); note_launch(c);
+    zero_if_kernel<<<grid, kRedThreads, 0, c->stream>>>(nv, x, ws->ss, 1); note_launch(c);
+    solve_stats_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ns, 2); note_launch(c);
 }
 
 // One slab for every shot: per-shot right-hand sides and initial guesses, ONE stacked
@@ -971,7 +1088,10 @@ int solver_setup(stdg_ctx* c) {
     Workspace* ws = new Workspace();
     c->ws = ws;
     ws->m = std::max(2, std::min(c->opt.gmres_restart > 0 ? c->opt.gmres_restart : 30, kMaxRestart));
+    ws->ns = c->n_shots;
+    ws->nvec = c->nvel;
     ws->n = c->nvel * (int64_t)c->n_shots;
+    ws->G = (unsigned)std::max(1, kRedBlocks / ws->ns);
     const int64_t n = ws->n;
     const bool cn = c->opt.scheme == STDG_SCHEME_CN;
     const bool mixed = c->opt.precision != STDG_FP64;
@@ -980,7 +1100,8 @@ int solver_setup(stdg_ctx* c) {
 #define ALLOC(ptr, bytes) do { if ((rc = dev_alloc(c, (void**)&(ptr), (bytes))) != STDG_OK) return rc; \
                                ws->owned.push_back((void*)(ptr)); } while (0)
     ALLOC(ws->sc, sizeof(DevScalars));
-    ALLOC(ws->partials, sizeof(double) * (kMaxRestart + 2) * kRedBlocks);
+    ALLOC(ws->ss, sizeof(ShotScalars) * ws->ns);
+    ALLOC(ws->partials, sizeof(double) * (kMaxRestart + 2) * ws->G * ws->ns);
     ALLOC(ws->dparams, sizeof(double) * 4);
     ALLOC(c->d_b, sizeof(double) * n);
     ALLOC(c->d_x, sizeof(double) * n);
@@ -999,6 +1120,7 @@ int solver_setup(stdg_ctx* c) {
     }
 #undef ALLOC
     cudaMemsetAsync(ws->sc, 0, sizeof(DevScalars), c->stream);
+    cudaMemsetAsync(ws->ss, 0, sizeof(ShotScalars) * ws->ns, c->stream);
     cudaMemsetAsync(ws->dparams, 0, sizeof(double) * 4, c->stream);
     for (auto& s : ws->side) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     return STDG_OK;

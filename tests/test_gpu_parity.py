@@ -235,6 +235,22 @@ def test_multishot_batch_matches_oracle_per_shot(precision, tol, rel_tol):
         assert rel_l2(rec[k], np.array(sim.records)) < 10 * tol
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multishot_iterations_follow_each_shot(precision):
+    # every shot keeps its own Krylov recurrence inside the stacked solve, so the batch takes
+    # as many iterations as its slowest shot alone
+    import dataclasses
+    need_gpu()
+    w = synth.scaled("c4", ny=8, steps=2, n_shots=3)
+    st = gpu_solver(w, precision=precision, rel_tol=1e-10, max_iters=20000).step(w.dt, 2)
+    assert st["status"] == 0
+    singles = []
+    for k in range(3):
+        wk = dataclasses.replace(w, shots_xs=w.shots_xs[k:k + 1], shots_dir=w.shots_dir[k:k + 1])
+        singles.append(gpu_solver(wk, precision=precision, rel_tol=1e-10, max_iters=20000).step(w.dt, 2)["iters_max"])
+    assert st["iters_max"] <= max(singles) + 2, (st["iters_max"], singles)
+
+
 @pytest.mark.parametrize("precision,tol,rel_tol", [("fp64", 1e-10, 1e-13), ("mixed", 1e-8, 1e-12)])
 def test_ragged_union_matches_oracle_per_part(precision, tol, rel_tol):
     # meshes of different sizes placed side by side as one disconnected mesh with one source
