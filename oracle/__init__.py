@@ -15,6 +15,8 @@ Modules
              (Sec. 3, "Two space dimensions" / "Three space dimensions")
   operators  M_j, Mbar_i, D_{i,j}, Q_{i,j}, time matrices (Eqs. MD_2 - SD_1), the
              Schur velocity system (Eq. velocity.sys, Eq. velocity.sys.cn)
+  precond    Appendix A preconditioners on the assembled system: block Jacobi (Eq. pre1)
+             and the stencil-local inverse (Eqs. APPRE1 / APPRE2)
   stepper    one time slab: right-hand side, direct solve, stress back-substitution
              (Eq. NM26 / NM26.cn), traces, energy (Eq. SP3F), receivers, Ricker point
              sources (Sec. 6.3)
@@ -22,4 +24,4 @@ Modules
 Parity status of every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, theorems of the paper and brute-force checks; see each module header.
 """
-from . import basis, quadrature, mesh, operators, stepper  # noqa: F401
+from . import basis, quadrature, mesh, operators, precond, stepper  # noqa: F401
