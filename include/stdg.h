@@ -62,7 +62,12 @@ typedef struct {
     double inner_tol;   /* relative tolerance of the FP32 inner solve (mixed precision)  */
     int use_graph;      /* 1: one CUDA graph per step with device-side loops; 0: host loop */
     int preconditioner; /* 0: none; 1: block Jacobi "Pre1" (Appendix A, Eq. pre1): exact inverse of
-                           every element's diagonal block, applied on the right (GMRES) or as PCG */
+                           every element's diagonal block, applied on the right (GMRES) or as PCG;
+                           2: stencil preconditioner "Pre2" (Appendix A, Eqs. APPRE1-APPRE2): first
+                           block row of the inverse of the system restricted to the element and its
+                           face neighbours.  Pre2 is not symmetric, so Crank-Nicolson then runs
+                           GMRES instead of CG.  Needs d N_phi N_gamma <= 128 (else STDG_EINVAL at
+                           stdg_set_material); costs (d N_phi N_gamma)^2 values per element.    */
 } stdg_options;
 
 typedef struct {
@@ -158,8 +163,9 @@ int stdg_query(stdg_ctx* ctx, int what, int64_t* out);
 /* Face table as built by stdg_set_mesh: l(j), r(j) (-1 on the boundary). */
 int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);
 
-/* z = P^{-1} r with the block-Jacobi preconditioner Pre1 for slab size dt (canonical
- * velocity layout, one shot, FP64, host pointers).  Requires preconditioner = 1. */
+/* z = P^{-1} r with the context's preconditioner (Pre1 or Pre2) for slab size dt
+ * (canonical velocity layout, one shot, FP64, host pointers).  Requires preconditioner
+ * 1 or 2; with 2, the shots must be set (stdg_set_shots or a source / state call). */
 int stdg_apply_preconditioner(stdg_ctx* ctx, double dt, const double* r, double* z);
 
 /* Residual of the velocity system without allocating: r_dev = b_dev - A x_dev for slab

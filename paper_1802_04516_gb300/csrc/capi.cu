@@ -76,6 +76,13 @@ static int alloc_state(stdg_ctx* c, int n_shots) {
     if ((rc = dev_alloc(c, (void**)&c->d_energy, sizeof(double) * std::max(1, n_shots))) != STDG_OK) return rc;
     STDG_CUDA(c, cudaMemsetAsync(c->d_vtr, 0, sizeof(double) * c->ntr * n_shots, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(c->d_sigtr, 0, sizeof(double) * c->nsig * n_shots, c->stream));
+    if (c->opt.preconditioner == 2) {   // stencil preconditioner scratch: two stacked vectors
+        dev_free(c, c->d_p2y);
+        dev_free(c, c->d_p2t);
+        c->d_p2y = c->d_p2t = nullptr;
+        if ((rc = dev_alloc(c, &c->d_p2y, sizeof(double) * c->nvel * n_shots)) != STDG_OK) return rc;
+        if ((rc = dev_alloc(c, &c->d_p2t, sizeof(double) * c->nvel * n_shots)) != STDG_OK) return rc;
+    }
     c->n_shots = n_shots;
     c->rec_steps = 0;
     solver_invalidate_graph(c);
@@ -140,7 +147,38 @@ static int setup_pre1(stdg_ctx* c) {
         extern cudaError_t launch_cast32(stdg_ctx*, const double*, float*, int64_t);
         STDG_CUDA(c, launch_cast32(c, c->d_preV, c->d_preV32, nv));
     }
+    if (c->opt.preconditioner == 2) {
+        if (!pre2_supported(c)) STDG_FAIL(c, STDG_EINVAL, "stencil preconditioner: element block too large for this shape");
+        const int N = c->dim * c->Nphi * c->Ng;
+        const int64_t nS = ne * (int64_t)N * N;
+        if (!c->d_pre2) {
+            if ((rc = dev_alloc(c, (void**)&c->d_pre2, sizeof(double) * nS)) != STDG_OK) return rc;
+            if (c->opt.precision != STDG_FP64 &&
+                (rc = dev_alloc(c, (void**)&c->d_pre2_32, sizeof(float) * nS)) != STDG_OK) return rc;
+            if ((rc = dev_alloc(c, (void**)&c->d_p2status, sizeof(int))) != STDG_OK) return rc;
+        }
+    }
     c->pre_dt = -1.0;
+    return STDG_OK;
+}
+
+// Time blocks of the block-Jacobi preconditioner and, for the stencil preconditioner, the
+// local Schur-complement inverses, for slab size dt (rebuilt only when dt changes).
+int precond_for_dt(stdg_ctx* c, double dt) {
+    if (!c->opt.preconditioner || c->pre_dt == dt) return STDG_OK;
+    STDG_CUDA(c, launch_pre1_time(c, dt));
+    c->pre_dt = dt;
+    if (c->opt.preconditioner == 2) {
+        STDG_CUDA(c, cudaMemsetAsync(c->d_p2status, 0, sizeof(int), c->stream));
+        STDG_CUDA(c, launch_pre2_setup(c, dt, c->d_p2status));
+        int status = 0;
+        STDG_CUDA(c, cudaMemcpyAsync(&status, c->d_p2status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (status) {
+            c->pre_dt = -1.0;
+            STDG_FAIL(c, STDG_ECUDA, "stencil preconditioner: a local Schur complement is singular");
+        }
+    }
     return STDG_OK;
 }
 
@@ -163,6 +201,7 @@ int stdg_create(stdg_ctx** out, int dim, const stdg_options* opt, void* cuda_str
     if (opt->scheme != STDG_SCHEME_CN && opt->scheme != STDG_SCHEME_STDG) return STDG_EINVAL;
     if (opt->scheme == STDG_SCHEME_CN && opt->p_gamma != 0) return STDG_EINVAL;
     if (opt->precision != STDG_FP64 && opt->precision != STDG_MIXED_FP32) return STDG_EINVAL;
+    if (opt->preconditioner < 0 || opt->preconditioner > 2) return STDG_EINVAL;
     if (!(opt->rel_tol > 0.0) || opt->max_iters < 1) return STDG_EINVAL;
     stdg_ctx* c = new stdg_ctx();
     c->dim = dim;
@@ -623,16 +662,15 @@ int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z
     NEED_ALL(c);
     if (!c->opt.preconditioner || !c->d_preV) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
     if (!r || !z || !(dt > 0)) STDG_FAIL(c, STDG_EINVAL, "bad preconditioner arguments");
-    if (c->pre_dt != dt) {
-        STDG_CUDA(c, launch_pre1_time(c, dt));
-        c->pre_dt = dt;
-    }
+    int rc = precond_for_dt(c, dt);
+    if (rc != STDG_OK) return rc;
+    if (c->opt.preconditioner == 2 && !c->d_p2y) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_shots (or set a state) first");
     double *dr = nullptr, *dz = nullptr;
-    int rc;
     if ((rc = dev_alloc(c, (void**)&dr, sizeof(double) * c->nvel)) != STDG_OK) return rc;
     if ((rc = dev_alloc(c, (void**)&dz, sizeof(double) * c->nvel)) != STDG_OK) { dev_free(c, dr); return rc; }
     STDG_CUDA(c, cudaMemcpyAsync(dr, r, sizeof(double) * c->nvel, cudaMemcpyHostToDevice, c->stream));
-    STDG_CUDA(c, launch_pre1_apply(c, dr, dz, nullptr, 0));
+    if (c->opt.preconditioner == 2) STDG_CUDA(c, launch_pre2_apply(c, dr, dz, nullptr, 0, 1));
+    else STDG_CUDA(c, launch_pre1_apply(c, dr, dz, nullptr, 0));
     STDG_CUDA(c, cudaMemcpyAsync(z, dz, sizeof(double) * c->nvel, cudaMemcpyDeviceToHost, c->stream));
     STDG_CUDA(c, cudaStreamSynchronize(c->stream));
     dev_free(c, dr);

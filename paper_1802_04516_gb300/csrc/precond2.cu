@@ -1,0 +1,310 @@
+// Stencil preconditioner "Pre2" (Appendix A, Eqs. APPRE1 - APPRE2): for element i with
+// face neighbours e, the first block row of the inverse of the local system A_i formed
+// by i and its neighbours, applied to the stencil's values.
+//
+// In a simplex mesh no two face neighbours of an element share a face (that would need
+// a closed fan of three elements around an interior vertex in 2D, or around an interior
+// edge in 3D, which the meshes here do not contain), so A_i is an "arrow": D_i in the
+// corner, the couplings N_{i,e} and N_{e,i} in its first block row and column, and the
+// neighbours' own diagonal blocks D_e.  Block elimination of the neighbours gives the
+// first block row of A_i^{-1} in closed form:
+//   z_i = S_i^{-1} (r_i - sum_e N_{i,e} D_e^{-1} r_e),   S_i = D_i - sum_e N_{i,e} D_e^{-1} N_{e,i},
+// so one application is: y = P_1 r (the block-Jacobi apply), t = r - N y (the face term's
+// neighbour-to-neighbour part), z = S^{-1} t (one dense block per element).
+//
+// Set-up, per slab size dt, FP64, one CTA per element.  Every block has the Kronecker
+// form of the operator (space (x) time): D_i = M_i (x) T + c dt^2 K_ii (x) S and
+// N_{i,e} = c dt^2 K_ie (x) S, with K_ie the spatial face coupling of elements i and e
+// and K_ei = K_ie^T.  With D_e^{-1} = (V_e (x) I) blockdiag_q(B_{e,q}) (V_e^T (x) I) from
+// the block-Jacobi set-up,
+//   N_{i,e} D_e^{-1} N_{e,i} = (c dt^2)^2 sum_q (k_q k_q^T) (x) (S B_{e,q} S),  k_q = K_ie V_e[:, q],
+// which assembles S_i without any n^3 product; S_i (order d N_phi N_gamma) is then
+// inverted by Gauss-Jordan elimination with partial pivoting and stored column-major.
+#include <algorithm>
+#include <cmath>
+
+#include "stdg_internal.h"
+
+namespace stdg {
+
+constexpr int kP2Threads = 256;
+constexpr int kP2MaxRows = 4;                 // rows per lane in the apply: N <= 128
+
+// K^{(j)}[(k,n),(k',n')] += lam P(k,k') + mu P(k',k) + delta_kk' mu sum_l P(l,l),
+// P(a,b)[n][n'] = sum_m Da[a][n][m] Db[b][n'][m]   (Da: row element's D~, Db: column element's)
+__device__ void add_face_coupling(double* K, int n, int dim, int NP, const double* Da, const double* Db, double lam,
+                                  double mu, double scale) {
+    for (int ent = threadIdx.x; ent < n * n; ent += blockDim.x) {
+        const int r = ent / n, c = ent % n;
+        const int k = r / NP, nn = r % NP, k2 = c / NP, n2 = c % NP;
+        auto P = [&](int a, int b) {
+            const double* x = Da + (a * NP + nn) * NP;
+            const double* y = Db + (b * NP + n2) * NP;
+            double s = 0;
+            for (int m = 0; m < NP; ++m) s += x[m] * y[m];
+            return s;
+        };
+        double v = lam * P(k, k2) + mu * P(k2, k);
+        if (k == k2)
+            for (int l = 0; l < dim; ++l) v += mu * P(l, l);
+        K[ent] += scale * v;
+    }
+}
+
+// smem: A (N x 2N augmented), K (n x n), kv (n x n), W (n x NG x NG), Da, Db (dim NP NP each), f (N)
+__global__ void __launch_bounds__(kP2Threads) pre2_setup_kernel(
+    int64_t n_elem, int dim, const RefTables* __restrict__ rtp, const int32_t* __restrict__ elem_face,
+    const int32_t* __restrict__ face_l, const int32_t* __restrict__ face_r, const double* __restrict__ D,
+    const double* __restrict__ lamf, const double* __restrict__ muf, const double* __restrict__ rhoJ,
+    const double* __restrict__ preV, const double* __restrict__ preB, double cdt2, double* __restrict__ out64,
+    float* __restrict__ out32, int* __restrict__ status) {
+    extern __shared__ double sm[];
+    const int NP = rtp->Nphi, NG = rtp->Ng;
+    const int n = dim * NP;
+    const int N = n * NG;
+    const int ldA = 2 * N;
+    double* A = sm;                         // N x 2N
+    double* K = A + (size_t)N * ldA;        // n x n
+    double* kv = K + n * n;                 // n x n: kv[s][q] = (K_ie V_e)[s][q]
+    double* W = kv + n * n;                 // n x NG x NG: S B_q S
+    double* Da = W + n * NG * NG;
+    double* Db = Da + dim * NP * NP;
+    double* f = Db + dim * NP * NP;         // N
+    __shared__ int s_piv;
+    __shared__ int s_sing;
+    const int tid = threadIdx.x;
+    auto row_of = [&](int s, int a) { return ((s / NP) * NG + a) * NP + s % NP; };   // [k][a][n] layout
+    for (int64_t e = blockIdx.x; e < n_elem; e += gridDim.x) {
+        // ---- D_i: rho|J| (I (x) M_ref) (x) T + c dt^2 K_ii (x) S, and [ . | I ]
+        for (int t = tid; t < n * n; t += blockDim.x) K[t] = 0.0;
+        __syncthreads();
+        for (int fi = 0; fi <= dim; ++fi) {
+            const int j = elem_face[e * (dim + 1) + fi];
+            const int side = face_l[j] == (int)e ? 0 : 1;
+            const double* Dg = D + ((int64_t)j * 2 + side) * dim * NP * NP;
+            for (int t = tid; t < dim * NP * NP; t += blockDim.x) Da[t] = Dg[t];
+            __syncthreads();
+            add_face_coupling(K, n, dim, NP, Da, Da, lamf[j], muf[j], 1.0);
+            __syncthreads();
+        }
+        const double rj = rhoJ[e];
+        for (int ent = tid; ent < N * N; ent += blockDim.x) {
+            const int R = ent / N, C = ent % N;
+            const int k = R / (NG * NP), a = (R / NP) % NG, nn = R % NP;
+            const int k2 = C / (NG * NP), a2 = (C / NP) % NG, n2 = C % NP;
+            double v = cdt2 * K[(k * NP + nn) * n + k2 * NP + n2] * rtp->S[a * NG + a2];
+            if (k == k2) v += rj * rtp->Mref[nn * NP + n2] * rtp->T[a * NG + a2];
+            A[R * ldA + C] = v;
+            A[R * ldA + N + C] = R == C ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        // ---- minus N_{i,e} D_e^{-1} N_{e,i} for every face neighbour e
+        for (int fi = 0; fi <= dim; ++fi) {
+            const int j = elem_face[e * (dim + 1) + fi];
+            const int l = face_l[j], r = face_r[j];
+            if (r < 0) continue;
+            const int side = l == (int)e ? 0 : 1;
+            const int64_t nb = side == 0 ? r : l;
+            if (nb == e) continue;          // a periodic self-neighbour is part of D_i already
+            const double* Dg = D + (int64_t)j * 2 * dim * NP * NP;
+            for (int t = tid; t < dim * NP * NP; t += blockDim.x) {
+                Da[t] = Dg[side * dim * NP * NP + t];
+                Db[t] = Dg[(1 - side) * dim * NP * NP + t];
+            }
+            for (int t = tid; t < n * n; t += blockDim.x) K[t] = 0.0;
+            __syncthreads();
+            add_face_coupling(K, n, dim, NP, Da, Db, lamf[j], muf[j], 1.0);   // K_ie
+            __syncthreads();
+            const double* Ve = preV + nb * (int64_t)n * n;
+            for (int ent = tid; ent < n * n; ent += blockDim.x) {
+                const int s = ent / n, q = ent % n;
+                double acc = 0;
+                for (int s2 = 0; s2 < n; ++s2) acc += K[s * n + s2] * Ve[s2 * n + q];
+                kv[ent] = acc;
+            }
+            const double* Be = preB + nb * (int64_t)n * NG * NG;
+            for (int ent = tid; ent < n * NG * NG; ent += blockDim.x) {
+                const int q = ent / (NG * NG), a = (ent / NG) % NG, a2 = ent % NG;
+                double acc = 0;
+                for (int b = 0; b < NG; ++b)
+                    for (int b2 = 0; b2 < NG; ++b2)
+                        acc += rtp->S[a * NG + b] * Be[q * NG * NG + b * NG + b2] * rtp->S[b2 * NG + a2];
+                W[ent] = acc;
+            }
+            __syncthreads();
+            const double c2 = cdt2 * cdt2;
+            for (int ent = tid; ent < N * N; ent += blockDim.x) {
+                const int R = ent / N, C = ent % N;
+                const int k = R / (NG * NP), a = (R / NP) % NG, nn = R % NP;
+                const int k2 = C / (NG * NP), a2 = (C / NP) % NG, n2 = C % NP;
+                const double* k1 = kv + (k * NP + nn) * n;
+                const double* kk2 = kv + (k2 * NP + n2) * n;
+                double acc = 0;
+                for (int q = 0; q < n; ++q) acc += k1[q] * kk2[q] * W[(q * NG + a) * NG + a2];
+                A[R * ldA + C] -= c2 * acc;
+            }
+            __syncthreads();
+        }
+        // ---- Gauss-Jordan on [S_i | I] with partial pivoting
+        if (tid == 0) s_sing = 0;
+        for (int col = 0; col < N; ++col) {
+            if (tid == 0) {
+                int p = col;
+                double best = fabs(A[col * ldA + col]);
+                for (int rr = col + 1; rr < N; ++rr) {
+                    const double v = fabs(A[rr * ldA + col]);
+                    if (v > best) { best = v; p = rr; }
+                }
+                s_piv = p;
+                if (!(best > 0.0)) s_sing = 1;
+            }
+            __syncthreads();
+            if (s_sing) break;
+            const int p = s_piv;
+            if (p != col)
+                for (int t = tid; t < ldA; t += blockDim.x) {
+                    const double u = A[col * ldA + t];
+                    A[col * ldA + t] = A[p * ldA + t];
+                    A[p * ldA + t] = u;
+                }
+            __syncthreads();
+            const double inv = 1.0 / A[col * ldA + col];
+            __syncthreads();
+            for (int t = tid; t < ldA; t += blockDim.x) A[col * ldA + t] *= inv;
+            for (int t = tid; t < N; t += blockDim.x) f[t] = A[t * ldA + col];
+            __syncthreads();
+            for (int ent = tid; ent < N * ldA; ent += blockDim.x) {
+                const int rr = ent / ldA, cc = ent % ldA;
+                if (rr != col && cc >= col) A[ent] -= f[rr] * A[col * ldA + cc];
+            }
+            __syncthreads();
+        }
+        if (s_sing && tid == 0) atomicExch(status, 1);
+        // ---- store S_i^{-1} column-major: out[e][C][R]
+        for (int ent = tid; ent < N * N; ent += blockDim.x) {
+            const int C = ent / N, R = ent % N;
+            const double v = A[R * ldA + N + C];
+            if (out64) out64[e * (int64_t)N * N + ent] = v;
+            if (out32) out32[e * (int64_t)N * N + ent] = (float)v;
+        }
+        __syncthreads();
+    }
+}
+
+// z_e = S_e^{-1} t_e, one warp per element; lane holds rows lane + 32 i, columns of S^{-1}
+// (contiguous) are streamed once per group of SG shots.
+template <typename R, int SG>
+__global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, const R* __restrict__ Sinv,
+                                                         const R* __restrict__ t, R* __restrict__ z, int nshots,
+                                                         int64_t nvec) {
+    extern __shared__ unsigned char smraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    R* st = reinterpret_cast<R*>(smraw) + (size_t)warp * SG * N;
+    for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
+        const R* Se = Sinv + e * (int64_t)N * N;
+        for (int s0 = 0; s0 < nshots; s0 += SG) {
+            const int sg = min(SG, nshots - s0);
+            for (int q = lane; q < SG * N; q += 32) {
+                const int g = q / N, c = q % N;
+                st[q] = g < sg ? t[(int64_t)(s0 + g) * nvec + e * N + c] : (R)0;
+            }
+            __syncwarp();
+            R acc[kP2MaxRows][SG];
+#pragma unroll
+            for (int i = 0; i < kP2MaxRows; ++i)
+#pragma unroll
+                for (int g = 0; g < SG; ++g) acc[i][g] = 0;
+            for (int c = 0; c < N; ++c) {
+                const R* col = Se + (int64_t)c * N;
+#pragma unroll
+                for (int i = 0; i < kP2MaxRows; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r < N) {
+                        const R a = col[r];
+#pragma unroll
+                        for (int g = 0; g < SG; ++g) acc[i][g] = fma(a, st[g * N + c], acc[i][g]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kP2MaxRows; ++i) {
+                const int r = lane + 32 * i;
+                if (r < N)
+#pragma unroll
+                    for (int g = 0; g < SG; ++g)
+                        if (g < sg) z[(int64_t)(s0 + g) * nvec + e * N + r] = acc[i][g];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// out = x (+ column *xidx at stride ld)
+template <typename R>
+__global__ void copy_col_kernel(int64_t n, const R* __restrict__ x, const int* __restrict__ xidx, int64_t ld,
+                                R* __restrict__ out) {
+    if (xidx) x += (int64_t)(*xidx) * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i];
+}
+
+static size_t pre2_setup_smem(int dim, int NP, int NG) {
+    const int n = dim * NP, N = n * NG;
+    return sizeof(double) * ((size_t)N * 2 * N + 2 * (size_t)n * n + (size_t)n * NG * NG + 2 * (size_t)dim * NP * NP + N);
+}
+
+bool pre2_supported(const stdg_ctx* c) {
+    const int N = c->dim * c->Nphi * c->Ng;
+    return N <= 32 * kP2MaxRows && pre2_setup_smem(c->dim, c->Nphi, c->Ng) <= 227 * 1024;
+}
+
+cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status) {
+    const double cfac = c->opt.scheme == STDG_SCHEME_CN ? 0.25 : 1.0;
+    const size_t smem = pre2_setup_smem(c->dim, c->Nphi, c->Ng);
+    cudaFuncSetAttribute(pre2_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = (int)std::min<int64_t>(c->n_elem, 152 * 8);
+    pre2_setup_kernel<<<grid, kP2Threads, smem, c->stream>>>(c->n_elem, c->dim, c->d_rt, c->d_elem_face, c->d_face_l,
+                                                             c->d_face_r, c->d_D, c->d_lamf, c->d_muf, c->d_rhoJ, c->d_preV,
+                                                             c->d_preB, cfac * dt * dt, c->d_pre2, c->d_pre2_32, d_status);
+    note_launch(c);
+    return cudaGetLastError();
+}
+
+// z = P_2 r for nshots stacked shots: y = P_1 r, t = r - N y, z = S^{-1} t
+template <typename R>
+static cudaError_t pre2_apply_t(stdg_ctx* c, const R* Sinv, const R* r, R* z, const int* ridx, int64_t ld, int nshots,
+                                bool fp32) {
+    const int64_t n = c->nvel * (int64_t)nshots;
+    R* y = reinterpret_cast<R*>(c->d_p2y);
+    R* t = reinterpret_cast<R*>(c->d_p2t);
+    cudaError_t e;
+    if (fp32) e = launch_pre1_apply32(c, (const float*)r, (float*)y, ridx, ld, nshots);
+    else e = launch_pre1_apply(c, (const double*)r, (double*)y, ridx, ld, nshots);
+    if (e != cudaSuccess) return e;
+    copy_col_kernel<R><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, c->stream>>>(n, r, ridx, ld, t);
+    note_launch(c);
+    const double cfac = c->opt.scheme == STDG_SCHEME_CN ? 0.25 : 1.0;
+    if ((e = launch_face_cross(c, -cfac * c->pre_dt * c->pre_dt, y, t, fp32 ? 1 : 0, nshots)) != cudaSuccess) return e;
+    const int N = c->dim * c->Nphi * c->Ng;
+    const int wpb = 4;
+    const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
+    if (nshots == 1) {
+        pre2_local_kernel<R, 1><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * N, c->stream>>>(c->n_elem, N, Sinv, t, z,
+                                                                                             nshots, c->nvel);
+    } else {
+        pre2_local_kernel<R, 4><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * 4 * N, c->stream>>>(c->n_elem, N, Sinv, t,
+                                                                                                 z, nshots, c->nvel);
+    }
+    note_launch(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots) {
+    return pre2_apply_t<double>(c, c->d_pre2, r, z, ridx, ld, nshots, false);
+}
+
+cudaError_t launch_pre2_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots) {
+    return pre2_apply_t<float>(c, c->d_pre2_32, r, z, ridx, ld, nshots, true);
+}
+
+}  // namespace stdg

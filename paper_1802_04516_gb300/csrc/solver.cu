@@ -1013,15 +1013,21 @@ static void record_solve(Flow& F, double dt, double* b, double* x) {
     const int64_t nv = ws->nvec;
     const int ns = ws->ns, G = (int)ws->G;
     const dim3 grid = ws->grid();
-    const bool cn = c->opt.scheme == STDG_SCHEME_CN;
+    // CG for the SPD Crank-Nicolson system unless the preconditioner is the (non-symmetric) stencil one
+    const bool cn = c->opt.scheme == STDG_SCHEME_CN && c->opt.preconditioner != 2;
     const bool pre = c->opt.preconditioner != 0;
+    const bool p2 = c->opt.preconditioner == 2;
     const int64_t ldv = ws->ldv;
     auto A64 = [&](const double* xx, double* yy) { return launch_apply(c, dt, xx, yy, 1.0, nullptr, 0, ns); };
     auto A64i = [&](const double* V, const int* idx, double* yy) { return launch_apply(c, dt, V, yy, 1.0, idx, ldv, ns); };
     auto A32 = [&](const float* xx, float* yy) { return launch_apply32(c, dt, xx, yy, 1.0, nullptr, 0, ns); };
     auto A32i = [&](const float* V, const int* idx, float* yy) { return launch_apply32(c, dt, V, yy, 1.0, idx, ldv, ns); };
-    auto P64 = [&](const double* r, double* z, const int* idx, int64_t ld) { return launch_pre1_apply(c, r, z, idx, ld, ns); };
-    auto P32 = [&](const float* r, float* z, const int* idx, int64_t ld) { return launch_pre1_apply32(c, r, z, idx, ld, ns); };
+    auto P64 = [&](const double* r, double* z, const int* idx, int64_t ld) {
+        return p2 ? launch_pre2_apply(c, r, z, idx, ld, ns) : launch_pre1_apply(c, r, z, idx, ld, ns);
+    };
+    auto P32 = [&](const float* r, float* z, const int* idx, int64_t ld) {
+        return p2 ? launch_pre2_apply32(c, r, z, idx, ld, ns) : launch_pre1_apply32(c, r, z, idx, ld, ns);
+    };
     auto P64c = [&](const double* r, double* z) { return launch_pre1_apply(c, r, z, nullptr, 0, ns); };
     auto P32c = [&](const float* r, float* z) { return launch_pre1_apply32(c, r, z, nullptr, 0, ns); };
     const double tol = c->opt.rel_tol;
@@ -1093,7 +1099,7 @@ int solver_setup(stdg_ctx* c) {
     ws->n = c->nvel * (int64_t)c->n_shots;
     ws->G = (unsigned)std::max(1, kRedBlocks / ws->ns);
     const int64_t n = ws->n;
-    const bool cn = c->opt.scheme == STDG_SCHEME_CN;
+    const bool cn = c->opt.scheme == STDG_SCHEME_CN && c->opt.preconditioner != 2;   // CG workspace
     const bool mixed = c->opt.precision != STDG_FP64;
     const bool pre = c->opt.preconditioner != 0;
     int rc;
@@ -1158,9 +1164,9 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_total, 0, sizeof(int) * 4, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_final_rel, 0, sizeof(double) * 2, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->launches, 0, sizeof(unsigned long long), c->stream));
-    if (c->opt.preconditioner && c->pre_dt != dt) {
-        STDG_CUDA(c, launch_pre1_time(c, dt));
-        c->pre_dt = dt;
+    {
+        const int rc = precond_for_dt(c, dt);
+        if (rc != STDG_OK) return rc;
     }
     const double t0 = c->t;
     STDG_CUDA(c, cudaMemcpyAsync(ws->dparams, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream));

@@ -129,6 +129,11 @@ struct stdg_ctx {
     float *d_preV32 = nullptr, *d_preB32 = nullptr;
     int32_t* d_elem_face = nullptr;
     double pre_dt = -1.0;    // slab size the time blocks d_preB were built for
+    // ---- stencil preconditioner (precond2.cu): S_i^{-1} per element, column-major
+    double* d_pre2 = nullptr;
+    float* d_pre2_32 = nullptr;
+    void *d_p2y = nullptr, *d_p2t = nullptr;   // two stacked velocity vectors (FP64-sized)
+    int* d_p2status = nullptr;
 
     // ---- device error word: set by kernels whose bounded waits ran out (checked after each call)
     int* d_err = nullptr;
@@ -193,6 +198,16 @@ cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* 
 cudaError_t launch_pre1_time(stdg_ctx* c, double dt);
 cudaError_t launch_pre1_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
 cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots = 1);
+
+// precond2.cu
+bool pre2_supported(const stdg_ctx* c);
+cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status);
+cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
+cudaError_t launch_pre2_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots = 1);
+// kernels.cu: off-diagonal face coupling, t += scale * N y
+cudaError_t launch_face_cross(stdg_ctx* c, double scale, const void* y, void* t, int fp32, int nshots);
+// (re)build the dt-dependent preconditioner blocks when dt changes (capi.cu)
+int precond_for_dt(stdg_ctx* c, double dt);
 
 // solver.cu
 int solver_setup(stdg_ctx* c);

@@ -273,3 +273,72 @@ def test_ragged_union_matches_oracle_per_part(precision, tol, rel_tol):
         assert stress_field_rel(sig[f0:f0 + nf], sim.sig_tr, sim.disc) < tol
         f0 += nf
     assert f0 == sig.shape[0]
+
+
+PRE2_CASES = [OP_CASES[i] for i in (0, 2, 3, 4)]
+
+
+@pytest.mark.parametrize("name,make", PRE2_CASES, ids=[c[0] for c in PRE2_CASES])
+def test_stencil_preconditioner_matches_oracle(name, make):
+    # Pre2 (Appendix A, Eqs. APPRE1-APPRE2): the GPU forms the first block row of the local
+    # inverse by block elimination of the neighbours; the oracle inverts the local system
+    from oracle.precond import pre2
+    need_gpu()
+    w = make()
+    sim = oracle_sim(w)
+    s = gpu_solver(w, with_sources=False, with_receivers=False, preconditioner=2)
+    s.set_shots(1)
+    r = np.random.default_rng(11).normal(size=sim.A.shape[0])
+    z = s.apply_preconditioner(w.dt, r)
+    zo = pre2(sim.A, w.n_elem, sim.mesh.elem_nbr) @ r
+    err = rel_l2(z, zo)
+    print(name, "pre2 rel diff", err)
+    assert err < max(1e-9, 1e4 * oracle_rounding_spread(sim, w)), err
+
+
+@pytest.mark.parametrize("precision,tol,rel_tol", [("fp64", 1e-10, 1e-13), ("mixed", 1e-8, 1e-12)])
+def test_stencil_preconditioned_steps_match_oracle(precision, tol, rel_tol):
+    # scaled sliver mesh, p = 2: same states as the oracle, in far fewer iterations than Pre1
+    need_gpu()
+    w = synth.scaled("c2", ny=10, steps=3, p=2)
+    st = {}
+    for pre in (1, 2):
+        s = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000, preconditioner=pre)
+        st[pre] = s.step(w.dt, 3)
+        assert st[pre]["status"] == 0
+        if pre == 2:
+            v, sig = s.get_state()
+    sim = oracle_sim(w)
+    sim.set_source(w.shots_xs[0], w.shots_dir[0], w.f0, w.t_delay, w.a1)
+    sim.step(3)
+    assert rel_l2(v, sim.v_tr) < tol
+    assert stress_field_rel(sig, sim.sig_tr, sim.disc) < tol
+    print(precision, "iterations pre1", st[1]["iters_max"], "pre2", st[2]["iters_max"])
+    assert st[2]["iters_max"] * 2 <= st[1]["iters_max"]
+
+
+def test_stencil_preconditioner_crank_nicolson_runs_gmres():
+    # Pre2 is not symmetric: the Crank-Nicolson system is then solved by GMRES
+    need_gpu()
+    w = synth.c1_periodic_pwave(n=8, p=2, steps=3)
+    s = gpu_solver(w, rel_tol=1e-13, max_iters=20000, preconditioner=2)
+    assert s.step(w.dt, 3)["status"] == 0
+    v, sig = s.get_state()
+    sim = oracle_sim(w)
+    sim.step(3)
+    assert rel_l2(v, sim.v_tr) < 1e-10
+    assert stress_field_rel(sig, sim.sig_tr, sim.disc) < 1e-10
+
+
+def test_stencil_preconditioned_multishot_matches_oracle():
+    need_gpu()
+    w = synth.scaled("c4", ny=8, steps=2, n_shots=3)
+    s = gpu_solver(w, precision="mixed", rel_tol=1e-12, max_iters=20000, preconditioner=2)
+    assert s.step(w.dt, 2)["status"] == 0
+    for k in range(3):
+        sim = oracle_sim(w)
+        sim.set_source(w.shots_xs[k], w.shots_dir[k], w.f0, w.t_delay, w.a1)
+        sim.step(2)
+        v, sig = s.get_state(k)
+        assert rel_l2(v, sim.v_tr) < 1e-8
+        assert stress_field_rel(sig, sim.sig_tr, sim.disc) < 1e-8
