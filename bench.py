@@ -5,7 +5,8 @@ Workload: the 2D layered medium on [0,2]x[0,1] with 448x224x2 = 200,704 jittered
 triangles, 1% slivers, free surface, p = p_gamma = 3, one Ricker point source, 16
 receivers, dt at 10x the explicit CFL.  One "step" is one space-time slab of the whole
 path: right-hand side, the preconditioned Krylov solve of the Schur velocity system to
-1e-8 relative residual, stress back-substitution, traces and receivers.
+1e-8 relative residual (stencil preconditioner Pre2 by default, --pre), stress
+back-substitution, traces and receivers.
 
 Metric: space-time DOF-steps/s = (velocity + stress space-time DOFs per slab) x steps x
 shots / time.  `value` is the mixed-precision path (FP32 operator and Krylov, FP64
@@ -103,10 +104,10 @@ def peaks():
         return {}
 
 
-def build_solver(w, precision, stream, shot_offset=0.0, restart=10, inner_tol=1e-2, use_graph=True):
+def build_solver(w, precision, stream, shot_offset=0.0, restart=10, inner_tol=1e-2, use_graph=True, pre=2):
     from paper_1802_04516_gb300.binding import Solver
     s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=restart,
-               inner_tol=inner_tol, use_graph=use_graph, stream=stream, preconditioner=1)
+               inner_tol=inner_tol, use_graph=use_graph, stream=stream, preconditioner=pre)
     s.set_mesh(w.xyz, w.elem_vert, w.period)
     s.set_material(w.lam, w.mu, w.rho)
     if w.shots_xs is not None:
@@ -204,14 +205,14 @@ def multishot_section(torch, args, stream, dist, world):
     import synth
     w = synth.c4_multishot(ny=args.ny, n_shots=args.shots, steps=args.ms_steps)
     s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
-                     use_graph=not args.host_loop)
+                     use_graph=not args.host_loop, pre=args.pre)
     n_face = s.n_face
     ms, iters, launches, st = time_steps(torch, s, w, args.ms_steps, 1, stream, dist)
     s.close()
     dofs_shot = dofs_per_slab(w, n_face)
     w1 = synth.c4_multishot(ny=args.ny, n_shots=1, steps=args.ms_steps)
     w1.shots_xs, w1.shots_dir = w.shots_xs[:1], w.shots_dir[:1]
-    s1 = build_solver(w1, "fp64", stream.cuda_stream, restart=args.restart, use_graph=not args.host_loop)
+    s1 = build_solver(w1, "fp64", stream.cuda_stream, restart=args.restart, use_graph=not args.host_loop, pre=args.pre)
     ms1, it1, _, _ = time_steps(torch, s1, w1, args.ms_steps, 1, stream, dist)
     s1.close()
     multi = world * w.n_shots * args.ms_steps / (ms * 1e-3)
@@ -232,7 +233,7 @@ def ragged_section(torch, args, stream, dist, world):
     import synth
     w, spans = synth.ragged_union(steps=args.ms_steps)
     s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
-                     use_graph=not args.host_loop)
+                     use_graph=not args.host_loop, pre=args.pre)
     n_face = s.n_face
     ms, iters, launches, st = time_steps(torch, s, w, args.ms_steps, 1, stream, dist)
     s.close()
@@ -243,6 +244,32 @@ def ragged_section(torch, args, stream, dist, world):
             "mesh_steps_per_s": world * len(spans) * args.ms_steps / (ms * 1e-3),
             "ms_per_step": ms / args.ms_steps, "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"],
             "gpu_launches": launches, "steps": args.ms_steps}
+
+
+def pre2_local_roofline(s, w, pk):
+    """Element-local step of the stencil preconditioner, z = S^{-1} (2 r - w) in FP32: one
+    dense (d N_phi N_gamma)^2 block per element streamed from HBM, plus r, w read and z written."""
+    from math import comb
+    nphi = comb(w.p + w.dim, w.dim)
+    N = w.dim * nphi * (w.p_gamma + 1)
+    nvel = w.n_elem * N
+    bytes_alg = w.n_elem * N * N * 4 + 3 * nvel * 4
+    ms = s.time_kernel(w.dt, 2, fp32=True, n=20)
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    achieved = bytes_alg / (ms * 1e-3) / 1e9
+    return {"kernel": "pre2_local_kernel<float,1>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(2 * w.n_elem * N * N),
+            "ms_per_launch": round(ms, 4), "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
+
+
+def dominant_roofline(cands, per_iter):
+    """The candidate with the largest device time per Krylov iteration (ms per launch x
+    launches per iteration); all candidates are reported under "kernels"."""
+    best = max(cands, key=lambda k: cands[k]["ms_per_launch"] * per_iter[k])
+    out = dict(cands[best])
+    out["launches_per_krylov_iteration"] = per_iter[best]
+    return out
 
 
 def cpu_baseline(max_seconds=25.0, ny=12, steps=20):
@@ -295,6 +322,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--restart", type=int, default=10, help="GMRES restart length")
     ap.add_argument("--inner-tol", type=float, default=1e-2, help="relative tolerance of the FP32 inner solve")
+    ap.add_argument("--pre", type=int, default=2, choices=[0, 1, 2],
+                    help="preconditioner: 0 none, 1 block Jacobi (Pre1), 2 stencil (Pre2)")
     ap.add_argument("--shots", type=int, default=64, help="shots of the multi-shot batch")
     ap.add_argument("--ms-steps", type=int, default=2, help="timed slabs of the multi-shot and ragged batches")
     ap.add_argument("--no-multishot", action="store_true")
@@ -326,7 +355,7 @@ def main():
     pk = peaks()
     with torch.cuda.stream(stream):
         s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=0.01 * rank, restart=args.restart,
-                         inner_tol=args.inner_tol, use_graph=not args.host_loop)
+                         inner_tol=args.inner_tol, use_graph=not args.host_loop, pre=args.pre)
         n_face = s.n_face
         dofs = dofs_per_slab(w, n_face)
         sampler = ClockSampler(local)
@@ -334,13 +363,18 @@ def main():
         ms, iters, launches, st = time_steps(torch, s, w, args.steps, args.warmup, stream, dist)
         clocks = sampler.stop()
         value = world * dofs * args.steps / (ms * 1e-3)
-        roof = face_kernel_roofline(s, w, True, n_face, pk)
+        cands = {"face": face_kernel_roofline(s, w, True, n_face, pk)}
+        per_iter = {"face": 2 if args.pre == 2 else 1}   # the Krylov operator, plus one inside Pre2
+        if args.pre == 2:
+            cands["pre2_local"] = pre2_local_roofline(s, w, pk)
+            per_iter["pre2_local"] = 1
+        roof = dominant_roofline(cands, per_iter)
         e2e_ms, h2d, d2h = e2e_steps(torch, s, w, max(1, args.steps // 2), stream)
         e2e_value = dofs * max(1, args.steps // 2) / (e2e_ms * 1e-3) * world
         fp64 = None
         if not args.no_fp64 and args.fp64_steps > 0:
             s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=0.01 * rank, restart=args.restart,
-                               use_graph=not args.host_loop)
+                               use_graph=not args.host_loop, pre=args.pre)
             ms64, it64, _, _ = time_steps(torch, s64, w, args.fp64_steps, 1, stream, dist)
             fp64 = {"value": world * dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
                     "krylov_iters_per_step": it64, "roofline": face_kernel_roofline(s64, w, False, n_face, pk)}
@@ -358,7 +392,8 @@ def main():
         "dtype": "f32 operator/Krylov + f64 refinement", "data": "synthetic",
         "config": {"workload": "c2_layered_slivers_p3: %d triangles (448x224x2, 1%% slivers), p=p_gamma=3, "
                                "1 Ricker shot/GPU, 16 receivers, dt=%.4g (10x CFL)" % (w.n_elem, w.dt),
-                   "dofs_per_slab": dofs, "n_face": n_face, "preconditioner": "block Jacobi (Pre1)",
+                   "dofs_per_slab": dofs, "n_face": n_face,
+                   "preconditioner": {0: "none", 1: "block Jacobi (Pre1)", 2: "stencil (Pre2)"}[args.pre],
                    "gmres_restart": args.restart, "inner_tol": args.inner_tol,
                    "control": "host loop" if args.host_loop else "CUDA graph per step (device while loops)", "l2": "working set (blocks, Krylov basis) > 129 MB L2; no flush",
                    "parallelism": "independent shot per GPU"},
@@ -366,6 +401,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roof,
+        "kernels": cands,
         "e2e": {"value": e2e_value, "unit": "DOF-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "fp64": fp64,
         "multishot": multishot,

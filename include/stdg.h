@@ -187,6 +187,15 @@ int stdg_residual_noalloc(stdg_ctx* ctx, double dt, const double* x_dev, const d
  * FP32 one) on the context stream, measured with CUDA events: *ms_out. */
 int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out);
 
+/* Average device time of one launch of a single kernel, over n back-to-back launches on
+ * the context's stream (CUDA events), for roofline figures.  which: 0 face term of the
+ * operator (as stdg_time_operator), 1 block-Jacobi apply, 2 the element-local step of the
+ * stencil preconditioner (z = S^{-1} (2 r - w)), 3 the whole operator (mass + face).
+ * fp32 selects the FP32 blocks (mixed-precision contexts only for 1 and 2).  Timing only:
+ * the kernels run on zero vectors in buffers allocated for the call.  No counterpart in
+ * the paper. */
+int stdg_time_kernel(stdg_ctx* ctx, double dt, int which, int fp32, int n, double* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

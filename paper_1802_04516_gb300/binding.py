@@ -59,6 +59,7 @@ SIGNATURES = {
     "stdg_query": (C.c_int, [_P, C.c_int, _I64]),
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
+    "stdg_time_kernel": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
     "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_residual_noalloc": (C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
 }
@@ -243,6 +244,12 @@ class Solver:
         fr = np.zeros(self.n_face, dtype=np.int32)
         self._chk(self.lib.stdg_get_faces(self.h, fl.ctypes.data_as(_I32), fr.ctypes.data_as(_I32)))
         return fl, fr
+
+    def time_kernel(self, dt, which, fp32=False, n=20):
+        """Average ms of one launch: which 0 face term, 1 block Jacobi, 2 stencil local step, 3 operator."""
+        ms = C.c_double(0.0)
+        self._chk(self.lib.stdg_time_kernel(self.h, dt, int(which), 1 if fp32 else 0, n, C.byref(ms)))
+        return ms.value
 
     def time_operator(self, dt, fp32=False, n=20):
         ms = C.c_double()

@@ -678,25 +678,44 @@ int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z
     return STDG_OK;
 }
 
-int stdg_time_operator(stdg_ctx* c, double dt, int fp32, int n, double* ms_out) {
+int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double* ms_out) {
     CHECK_CTX(c);
     NEED_ALL(c);
-    if (n < 1 || !ms_out) STDG_FAIL(c, STDG_EINVAL, "bad timing arguments");
+    if (n < 1 || !ms_out || which < 0 || which > 3) STDG_FAIL(c, STDG_EINVAL, "bad timing arguments");
+    if (which == 1 && !c->opt.preconditioner) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
+    if (which == 2 && c->opt.preconditioner != 2) STDG_FAIL(c, STDG_ESTATE, "context created without the stencil preconditioner");
+    if (which == 2 && fp32 && !c->d_pre2_32) STDG_FAIL(c, STDG_ESTATE, "FP32 stencil blocks exist only in mixed precision");
+    if (which == 1 && fp32 && !c->d_preV32) STDG_FAIL(c, STDG_ESTATE, "FP32 block-Jacobi blocks exist only in mixed precision");
     int rc;
     if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
     if (fp32 && (rc = upload_material32(c)) != STDG_OK) return rc;
-    void *dx = nullptr, *dy = nullptr;
+    if (which == 1 || which == 2) {
+        if ((rc = precond_for_dt(c, dt)) != STDG_OK) return rc;
+    }
+    void *dx = nullptr, *dy = nullptr, *dw = nullptr;
     const size_t bytes = (fp32 ? sizeof(float) : sizeof(double)) * c->nvel;
     if ((rc = dev_alloc(c, &dx, bytes)) != STDG_OK) return rc;
     if ((rc = dev_alloc(c, &dy, bytes)) != STDG_OK) { dev_free(c, dx); return rc; }
+    if ((rc = dev_alloc(c, &dw, bytes)) != STDG_OK) { dev_free(c, dx); dev_free(c, dy); return rc; }
     STDG_CUDA(c, cudaMemsetAsync(dx, 0, bytes, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(dy, 0, bytes, c->stream));
-    STDG_CUDA(c, launch_face_only(c, dt, dx, dy, 1.0, fp32));   // warm-up
+    STDG_CUDA(c, cudaMemsetAsync(dw, 0, bytes, c->stream));
+    auto launch = [&]() -> cudaError_t {
+        switch (which) {
+            case 0: return launch_face_only(c, dt, dx, dy, 1.0, fp32);
+            case 1: return fp32 ? launch_pre1_apply32(c, (const float*)dx, (float*)dy, nullptr, 0)
+                                : launch_pre1_apply(c, (const double*)dx, (double*)dy, nullptr, 0);
+            case 2: return launch_pre2_local(c, fp32, dx, dw, dy);
+            default: return fp32 ? launch_apply32(c, dt, (const float*)dx, (float*)dy, 1.0, nullptr, 0, 1)
+                                 : launch_apply(c, dt, (const double*)dx, (double*)dy, 1.0, nullptr, 0, 1);
+        }
+    };
+    STDG_CUDA(c, launch());   // warm-up
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, c->stream);
-    for (int i = 0; i < n; ++i) STDG_CUDA(c, launch_face_only(c, dt, dx, dy, 1.0, fp32));
+    for (int i = 0; i < n; ++i) STDG_CUDA(c, launch());
     cudaEventRecord(e1, c->stream);
     STDG_CUDA(c, cudaEventSynchronize(e1));
     float ms = 0;
@@ -706,7 +725,12 @@ int stdg_time_operator(stdg_ctx* c, double dt, int fp32, int n, double* ms_out) 
     *ms_out = ms / n;
     dev_free(c, dx);
     dev_free(c, dy);
+    dev_free(c, dw);
     return STDG_OK;
+}
+
+int stdg_time_operator(stdg_ctx* c, double dt, int fp32, int n, double* ms_out) {
+    return stdg_time_kernel(c, dt, 0, fp32, n, ms_out);
 }
 
 }  // extern "C"

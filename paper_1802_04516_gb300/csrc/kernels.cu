@@ -532,88 +532,6 @@ __global__ void __launch_bounds__(128) face_apply_kernel(int64_t n_face, int NG,
     }
 }
 
-// Off-diagonal (neighbour-to-neighbour) part of the face term only, for the stencil
-// preconditioner: for every interior face j with elements l, r,
-//   t_l += scale D~_l S E_j : (D~_r^T y_r),   t_r += scale D~_r S E_j : (D~_l^T y_l),
-// i.e. t += scale * (A - blockdiag(A)) y restricted to the face terms.  Each side's values
-// are bracketed alone (the other side zeroed) and scattered to the opposite element.
-template <int DIM, int NP, typename R>
-__global__ void __launch_bounds__(128) face_cross_kernel(int64_t n_face, int NG, const int32_t* __restrict__ fl,
-                                                         const int32_t* __restrict__ fr, const R* __restrict__ D,
-                                                         const R* __restrict__ lamf, const R* __restrict__ muf,
-                                                         const RefTables* __restrict__ rtp, const R* __restrict__ y,
-                                                         R* __restrict__ t, R scale, int nshots, int64_t nvec) {
-    extern __shared__ unsigned char smraw[];
-    R* sm = reinterpret_cast<R*>(smraw);
-    const FaceSmem L = face_smem(DIM, NP, NG);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    R* sS = sm;
-    R* base = sm + kMaxNG * kMaxNG + warp * L.total;
-    R *sD = base, *sv = sD + L.D, *sg = sv + L.v, *st = sg + L.g, *sh = st + L.t;
-    for (int q = threadIdx.x; q < NG * NG; q += blockDim.x) sS[q] = (R)rtp->S[q];
-    __syncthreads();
-    constexpr int NS = DIM == 2 ? 3 : 6;
-    const int ng_np = NG * NP;
-    const int nvs = DIM * ng_np;
-    for (int64_t f = blockIdx.x * (int64_t)wpb + warp; f < n_face; f += (int64_t)gridDim.x * wpb) {
-        const int el = fl[f], er = fr[f];
-        if (er < 0) continue;                 // boundary face: no neighbour coupling
-        const R lam = lamf[f], mu = muf[f];
-        face_load_D<DIM, NP, R>(f, lane, D, sD);
-        for (int s = 0; s < nshots; ++s) {
-            const R* ys = y + (int64_t)s * nvec;
-            R* ts = t + (int64_t)s * nvec;
-            for (int src = 0; src < 2; ++src) {
-                const int es = src == 0 ? el : er;
-                for (int q = lane; q < nvs; q += 32) {
-                    const R v = ys[(int64_t)es * nvs + q];
-                    sv[q] = src == 0 ? v : (R)0;
-                    sv[nvs + q] = src == 0 ? (R)0 : v;
-                }
-                __syncwarp();
-                face_bracket<DIM, NP, R>(NG, lane, sD, sv, sg, st, lam, mu);
-                for (int ent = lane; ent < NS * ng_np; ent += 32) {
-                    const int c = ent / ng_np, b = (ent / NP) % NG, m = ent % NP;
-                    R acc = 0;
-                    for (int b2 = 0; b2 < NG; ++b2) acc += sS[b * NG + b2] * st[(c * NG + b2) * NP + m];
-                    sh[ent] = scale * acc;
-                }
-                __syncwarp();
-                const int side = 1 - src;             // scatter to the opposite element only
-                const int e = side == 0 ? el : er;
-                for (int r = lane; r < nvs; r += 32) {
-                    const int k = r / ng_np, b = (r / NP) % NG, n = r % NP;
-                    R acc = 0;
-#pragma unroll
-                    for (int l = 0; l < DIM; ++l) {
-                        const R* Dp = sD + ((side * DIM + l) * NP + n) * NP;
-                        const R* hp = sh + (sym_c<DIM>(k, l) * NG + b) * NP;
-#pragma unroll
-                        for (int m = 0; m < NP; ++m) acc += Dp[m] * hp[m];
-                    }
-                    atomicAdd(&ts[(int64_t)e * nvs + r], acc);
-                }
-                __syncwarp();
-            }
-        }
-    }
-}
-
-template <int DIM, int NP, typename R>
-static cudaError_t face_cross_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* y, R* t, double scale,
-                                   int nshots) {
-    const FaceSmem L = face_smem(DIM, NP, c->Ng);
-    const int wpb = 4;
-    const size_t smem = sizeof(R) * (kMaxNG * kMaxNG + (size_t)wpb * L.total);
-    cudaFuncSetAttribute(face_cross_kernel<DIM, NP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 152 * 64);
-    face_cross_kernel<DIM, NP, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
-        c->n_face, c->Ng, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, y, t, (R)scale, nshots, c->nvel);
-    note_launch(c);
-    return cudaGetLastError();
-}
-
 template <int DIM, int NP, typename R>
 static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* rhoJ,
                               const R* x, R* y, double scale, bool mass, bool face = true,
@@ -671,16 +589,6 @@ cudaError_t launch_apply32(stdg_ctx* c, double dt, const float* x, float* y, dou
                            int nshots) {
     const double scale = cfac * schur_c(c) * dt * dt;
     STDG_DISPATCH(c->dim, c->Nphi, return (apply_tmpl<D_, N_, float>(c, c->d_D32, c->d_lamf32, c->d_muf32, c->d_rhoJ32, x, y, scale, true, true, xidx, ld, nshots)));
-    return cudaSuccess;
-}
-
-// t += scale * (off-diagonal face coupling) y  (stencil preconditioner, FP64 or FP32 blocks)
-cudaError_t launch_face_cross(stdg_ctx* c, double scale, const void* y, void* t, int fp32, int nshots) {
-    if (fp32) {
-        STDG_DISPATCH(c->dim, c->Nphi, return (face_cross_tmpl<D_, N_, float>(c, c->d_D32, c->d_lamf32, c->d_muf32, (const float*)y, (float*)t, scale, nshots)));
-    } else {
-        STDG_DISPATCH(c->dim, c->Nphi, return (face_cross_tmpl<D_, N_, double>(c, c->d_D, c->d_lamf, c->d_muf, (const double*)y, (double*)t, scale, nshots)));
-    }
     return cudaSuccess;
 }
 

@@ -9,8 +9,8 @@
 // neighbours' own diagonal blocks D_e.  Block elimination of the neighbours gives the
 // first block row of A_i^{-1} in closed form:
 //   z_i = S_i^{-1} (r_i - sum_e N_{i,e} D_e^{-1} r_e),   S_i = D_i - sum_e N_{i,e} D_e^{-1} N_{e,i},
-// so one application is: y = P_1 r (the block-Jacobi apply), t = r - N y (the face term's
-// neighbour-to-neighbour part), z = S^{-1} t (one dense block per element).
+// so one application is: y = P_1 r (the block-Jacobi apply), t = r - N y = 2 r - A y (since
+// D y = r), z = S^{-1} t (one dense block per element).
 //
 // Set-up, per slab size dt, FP64, one CTA per element.  Every block has the Kronecker
 // form of the operator (space (x) time): D_i = M_i (x) T + c dt^2 K_ii (x) S and
@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(kP2Threads) pre2_setup_kernel(
     __shared__ int s_piv;
     __shared__ int s_sing;
     const int tid = threadIdx.x;
-    auto row_of = [&](int s, int a) { return ((s / NP) * NG + a) * NP + s % NP; };   // [k][a][n] layout
     for (int64_t e = blockIdx.x; e < n_elem; e += gridDim.x) {
         // ---- D_i: rho|J| (I (x) M_ref) (x) T + c dt^2 K_ii (x) S, and [ . | I ]
         for (int t = tid; t < n * n; t += blockDim.x) K[t] = 0.0;
@@ -191,13 +190,15 @@ __global__ void __launch_bounds__(kP2Threads) pre2_setup_kernel(
     }
 }
 
-// z_e = S_e^{-1} t_e, one warp per element; lane holds rows lane + 32 i, columns of S^{-1}
-// (contiguous) are streamed once per group of SG shots.
+// z_e = S_e^{-1} (2 r_e - w_e), w = A P_1 r: one warp per element; lane holds rows lane + 32 i,
+// columns of S^{-1} (contiguous) are streamed once per group of SG shots.
 template <typename R, int SG>
 __global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, const R* __restrict__ Sinv,
-                                                         const R* __restrict__ t, R* __restrict__ z, int nshots,
-                                                         int64_t nvec) {
+                                                         const R* __restrict__ r, const int* __restrict__ ridx,
+                                                         int64_t ld, const R* __restrict__ w, R* __restrict__ z,
+                                                         int nshots, int64_t nvec) {
     extern __shared__ unsigned char smraw[];
+    if (ridx) r += (int64_t)(*ridx) * ld;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     R* st = reinterpret_cast<R*>(smraw) + (size_t)warp * SG * N;
     for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, 
             const int sg = min(SG, nshots - s0);
             for (int q = lane; q < SG * N; q += 32) {
                 const int g = q / N, c = q % N;
-                st[q] = g < sg ? t[(int64_t)(s0 + g) * nvec + e * N + c] : (R)0;
+                const int64_t i = (int64_t)(s0 + g) * nvec + e * N + c;
+                st[q] = g < sg ? (R)2 * r[i] - w[i] : (R)0;
             }
             __syncwarp();
             R acc[kP2MaxRows][SG];
@@ -218,9 +220,9 @@ __global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, 
                 const R* col = Se + (int64_t)c * N;
 #pragma unroll
                 for (int i = 0; i < kP2MaxRows; ++i) {
-                    const int r = lane + 32 * i;
-                    if (r < N) {
-                        const R a = col[r];
+                    const int rr = lane + 32 * i;
+                    if (rr < N) {
+                        const R a = col[rr];
 #pragma unroll
                         for (int g = 0; g < SG; ++g) acc[i][g] = fma(a, st[g * N + c], acc[i][g]);
                     }
@@ -228,24 +230,15 @@ __global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, 
             }
 #pragma unroll
             for (int i = 0; i < kP2MaxRows; ++i) {
-                const int r = lane + 32 * i;
-                if (r < N)
+                const int rr = lane + 32 * i;
+                if (rr < N)
 #pragma unroll
                     for (int g = 0; g < SG; ++g)
-                        if (g < sg) z[(int64_t)(s0 + g) * nvec + e * N + r] = acc[i][g];
+                        if (g < sg) z[(int64_t)(s0 + g) * nvec + e * N + rr] = acc[i][g];
             }
             __syncwarp();
         }
     }
-}
-
-// out = x (+ column *xidx at stride ld)
-template <typename R>
-__global__ void copy_col_kernel(int64_t n, const R* __restrict__ x, const int* __restrict__ xidx, int64_t ld,
-                                R* __restrict__ out) {
-    if (xidx) x += (int64_t)(*xidx) * ld;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = x[i];
 }
 
 static size_t pre2_setup_smem(int dim, int NP, int NG) {
@@ -270,33 +263,46 @@ cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status) {
     return cudaGetLastError();
 }
 
-// z = P_2 r for nshots stacked shots: y = P_1 r, t = r - N y, z = S^{-1} t
 template <typename R>
-static cudaError_t pre2_apply_t(stdg_ctx* c, const R* Sinv, const R* r, R* z, const int* ridx, int64_t ld, int nshots,
-                                bool fp32) {
-    const int64_t n = c->nvel * (int64_t)nshots;
-    R* y = reinterpret_cast<R*>(c->d_p2y);
-    R* t = reinterpret_cast<R*>(c->d_p2t);
-    cudaError_t e;
-    if (fp32) e = launch_pre1_apply32(c, (const float*)r, (float*)y, ridx, ld, nshots);
-    else e = launch_pre1_apply(c, (const double*)r, (double*)y, ridx, ld, nshots);
-    if (e != cudaSuccess) return e;
-    copy_col_kernel<R><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, c->stream>>>(n, r, ridx, ld, t);
-    note_launch(c);
-    const double cfac = c->opt.scheme == STDG_SCHEME_CN ? 0.25 : 1.0;
-    if ((e = launch_face_cross(c, -cfac * c->pre_dt * c->pre_dt, y, t, fp32 ? 1 : 0, nshots)) != cudaSuccess) return e;
+static cudaError_t pre2_local_t(stdg_ctx* c, const R* Sinv, const R* r, const int* ridx, int64_t ld, const R* w, R* z,
+                                int nshots) {
     const int N = c->dim * c->Nphi * c->Ng;
     const int wpb = 4;
     const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
     if (nshots == 1) {
-        pre2_local_kernel<R, 1><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * N, c->stream>>>(c->n_elem, N, Sinv, t, z,
-                                                                                             nshots, c->nvel);
+        pre2_local_kernel<R, 1><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * N, c->stream>>>(c->n_elem, N, Sinv, r, ridx,
+                                                                                             ld, w, z, nshots, c->nvel);
     } else {
-        pre2_local_kernel<R, 4><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * 4 * N, c->stream>>>(c->n_elem, N, Sinv, t,
-                                                                                                 z, nshots, c->nvel);
+        pre2_local_kernel<R, 4><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * 4 * N, c->stream>>>(
+            c->n_elem, N, Sinv, r, ridx, ld, w, z, nshots, c->nvel);
     }
     note_launch(c);
     return cudaGetLastError();
+}
+
+// the element-local step alone, z = S^{-1} (2 r - w), one shot (kernel timing)
+cudaError_t launch_pre2_local(stdg_ctx* c, int fp32, const void* r, const void* w, void* z) {
+    if (fp32) return pre2_local_t<float>(c, c->d_pre2_32, (const float*)r, nullptr, 0, (const float*)w, (float*)z, 1);
+    return pre2_local_t<double>(c, c->d_pre2, (const double*)r, nullptr, 0, (const double*)w, (double*)z, 1);
+}
+
+// z = P_2 r for nshots stacked shots: y = P_1 r, w = A y, z = S^{-1} (2 r - w).
+// Since D_i y_i = r_i, (2 r - A y)_i = r_i - sum_e N_{i,e} y_e: the neighbour coupling comes
+// out of one ordinary operator application.
+template <typename R>
+static cudaError_t pre2_apply_t(stdg_ctx* c, const R* Sinv, const R* r, R* z, const int* ridx, int64_t ld, int nshots,
+                                bool fp32) {
+    R* y = reinterpret_cast<R*>(c->d_p2y);
+    R* w = reinterpret_cast<R*>(c->d_p2t);
+    cudaError_t e;
+    if (fp32) {
+        if ((e = launch_pre1_apply32(c, (const float*)r, (float*)y, ridx, ld, nshots)) != cudaSuccess) return e;
+        if ((e = launch_apply32(c, c->pre_dt, (const float*)y, (float*)w, 1.0, nullptr, 0, nshots)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_pre1_apply(c, (const double*)r, (double*)y, ridx, ld, nshots)) != cudaSuccess) return e;
+        if ((e = launch_apply(c, c->pre_dt, (const double*)y, (double*)w, 1.0, nullptr, 0, nshots)) != cudaSuccess) return e;
+    }
+    return pre2_local_t<R>(c, Sinv, r, ridx, ld, w, z, nshots);
 }
 
 cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots) {

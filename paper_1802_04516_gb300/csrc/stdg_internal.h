@@ -132,7 +132,7 @@ struct stdg_ctx {
     // ---- stencil preconditioner (precond2.cu): S_i^{-1} per element, column-major
     double* d_pre2 = nullptr;
     float* d_pre2_32 = nullptr;
-    void *d_p2y = nullptr, *d_p2t = nullptr;   // two stacked velocity vectors (FP64-sized)
+    void *d_p2y = nullptr, *d_p2t = nullptr;   // P_1 r and A P_1 r, stacked over shots (FP64-sized)
     int* d_p2status = nullptr;
 
     // ---- device error word: set by kernels whose bounded waits ran out (checked after each call)
@@ -204,8 +204,7 @@ bool pre2_supported(const stdg_ctx* c);
 cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status);
 cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
 cudaError_t launch_pre2_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots = 1);
-// kernels.cu: off-diagonal face coupling, t += scale * N y
-cudaError_t launch_face_cross(stdg_ctx* c, double scale, const void* y, void* t, int fp32, int nshots);
+cudaError_t launch_pre2_local(stdg_ctx* c, int fp32, const void* r, const void* w, void* z);
 // (re)build the dt-dependent preconditioner blocks when dt changes (capi.cu)
 int precond_for_dt(stdg_ctx* c, double dt);
 
