@@ -17,6 +17,8 @@ Modules
              Schur velocity system (Eq. velocity.sys, Eq. velocity.sys.cn)
   precond    Appendix A preconditioners on the assembled system: block Jacobi (Eq. pre1)
              and the stencil-local inverse (Eqs. APPRE1 / APPRE2)
+  adjoint    receiver misfit and its exact discrete gradient w.r.t. per-element lambda, mu,
+             rho (not in the paper: the adjoint of the oracle's own forward map)
   stepper    one time slab: right-hand side, direct solve, stress back-substitution
              (Eq. NM26 / NM26.cn), traces, energy (Eq. SP3F), receivers, Ricker point
              sources (Sec. 6.3)
@@ -24,4 +26,4 @@ Modules
 Parity status of every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, theorems of the paper and brute-force checks; see each module header.
 """
-from . import basis, quadrature, mesh, operators, precond, stepper  # noqa: F401
+from . import adjoint, basis, quadrature, mesh, operators, precond, stepper  # noqa: F401
