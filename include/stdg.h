@@ -183,6 +183,23 @@ int stdg_apply_preconditioner(stdg_ctx* ctx, double dt, const double* r, double*
 int stdg_residual_noalloc(stdg_ctx* ctx, double dt, const double* x_dev, const double* b_dev,
                           double* r_dev, double* out_dev);
 
+/* Receiver misfit and its gradient (full-waveform inversion).  From the current state of
+ * every shot, advance n_steps slabs of size dt and return
+ *   *loss = 1/2 sum_shots sum_{n=1..n_steps} sum_r |v_h(x_r, t^n) - data|^2,
+ * data laid out [shot][step][receiver][component] (as stdg_read_receivers returns).  With
+ * any of g_lambda, g_mu, g_rho non-NULL (host arrays of n_elem values), also the exact
+ * gradient of the discrete misfit with respect to the per-element lambda, mu and rho, by
+ * the adjoint of the slab map: the transposed velocity system is solved as the forward
+ * system on time-reversed vectors (A^T = J A J for the reversal J of the Gauss-Legendre
+ * time nodes), with the context's solver, precision and preconditioner; states are
+ * checkpointed every checkpoint_every slabs (<= 0: 20) and each segment is recomputed
+ * once in the backward sweep.  Space-time DG only (STDG_EINVAL for Crank-Nicolson); needs
+ * receivers.  The context ends at the final time with the final states, as after
+ * stdg_step; stats (may be NULL) sums the Krylov work of all forward and adjoint solves.
+ * The paper has no adjoint: this is the gradient of the library's own discrete map. */
+int stdg_misfit_grad(stdg_ctx* ctx, double dt, int n_steps, const double* data, int checkpoint_every,
+                     double* loss, double* g_lambda, double* g_mu, double* g_rho, stdg_stats* stats);
+
 /* Average device time of `n` launches of the operator's face kernel (fp32 != 0: the
  * FP32 one) on the context stream, measured with CUDA events: *ms_out. */
 int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out);

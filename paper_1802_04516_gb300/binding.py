@@ -60,6 +60,7 @@ SIGNATURES = {
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
     "stdg_time_kernel": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
+    "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
     "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_residual_noalloc": (C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
 }
@@ -244,6 +245,21 @@ class Solver:
         fr = np.zeros(self.n_face, dtype=np.int32)
         self._chk(self.lib.stdg_get_faces(self.h, fl.ctypes.data_as(_I32), fr.ctypes.data_as(_I32)))
         return fl, fr
+
+    def misfit_grad(self, dt, n_steps, data, checkpoint_every=20, grad=True):
+        """(loss, g_lambda, g_mu, g_rho, stats) of n_steps slabs from the current states;
+        data: (n_shots, n_steps, n_rec, dim).  grad=False: the loss only (forward run)."""
+        data = _f64(data)
+        loss = C.c_double(0.0)
+        g = [np.zeros(self.n_elem) for _ in range(3)] if grad else [None, None, None]
+        st = stdg_stats()
+
+        def ptr(a):
+            return _d(a) if a is not None else None
+
+        self._chk(self.lib.stdg_misfit_grad(self.h, dt, n_steps, _d(data), checkpoint_every, C.byref(loss),
+                                            ptr(g[0]), ptr(g[1]), ptr(g[2]), C.byref(st)))
+        return loss.value, g[0], g[1], g[2], st.as_dict()
 
     def time_kernel(self, dt, which, fp32=False, n=20):
         """Average ms of one launch: which 0 face term, 1 block Jacobi, 2 stencil local step, 3 operator."""

@@ -558,6 +558,26 @@ int stdg_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* out) {
     return solver_step(c, dt, n_steps, out);
 }
 
+int stdg_misfit_grad(stdg_ctx* c, double dt, int n_steps, const double* data, int checkpoint_every, double* loss,
+                     double* g_lambda, double* g_mu, double* g_rho, stdg_stats* out) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || !data || !loss)
+        STDG_FAIL(c, STDG_EINVAL, "bad misfit arguments");
+    if (c->opt.scheme != STDG_SCHEME_STDG) STDG_FAIL(c, STDG_EINVAL, "the adjoint covers the space-time DG scheme only");
+    if (c->n_rec < 1) STDG_FAIL(c, STDG_ESTATE, "the misfit needs receivers (stdg_set_receivers)");
+    if (!c->d_vtr) STDG_FAIL(c, STDG_ESTATE, "no state: set sources, shots or a state first");
+    const int64_t nd = (int64_t)c->n_shots * n_steps * c->n_rec * c->dim;
+    if (!all_finite(data, nd)) STDG_FAIL(c, STDG_EINVAL, "non-finite data");
+    const int K = checkpoint_every > 0 ? std::min(checkpoint_every, n_steps) : std::min(20, n_steps);
+    int rc = ensure_records(c, n_steps);
+    if (rc != STDG_OK) return rc;
+    stdg_stats st;
+    rc = misfit_grad_impl(c, dt, n_steps, data, K, loss, g_lambda, g_mu, g_rho, &st);
+    if (out) *out = st;
+    return rc;
+}
+
 int stdg_get_time(stdg_ctx* c, double* t) {
     CHECK_CTX(c);
     if (!t) return STDG_EINVAL;

@@ -78,9 +78,10 @@ struct Workspace {
     float *z32 = nullptr, *t32 = nullptr;
     cudaStream_t side[6] = {};
     int depth = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    double graph_dt = -1.0;
+    // cached graphs: [0] one whole step, [1] the solve alone (adjoint)
+    cudaGraph_t graph[2] = {};
+    cudaGraphExec_t exec[2] = {};
+    double graph_dt[2] = {-1.0, -1.0};
     std::vector<void*> owned;   // device buffers of this workspace
     dim3 grid() const { return dim3(G, (unsigned)ns); }
 };
@@ -1135,8 +1136,10 @@ int solver_setup(stdg_ctx* c) {
 void solver_free(stdg_ctx* c) {
     Workspace* ws = W(c);
     if (!ws) return;
-    if (ws->exec) cudaGraphExecDestroy(ws->exec);
-    if (ws->graph) cudaGraphDestroy(ws->graph);
+    for (int k = 0; k < 2; ++k) {
+        if (ws->exec[k]) cudaGraphExecDestroy(ws->exec[k]);
+        if (ws->graph[k]) cudaGraphDestroy(ws->graph[k]);
+    }
     for (auto& s : ws->side) if (s) cudaStreamDestroy(s);
     cudaStreamSynchronize(c->stream);
     for (void* p : ws->owned) dev_release(c, p);
@@ -1148,39 +1151,49 @@ void solver_free(stdg_ctx* c) {
 void solver_invalidate_graph(stdg_ctx* c) {
     Workspace* ws = W(c);
     if (!ws) return;
-    if (ws->exec) cudaGraphExecDestroy(ws->exec);
-    if (ws->graph) cudaGraphDestroy(ws->graph);
-    ws->exec = nullptr;
-    ws->graph = nullptr;
-    ws->graph_dt = -1.0;
+    for (int k = 0; k < 2; ++k) {
+        if (ws->exec[k]) cudaGraphExecDestroy(ws->exec[k]);
+        if (ws->graph[k]) cudaGraphDestroy(ws->graph[k]);
+        ws->exec[k] = nullptr;
+        ws->graph[k] = nullptr;
+        ws->graph_dt[k] = -1.0;
+    }
 }
 
 double* solver_dparams(stdg_ctx* c) { return W(c) ? W(c)->dparams : nullptr; }
 
-int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
+// the solve alone: A x = b on the stacked c->d_b / c->d_x (x holds the initial guess)
+static void record_solve_only(Flow& F, double dt) {
+    stdg_ctx* c = F.c;
+    c->scopes.assign(1, 0);
+    record_solve(F, dt, c->d_b, c->d_x);
+    const long k = c->scopes.back() + 1;
+    c->scopes.clear();
+    count_kernel<<<1, 32, 0, c->stream>>>(F.ws->sc, k);
+    F.check(cudaGetLastError());
+}
+
+// Runs `n` repetitions of a recorded body (kind 0: a whole step, 1: the solve alone), as one
+// cached CUDA graph per kind and dt, or from the host loop; then reads the statistics.
+static int run_body_n(stdg_ctx* c, double dt, int n, int kind, stdg_stats* st) {
     Workspace* ws = W(c);
-    if (!ws) STDG_FAIL(c, STDG_ESTATE, "solver not set up");
-    // statistics reset (outside any graph)
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_total, 0, sizeof(int) * 4, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_final_rel, 0, sizeof(double) * 2, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->launches, 0, sizeof(unsigned long long), c->stream));
-    {
-        const int rc = precond_for_dt(c, dt);
-        if (rc != STDG_OK) return rc;
-    }
-    const double t0 = c->t;
-    STDG_CUDA(c, cudaMemcpyAsync(ws->dparams, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    {
-        double stepidx = (double)c->rec_steps;
-        STDG_CUDA(c, cudaMemcpyAsync(ws->dparams + 2, &stepidx, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    }
+    auto record = [&](Flow& F) {
+        if (kind == 0) record_step(F, dt);
+        else record_solve_only(F, dt);
+    };
     if (c->opt.use_graph) {
-        if (!ws->exec || ws->graph_dt != dt) {
-            solver_invalidate_graph(c);
+        if (!ws->exec[kind] || ws->graph_dt[kind] != dt) {
+            if (ws->exec[kind]) cudaGraphExecDestroy(ws->exec[kind]);
+            if (ws->graph[kind]) cudaGraphDestroy(ws->graph[kind]);
+            ws->exec[kind] = nullptr;
+            ws->graph[kind] = nullptr;
             cudaStream_t s0 = c->stream;
             STDG_CUDA(c, cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
             Flow F{c, ws, true};
-            record_step(F, dt);
+            record(F);
             c->stream = s0;
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(s0, &g);
@@ -1190,22 +1203,20 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
                 cudaGetLastError();
                 return STDG_ECUDA;
             }
-            ws->graph = g;
-            STDG_CUDA(c, cudaGraphInstantiate(&ws->exec, g, 0));
-            ws->graph_dt = dt;
+            ws->graph[kind] = g;
+            STDG_CUDA(c, cudaGraphInstantiate(&ws->exec[kind], g, 0));
+            ws->graph_dt[kind] = dt;
         }
-        for (int s = 0; s < n_steps; ++s) STDG_CUDA(c, cudaGraphLaunch(ws->exec, c->stream));
+        for (int s = 0; s < n; ++s) STDG_CUDA(c, cudaGraphLaunch(ws->exec[kind], c->stream));
     } else {
-        for (int s = 0; s < n_steps; ++s) {
+        for (int s = 0; s < n; ++s) {
             Flow F{c, ws, false};
-            record_step(F, dt);
+            record(F);
             if (F.err != cudaSuccess) STDG_CUDA(c, F.err);
         }
     }
     STDG_CUDA(c, cudaStreamSynchronize(c->stream));
     STDG_CUDA(c, cudaGetLastError());
-    c->t = t0 + n_steps * dt;
-    c->rec_steps += n_steps;
     DevScalars h;
     STDG_CUDA(c, cudaMemcpy(&h, ws->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
     if (st) {
@@ -1223,6 +1234,35 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
     }
     if (h.st_notconv) STDG_FAIL(c, STDG_ENOTCONV, "Krylov solve reached max_iters");
     return STDG_OK;
+}
+
+int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
+    Workspace* ws = W(c);
+    if (!ws) STDG_FAIL(c, STDG_ESTATE, "solver not set up");
+    {
+        const int rc = precond_for_dt(c, dt);
+        if (rc != STDG_OK) return rc;
+    }
+    const double t0 = c->t;
+    STDG_CUDA(c, cudaMemcpyAsync(ws->dparams, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    {
+        double stepidx = (double)c->rec_steps;
+        STDG_CUDA(c, cudaMemcpyAsync(ws->dparams + 2, &stepidx, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    const int rc = run_body_n(c, dt, n_steps, 0, st);
+    if (rc == STDG_OK || rc == STDG_ENOTCONV) {   // the state advanced either way
+        c->t = t0 + n_steps * dt;
+        c->rec_steps += n_steps;
+    }
+    return rc;
+}
+
+int solver_solve(stdg_ctx* c, double dt, stdg_stats* st) {
+    Workspace* ws = W(c);
+    if (!ws) STDG_FAIL(c, STDG_ESTATE, "solver not set up");
+    const int rc = precond_for_dt(c, dt);
+    if (rc != STDG_OK) return rc;
+    return run_body_n(c, dt, 1, 1, st);
 }
 
 }  // namespace stdg

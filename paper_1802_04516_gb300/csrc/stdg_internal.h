@@ -212,4 +212,9 @@ int precond_for_dt(stdg_ctx* c, double dt);
 int solver_setup(stdg_ctx* c);
 void solver_free(stdg_ctx* c);
 int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st);
+int solver_solve(stdg_ctx* c, double dt, stdg_stats* st);   // A x = b on the stacked d_b / d_x
+
+// adjoint.cu
+int misfit_grad_impl(stdg_ctx* c, double dt, int n_steps, const double* data, int checkpoint_every, double* loss,
+                     double* g_lam, double* g_mu, double* g_rho, stdg_stats* stats);
 }  // namespace stdg

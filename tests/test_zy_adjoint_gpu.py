@@ -1,0 +1,78 @@
+"""GPU misfit gradient (stdg_misfit_grad) against the oracle's discrete adjoint and
+against central finite differences of the GPU's own misfit."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import gpu_solver, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(p=1, ny=5, steps=12, n_shots=2, n_rec=6):
+    w = synth.c5_adjoint(ny=ny, p=p, steps=steps, n_shots=n_shots, n_rec=n_rec)
+    wt = synth.c5_adjoint(ny=ny, p=p, steps=steps, n_shots=n_shots, n_rec=n_rec, true_model=True)
+    return w, wt
+
+
+def _oracle(w, wt):
+    from oracle import adjoint as adj
+    geom = (w.xyz, w.elem_vert, w.period, w.p, w.p_gamma, w.dt)
+    geom_t = (wt.xyz, wt.elem_vert, wt.period, wt.p, wt.p_gamma, wt.dt)
+    src = [(w.shots_xs[k], w.shots_dir[k]) for k in range(w.n_shots)]
+    data = np.array([adj.forward(adj.make_sim(geom_t, wt.lam, wt.mu, wt.rho), w.n_steps, s, w.f0, w.t_delay, w.a1,
+                                 w.receivers)[0] for s in src])
+    return data, adj.misfit_gradient(geom, w.lam, w.mu, w.rho, w.n_steps, src, w.f0, w.t_delay, w.a1,
+                                     w.receivers, data)
+
+
+@pytest.mark.parametrize("p,precision,pre,ckpt", [(1, "fp64", 2, 5), (2, "fp64", 1, 20), (2, "mixed", 2, 4)])
+def test_misfit_gradient_matches_oracle(p, precision, pre, ckpt):
+    need_gpu()
+    w, wt = _case(p=p)
+    data, (L, gl, gm, gr) = _oracle(w, wt)
+    rel_tol = 1e-13 if precision == "fp64" else 1e-12
+    s = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000, preconditioner=pre)
+    Lg, glg, gmg, grg, st = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=ckpt)
+    # The residual rec - d of a small model perturbation cancels: a relative error e of the
+    # records becomes e * amp in the residual, amp = |d| / |rec - d|.  The bar is the solve
+    # tolerance's reach times that amplification (FP64 1e-13 solves, mixed 1e-12).
+    amp = np.linalg.norm(data) / np.sqrt(2.0 * L)
+    tol = (1e-11 if precision == "fp64" else 1e-10) * amp + 1e-10
+    errs = [np.abs(a - b).max() / np.abs(b).max() for a, b in ((glg, gl), (gmg, gm), (grg, gr))]
+    print(p, precision, pre, "amp %.3g tol %.3g loss err %.3g grad errs" % (amp, tol, abs(Lg - L) / L), errs)
+    assert abs(Lg - L) <= tol * L
+    assert max(errs) <= tol
+    # the context ends at the final time with the forward run's final states
+    f = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000, preconditioner=pre)
+    f.step(w.dt, w.n_steps)
+    for k in range(w.n_shots):
+        v1, s1 = s.get_state(k)
+        v2, s2 = f.get_state(k)
+        assert np.abs(v1 - v2).max() <= 1e-10 * np.abs(v2).max()
+
+
+def test_misfit_gradient_matches_gpu_finite_differences():
+    # the GPU's own misfit, FP64 solves to 1e-14, Richardson-extrapolated central differences
+    need_gpu()
+    w, wt = _case(p=2, steps=10)
+    data, _ = _oracle(w, wt)
+    s = gpu_solver(w, precision="fp64", rel_tol=1e-14, max_iters=20000, preconditioner=2)
+    _, gl, gm, gr, _ = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=3)
+    rng = np.random.default_rng(4)
+    for name, g in (("lam", gl), ("mu", gm), ("rho", gr)):
+        big = np.where(np.abs(g) >= 1e-2 * np.abs(g).max())[0]
+        for e in rng.choice(big, 2, replace=False):
+            fds = []
+            for hr in (1e-4, 0.5e-4):
+                Ls = []
+                for sgn in (1.0, -1.0):
+                    q = {"lam": w.lam.copy(), "mu": w.mu.copy(), "rho": w.rho.copy()}
+                    q[name][e] *= 1.0 + sgn * hr
+                    f = gpu_solver(w, precision="fp64", rel_tol=1e-14, max_iters=20000, preconditioner=2)
+                    f.set_material(q["lam"], q["mu"], q["rho"])
+                    f.set_sources(w.shots_xs, w.shots_dir, w.f0, w.t_delay, w.a1)
+                    Ls.append(f.misfit_grad(w.dt, w.n_steps, data, grad=False)[0])
+                fds.append((Ls[0] - Ls[1]) / (2 * hr * {"lam": w.lam, "mu": w.mu, "rho": w.rho}[name][e]))
+            fd = (4.0 * fds[1] - fds[0]) / 3.0
+            assert abs(fd - g[e]) <= 1e-6 * abs(g[e]) + 1e-9 * np.abs(g).max(), (name, e, fd, g[e])
