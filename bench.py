@@ -246,6 +246,42 @@ def ragged_section(torch, args, stream, dist, world):
             "gpu_launches": launches, "steps": args.ms_steps}
 
 
+def adjoint_section(torch, args, stream, dist, world):
+    """Full-waveform-inversion gradient on the 60,024-triangle random medium (p = p_gamma = 2,
+    8 Ricker shots, 100 receivers, 10x CFL, checkpoints every 20 slabs): one complete
+    stdg_misfit_grad per gradient -- forward run with checkpoints, misfit, segment
+    recompute and adjoint solves for all 8 shots -- in mixed precision.  The data are a
+    forward run of the perturbed ("true") model, made before the timed region."""
+    import synth
+    w = synth.c5_adjoint(steps=args.adj_steps)
+    wt = synth.c5_adjoint(steps=args.adj_steps, true_model=True)
+    gen = build_solver(wt, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol, pre=args.pre)
+    gen.step(wt.dt, wt.n_steps)
+    data = gen.read_receivers()
+    gen.close()
+    s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol, pre=args.pre)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    loss, gl, gm, gr, st = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=20)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([sec], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        sec = float(tt.item())
+    s.close()
+    return {"workload": "c5_adjoint: %d triangles, p=p_gamma=2, %d shots, %d receivers, %d slabs%s, dt=%.4g, "
+                        "checkpoint every 20" % (w.n_elem, w.n_shots, len(w.receivers), w.n_steps,
+                                                 "" if w.n_steps == 300 else " (of the workload's 300)", w.dt),
+            "grads_per_s": world / sec, "seconds_per_gradient": sec, "loss": loss,
+            "grad_norms": {"lambda": float(np.linalg.norm(gl)), "mu": float(np.linalg.norm(gm)),
+                           "rho": float(np.linalg.norm(gr))},
+            "krylov_iters_total": st["iters_total"], "precision": "mixed FP32/FP64 (1e-8 rel residual)",
+            "timing": "wall clock of one call, no warm-up (includes graph capture of the step and solve graphs)"}
+
+
 def pre2_local_roofline(s, w, pk):
     """Element-local step of the stencil preconditioner, z = S^{-1} (2 r - w) in FP32: one
     dense (d N_phi N_gamma)^2 block per element streamed from HBM, plus r, w read and z written."""
@@ -328,6 +364,9 @@ def main():
     ap.add_argument("--ms-steps", type=int, default=2, help="timed slabs of the multi-shot and ragged batches")
     ap.add_argument("--no-multishot", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=60,
+                    help="slabs of the misfit-gradient run (the workload has 300; 60 keeps the bench short)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solver loops from the host instead of CUDA-graph while nodes (for kernel profilers)")
     args = ap.parse_args()
@@ -382,6 +421,7 @@ def main():
         s.close()
         multishot = None if args.no_multishot else multishot_section(torch, args, stream, dist, world)
         ragged = None if args.no_ragged else ragged_section(torch, args, stream, dist, world)
+        adjoint = None if args.no_adjoint else adjoint_section(torch, args, stream, dist, world)
     if rank != 0:
         return
     cb = None if args.no_cpu_baseline else cpu_baseline()
@@ -406,6 +446,7 @@ def main():
         "fp64": fp64,
         "multishot": multishot,
         "ragged": ragged,
+        "adjoint": adjoint,
         "cpu_baseline": cb,
     }
     print(json.dumps(line))

@@ -291,3 +291,31 @@ def solver_from_workload(w, precision="fp64", rel_tol=1e-8, max_iters=5000, gmre
     if with_receivers and w.receivers is not None:
         s.set_receivers(w.receivers)
     return s
+
+
+def misfit(solver, lam, mu, rho, dt, n_steps, data, reset, checkpoint_every=20):
+    """Receiver misfit as a differentiable torch function of the per-element lambda, mu, rho.
+
+    Sets the material from the three tensors, calls ``reset()`` to put the initial states
+    back (for instance ``lambda: solver.set_sources(...)``), then runs stdg_misfit_grad:
+    the forward value is the misfit of ``n_steps`` slabs against ``data`` (n_shots, n_steps,
+    n_rec, dim); backward returns the adjoint gradients scaled by the incoming gradient.
+    """
+    import torch
+
+    class _Misfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, lam_t, mu_t, rho_t):
+            solver.set_material(lam_t.detach().cpu().double().numpy(), mu_t.detach().cpu().double().numpy(),
+                                rho_t.detach().cpu().double().numpy())
+            reset()
+            loss, gl, gm, gr, _ = solver.misfit_grad(dt, n_steps, data, checkpoint_every=checkpoint_every)
+            ctx.save_for_backward(*(torch.as_tensor(g, dtype=lam_t.dtype, device=lam_t.device) for g in (gl, gm, gr)))
+            return torch.tensor(loss, dtype=lam_t.dtype, device=lam_t.device)
+
+        @staticmethod
+        def backward(ctx, g_out):
+            gl, gm, gr = ctx.saved_tensors
+            return g_out * gl, g_out * gm, g_out * gr
+
+    return _Misfit.apply(lam, mu, rho)

@@ -76,3 +76,23 @@ def test_misfit_gradient_matches_gpu_finite_differences():
                 fds.append((Ls[0] - Ls[1]) / (2 * hr * {"lam": w.lam, "mu": w.mu, "rho": w.rho}[name][e]))
             fd = (4.0 * fds[1] - fds[0]) / 3.0
             assert abs(fd - g[e]) <= 1e-6 * abs(g[e]) + 1e-9 * np.abs(g).max(), (name, e, fd, g[e])
+
+
+def test_autograd_function_returns_the_adjoint_gradient():
+    import torch
+    from paper_1802_04516_gb300.binding import misfit
+    need_gpu()
+    w, wt = _case(p=1, steps=8)
+    data, (L, gl, gm, gr) = _oracle(w, wt)
+    s = gpu_solver(w, precision="fp64", rel_tol=1e-13, max_iters=20000, preconditioner=2)
+    lam = torch.tensor(w.lam, requires_grad=True)
+    mu = torch.tensor(w.mu, requires_grad=True)
+    rho = torch.tensor(w.rho, requires_grad=True)
+    loss = misfit(s, lam, mu, rho, w.dt, w.n_steps, data,
+                  reset=lambda: s.set_sources(w.shots_xs, w.shots_dir, w.f0, w.t_delay, w.a1))
+    (3.0 * loss).backward()
+    amp = np.linalg.norm(data) / np.sqrt(2.0 * L)
+    tol = 1e-11 * amp + 1e-10
+    assert abs(loss.item() - L) <= tol * L
+    for t, g in ((lam, gl), (mu, gm), (rho, gr)):
+        assert np.abs(t.grad.numpy() - 3.0 * g).max() <= tol * np.abs(3.0 * g).max()
