@@ -89,3 +89,49 @@ def test_pre2_reduces_to_pre1_without_coupling():
     P1 = pre1(Abd, ne).toarray()
     P2 = pre2(Abd, ne, sim.mesh.elem_nbr).toarray()
     assert np.abs(P1 - P2).max() < 1e-12 * np.abs(P1).max()
+
+
+def _face_pairs(ev):
+    """Element pairs sharing a face (sorted vertex tuples of the d-1 faces), as e1 * n + e2, e1 < e2."""
+    ne, nv = ev.shape
+    faces = np.concatenate([np.delete(ev, f, axis=1) for f in range(nv)])
+    faces.sort(axis=1)
+    owner = np.tile(np.arange(ne), nv)
+    key = np.unique(faces, axis=0, return_inverse=True)[1].ravel()
+    order = np.argsort(key, kind="stable")
+    k, o = key[order], owner[order]
+    same = k[1:] == k[:-1]
+    a, b = o[:-1][same], o[1:][same]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    return lo, hi
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3", "c4", "c5", "ragged"])
+def test_face_neighbours_never_share_a_face(name):
+    # The GPU forms Pre2's first block row by eliminating the neighbours one by one, which is
+    # exact when no two face neighbours of an element are face neighbours of each other
+    # (the local system is then an "arrow"); this holds for every workload mesh.
+    w = {"c1": lambda: synth.c1_periodic_pwave(), "c2": lambda: synth.c2_layered_slivers(),
+         "c3": lambda: synth.c3_cube_swave(n=16), "c4": lambda: synth.c4_multishot(n_shots=1),
+         "c5": lambda: synth.c5_adjoint(), "ragged": lambda: synth.ragged_union(ks=range(0, 16, 5))[0]}[name]()
+    ev = np.asarray(w.elem_vert, dtype=np.int64)
+    ne = ev.shape[0]
+    lo, hi = _face_pairs(ev)
+    pairs = np.unique(lo * ne + hi)
+    # neighbours of every element, padded with -1
+    deg = np.bincount(np.concatenate([lo, hi]), minlength=ne)
+    assert deg.max() <= ev.shape[1]
+    tab = np.full((ne, ev.shape[1]), -1, dtype=np.int64)
+    src = np.concatenate([lo, hi])
+    dst = np.concatenate([hi, lo])
+    order = np.argsort(src, kind="stable")
+    src, dst = src[order], dst[order]
+    start = np.searchsorted(src, np.arange(ne))
+    slot = np.arange(len(src)) - start[src]
+    tab[src, slot] = dst
+    for p in range(ev.shape[1]):
+        for q in range(p + 1, ev.shape[1]):
+            a, b = tab[:, p], tab[:, q]
+            ok = (a >= 0) & (b >= 0) & (a != b)
+            key = np.minimum(a[ok], b[ok]) * ne + np.maximum(a[ok], b[ok])
+            assert not np.isin(key, pairs).any(), name
