@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "stdg_internal.h"
+#include "tma.h"
 
 namespace stdg {
 
@@ -234,33 +235,6 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
 // above.  Every wait on an mbarrier is bounded; on timeout the kernel records the error
 // in *err and the warp stops.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// true when the phase with the given parity has completed; gives up after `limit` polls
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long limit) {
-    for (long i = 0; i < limit; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
 template <int DIM, int NP, int NG, typename R>
 struct FaceTma {
     static constexpr int NS = DIM == 2 ? 3 : 6;
