@@ -154,7 +154,7 @@ static int setup_pre1(stdg_ctx* c) {
         if (!c->d_pre2) {
             if ((rc = dev_alloc(c, (void**)&c->d_pre2, sizeof(double) * nS)) != STDG_OK) return rc;
             if (c->opt.precision != STDG_FP64 &&
-                (rc = dev_alloc(c, (void**)&c->d_pre2_16, 2 * ne * pre2_stride16(c))) != STDG_OK) return rc;
+                (rc = dev_alloc(c, (void**)&c->d_pre2_32, sizeof(float) * ne * pre2_stride32(c))) != STDG_OK) return rc;
             if ((rc = dev_alloc(c, (void**)&c->d_p2status, sizeof(int))) != STDG_OK) return rc;
         }
     }
@@ -704,7 +704,7 @@ int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double*
     if (n < 1 || !ms_out || which < 0 || which > 3) STDG_FAIL(c, STDG_EINVAL, "bad timing arguments");
     if (which == 1 && !c->opt.preconditioner) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
     if (which == 2 && c->opt.preconditioner != 2) STDG_FAIL(c, STDG_ESTATE, "context created without the stencil preconditioner");
-    if (which == 2 && fp32 && !c->d_pre2_16) STDG_FAIL(c, STDG_ESTATE, "reduced-precision stencil blocks exist only in mixed precision");
+    if (which == 2 && fp32 && !c->d_pre2_32) STDG_FAIL(c, STDG_ESTATE, "FP32 stencil blocks exist only in mixed precision");
     if (which == 1 && fp32 && !c->d_preV32) STDG_FAIL(c, STDG_ESTATE, "FP32 block-Jacobi blocks exist only in mixed precision");
     int rc;
     if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;

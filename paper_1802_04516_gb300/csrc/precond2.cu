@@ -19,17 +19,15 @@
 // the block-Jacobi set-up,
 //   N_{i,e} D_e^{-1} N_{e,i} = (c dt^2)^2 sum_q (k_q k_q^T) (x) (S B_{e,q} S),  k_q = K_ie V_e[:, q],
 // which assembles S_i without any n^3 product; S_i (order d N_phi N_gamma) is then
-// inverted by Gauss-Jordan elimination with partial pivoting and stored column-major:
-// in FP64 for the FP64 solver and in BF16 for the FP32 inner solver of the mixed path
-// (a preconditioner only has to be a fixed linear map close to the inverse; BF16 halves
-// the bytes of the dominant kernel and leaves the iteration counts unchanged).
+// inverted by Gauss-Jordan elimination with partial pivoting and stored column-major, in
+// FP64 for the FP64 solver and in FP32 for the FP32 inner solver of the mixed path.  (BF16
+// blocks halve the bytes, but on the heterogeneous 60,024-triangle inversion medium they
+// made the inner GMRES stagnate after 16 slabs; FP32 blocks converge there.)
 #include <algorithm>
 #include <cmath>
 
-#include <cuda_bf16.h>
 
 #include "stdg_internal.h"
-#include "tma.h"
 
 namespace stdg {
 
@@ -63,7 +61,7 @@ __global__ void __launch_bounds__(kP2Threads) pre2_setup_kernel(
     const int32_t* __restrict__ face_l, const int32_t* __restrict__ face_r, const double* __restrict__ D,
     const double* __restrict__ lamf, const double* __restrict__ muf, const double* __restrict__ rhoJ,
     const double* __restrict__ preV, const double* __restrict__ preB, double cdt2, double* __restrict__ out64,
-    __nv_bfloat16* __restrict__ out16, int64_t stride16, int* __restrict__ status) {
+    float* __restrict__ out32, int64_t stride32, int* __restrict__ status) {
     extern __shared__ double sm[];
     const int NP = rtp->Nphi, NG = rtp->Ng;
     const int n = dim * NP;
@@ -190,13 +188,13 @@ __global__ void __launch_bounds__(kP2Threads) pre2_setup_kernel(
             const int C = ent / N, R = ent % N;
             const double v = A[R * ldA + N + C];
             if (out64) out64[e * (int64_t)N * N + ent] = v;
-            if (out16) out16[e * stride16 + ent] = __float2bfloat16((float)v);
+            if (out32) out32[e * stride32 + ent] = (float)v;
         }
         __syncthreads();
     }
 }
 
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ double to_f(double v) { return v; }
 
 // z_e = S_e^{-1} (2 r_e - w_e), w = A P_1 r: one warp per element; lane holds rows lane + 32 i,
@@ -251,77 +249,6 @@ __global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, 
     }
 }
 
-// One shot, BF16 blocks, FP32 arithmetic, TMA-pipelined: each warp walks its elements with
-// two shared-memory stages; lane 0 copies the next element's whole S^{-1} block
-// (cp.async.bulk, completion on the stage's mbarrier) while the warp multiplies the
-// current one out of shared memory.  Every wait is bounded; on a timeout the warp records
-// the error in *err, drains its copy in flight (bounded as well) and stops.
-__global__ void __launch_bounds__(128) pre2_local_tma_kernel(int64_t n_elem, int N, int64_t es,
-                                                             const __nv_bfloat16* __restrict__ Sinv,
-                                                             const float* __restrict__ r, const int* __restrict__ ridx,
-                                                             int64_t ld, const float* __restrict__ w, float* __restrict__ z,
-                                                             int* __restrict__ err) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bars[4][2];
-    if (ridx) r += (int64_t)(*ridx) * ld;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    const int64_t stage_bytes = es * (int64_t)sizeof(__nv_bfloat16);       // a multiple of 16
-    unsigned char* base = smraw + (size_t)warp * (2 * stage_bytes + ((N * sizeof(float) + 15) / 16) * 16);
-    auto stage = [&](int s_) { return reinterpret_cast<__nv_bfloat16*>(base + s_ * stage_bytes); };
-    float* tv = reinterpret_cast<float*>(base + 2 * stage_bytes);
-    const uint32_t bar0 = smem_u32(&bars[warp][0]), bar1 = smem_u32(&bars[warp][1]);
-    if (lane == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    constexpr long kPollLimit = 1L << 24;
-    auto issue = [&](int64_t e, int st) {   // lane 0 only
-        const uint32_t bar = st ? bar1 : bar0;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, (uint32_t)stage_bytes);
-        bulk_g2s(smem_u32(stage(st)), Sinv + e * es, (uint32_t)stage_bytes, bar);
-    };
-    const int64_t stride = (int64_t)gridDim.x * wpb;
-    int64_t e = blockIdx.x * (int64_t)wpb + warp;
-    if (e < n_elem && lane == 0) issue(e, 0);
-    uint32_t ph0 = 0, ph1 = 0;
-    int st = 0;
-    for (; e < n_elem; e += stride) {
-        const int64_t en = e + stride;
-        if (en < n_elem && lane == 0) issue(en, st ^ 1);
-        for (int q = lane; q < N; q += 32) tv[q] = 2.0f * r[e * N + q] - w[e * N + q];
-        if (!mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit)) {
-            if (lane == 0) atomicExch(err, 1);
-            if (en < n_elem) mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit);
-            break;
-        }
-        if (st) ph1 ^= 1u; else ph0 ^= 1u;
-        __syncwarp();
-        const __nv_bfloat16* Sm = stage(st);
-        float acc[kP2MaxRows];
-#pragma unroll
-        for (int i = 0; i < kP2MaxRows; ++i) acc[i] = 0.f;
-        for (int c = 0; c < N; ++c) {
-            const float tc = tv[c];
-            const __nv_bfloat16* col = Sm + c * N;
-#pragma unroll
-            for (int i = 0; i < kP2MaxRows; ++i) {
-                const int rr = lane + 32 * i;
-                if (rr < N) acc[i] = fmaf(__bfloat162float(col[rr]), tc, acc[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kP2MaxRows; ++i) {
-            const int rr = lane + 32 * i;
-            if (rr < N) z[e * N + rr] = acc[i];
-        }
-        __syncwarp();   // the stage and tv are free before the next copy into them
-        st ^= 1;
-    }
-}
-
 static size_t pre2_setup_smem(int dim, int NP, int NG) {
     const int n = dim * NP, N = n * NG;
     return sizeof(double) * ((size_t)N * 2 * N + 2 * (size_t)n * n + (size_t)n * NG * NG + 2 * (size_t)dim * NP * NP + N);
@@ -339,14 +266,10 @@ cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status) {
     const int grid = (int)std::min<int64_t>(c->n_elem, 152 * 8);
     pre2_setup_kernel<<<grid, kP2Threads, smem, c->stream>>>(c->n_elem, c->dim, c->d_rt, c->d_elem_face, c->d_face_l,
                                                              c->d_face_r, c->d_D, c->d_lamf, c->d_muf, c->d_rhoJ, c->d_preV,
-                                                             c->d_preB, cfac * dt * dt, c->d_pre2, c->d_pre2_16,
-                                                             pre2_stride16(c), d_status);
+                                                             c->d_preB, cfac * dt * dt, c->d_pre2, c->d_pre2_32,
+                                                             pre2_stride32(c), d_status);
     note_launch(c);
     return cudaGetLastError();
-}
-
-static size_t pre2_tma_smem(int N, int64_t es) {
-    return 4 * (2 * (size_t)es * sizeof(__nv_bfloat16) + ((N * sizeof(float) + 15) / 16) * 16);
 }
 
 template <typename R, typename S>
@@ -355,17 +278,6 @@ static cudaError_t pre2_local_t(stdg_ctx* c, const S* Sinv, int64_t es, const R*
     const int N = c->dim * c->Nphi * c->Ng;
     const int wpb = 4;
     const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
-    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
-        if (nshots == 1 && c->d_err && pre2_tma_smem(N, es) <= 227 * 1024) {
-            const size_t smem = pre2_tma_smem(N, es);
-            cudaFuncSetAttribute(pre2_local_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int64_t tb = std::min<int64_t>(blocks, 152 * 4);
-            pre2_local_tma_kernel<<<(unsigned)tb, 32 * wpb, smem, c->stream>>>(c->n_elem, N, es, Sinv, r, ridx, ld, w, z,
-                                                                              c->d_err);
-            note_launch(c);
-            return cudaGetLastError();
-        }
-    }
     if (nshots == 1) {
         pre2_local_kernel<R, S, 1><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * N, c->stream>>>(
             c->n_elem, N, es, Sinv, r, ridx, ld, w, z, nshots, c->nvel);
@@ -381,8 +293,8 @@ static cudaError_t pre2_local_t(stdg_ctx* c, const S* Sinv, int64_t es, const R*
 cudaError_t launch_pre2_local(stdg_ctx* c, int fp32, const void* r, const void* w, void* z) {
     const int64_t N = c->dim * c->Nphi * c->Ng;
     if (fp32)
-        return pre2_local_t<float, __nv_bfloat16>(c, c->d_pre2_16, pre2_stride16(c), (const float*)r, nullptr, 0,
-                                                   (const float*)w, (float*)z, 1);
+        return pre2_local_t<float, float>(c, c->d_pre2_32, pre2_stride32(c), (const float*)r, nullptr, 0,
+                                           (const float*)w, (float*)z, 1);
     return pre2_local_t<double, double>(c, c->d_pre2, N * N, (const double*)r, nullptr, 0, (const double*)w, (double*)z, 1);
 }
 
@@ -411,7 +323,7 @@ cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int
 }
 
 cudaError_t launch_pre2_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots) {
-    return pre2_apply_t<float, __nv_bfloat16>(c, c->d_pre2_16, pre2_stride16(c), r, z, ridx, ld, nshots, true);
+    return pre2_apply_t<float, float>(c, c->d_pre2_32, pre2_stride32(c), r, z, ridx, ld, nshots, true);
 }
 
 }  // namespace stdg

@@ -1,7 +1,6 @@
 // Internal declarations of the stdg library (not part of the C ABI).
 #pragma once
 
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -132,7 +131,7 @@ struct stdg_ctx {
     double pre_dt = -1.0;    // slab size the time blocks d_preB were built for
     // ---- stencil preconditioner (precond2.cu): S_i^{-1} per element, column-major
     double* d_pre2 = nullptr;
-    __nv_bfloat16* d_pre2_16 = nullptr;        // BF16 copy for the FP32 solver, pre2_stride16 apart
+    float* d_pre2_32 = nullptr;                // FP32 copy for the FP32 solver, pre2_stride32 apart
     void *d_p2y = nullptr, *d_p2t = nullptr;   // P_1 r and A P_1 r, stacked over shots (FP64-sized)
     int* d_p2status = nullptr;
 
@@ -202,10 +201,10 @@ cudaError_t launch_pre1_apply32(stdg_ctx* c, const float* r, float* z, const int
 
 // precond2.cu
 bool pre2_supported(const stdg_ctx* c);
-// entries between consecutive BF16 blocks: (d N_phi N_gamma)^2 rounded up to 16 bytes
-inline int64_t pre2_stride16(const stdg_ctx* c) {
+// entries between consecutive FP32 blocks: (d N_phi N_gamma)^2 rounded up to 16 bytes
+inline int64_t pre2_stride32(const stdg_ctx* c) {
     const int64_t N = (int64_t)c->dim * c->Nphi * c->Ng;
-    return (N * N + 7) / 8 * 8;
+    return (N * N + 3) / 4 * 4;
 }
 cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status);
 cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
