@@ -167,6 +167,18 @@ def e2e_steps(torch, s, w, steps, stream):
     return dt * 1e3, v.nbytes + sig.nbytes, v.nbytes + sig.nbytes + rec_bytes
 
 
+# DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
+# 16,384-triangle copy of the 2D p = p_gamma = 3 construction (profiles/traffic_face_pre2_c2_16k.md),
+# scaled by the units one launch processes.  Valid for that shape only.
+TRAFFIC_PER_UNIT = {"face_fp32": 50534400 / 24768, "pre2_local_fp32": (429950208 + 2902016) / 16384}
+
+
+def _traffic(w, key, units):
+    if w.dim == 2 and w.p == 3 and w.p_gamma == 3:
+        return int(TRAFFIC_PER_UNIT[key] * units)
+    return None
+
+
 def face_kernel_roofline(s, w, fp32, n_face, pk):
     """Algorithmic bytes / FLOPs of one launch of the operator's face kernel, its measured
     average duration (CUDA events on the library stream) and the fraction of peak."""
@@ -187,8 +199,8 @@ def face_kernel_roofline(s, w, fp32, n_face, pk):
     if fp32:
         peak = float(pk.get("hbm_gbs", 6800.0))
         achieved = bytes_alg / (ms * 1e-3) / 1e9
-        return {"kernel": "face_apply_kernel<float>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+        return {"kernel": "face_apply_tma_kernel<float>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(w, "face_fp32", n_face),
                 "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
                 "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
     achieved = flops / (ms * 1e-3) / 1e12
@@ -295,7 +307,7 @@ def pre2_local_roofline(s, w, pk):
     peak = float(pk.get("hbm_gbs", 6800.0))
     achieved = bytes_alg / (ms * 1e-3) / 1e9
     return {"kernel": "pre2_local_kernel<float,float,1>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(w, "pre2_local_fp32", w.n_elem),
             "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(2 * w.n_elem * N * N),
             "ms_per_launch": round(ms, 4), "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
 
