@@ -104,7 +104,7 @@ def peaks():
         return {}
 
 
-def build_solver(w, precision, stream, shot_offset=0.0, restart=10, inner_tol=1e-2, use_graph=True, pre=2):
+def build_solver(w, precision, stream, shot_offset=0.0, restart=20, inner_tol=1e-4, use_graph=True, pre=2):
     from paper_1802_04516_gb300.binding import Solver
     s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=restart,
                inner_tol=inner_tol, use_graph=use_graph, stream=stream, preconditioner=pre)
@@ -369,8 +369,8 @@ def main():
     ap.add_argument("--ny", type=int, default=224, help="cells in y (224 = the 200,704-triangle mesh)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--restart", type=int, default=10, help="GMRES restart length")
-    ap.add_argument("--inner-tol", type=float, default=1e-2, help="relative tolerance of the FP32 inner solve")
+    ap.add_argument("--restart", type=int, default=20, help="GMRES restart length")
+    ap.add_argument("--inner-tol", type=float, default=1e-4, help="relative tolerance of the FP32 inner solve")
     ap.add_argument("--pre", type=int, default=2, choices=[0, 1, 2],
                     help="preconditioner: 0 none, 1 block Jacobi (Pre1), 2 stencil (Pre2)")
     ap.add_argument("--shots", type=int, default=64, help="shots of the multi-shot batch")
