@@ -10,6 +10,7 @@
 // decompositions are compile-time constants.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "stdg_internal.h"
 #include "tma.h"
@@ -94,6 +95,34 @@ struct FaceReg {
     static constexpr int PER_WARP = SZ_V + SZ_G + SZ_T + SZ_H;
 };
 
+// d = a * b + c on two FP32 lanes at once (Blackwell's packed FP32 FMA)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// acc + sum_{n<NP} a[n] row[n] for a broadcast shared-memory row.  FP32 with NP even: the
+// row starts on an 8-byte boundary, so pairs (n, n+1) come in one 8-byte load and go through
+// one packed FMA (even and odd partial sums, added at the end).
+template <int NP, typename R>
+__device__ __forceinline__ R dot_row(const R (&a)[NP], const R* row, R acc) {
+    if constexpr (std::is_same<R, float>::value && NP % 2 == 0) {
+        const float2* r2 = reinterpret_cast<const float2*>(row);
+        float2 s = make_float2(acc, 0.0f);
+#pragma unroll
+        for (int i = 0; i < NP / 2; ++i) s = ffma2(make_float2(a[2 * i], a[2 * i + 1]), r2[i], s);
+        return s.x + s.y;
+    } else {
+#pragma unroll
+        for (int n = 0; n < NP; ++n) acc = fma(a[n], row[n], acc);
+        return acc;
+    }
+}
+
 // Register-blocked face kernel.  Gather lanes own a column (l, m) of D~_s (both sides, N_phi
 // values each, in registers); scatter lanes own a row (s, n) of D~_s (all l, m).  The rows
 // of v and h they multiply are read by all lanes at once from shared memory (broadcast), so
@@ -161,11 +190,7 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
         for (int kb = 0; kb < DIM * NG; ++kb) {
             R acc = 0;
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const R* vr = sV + (s * DIM * NG + kb) * NPP;
-#pragma unroll
-                for (int n = 0; n < NP; ++n) acc = fma(Dg[s][n], vr[n], acc);
-            }
+            for (int s = 0; s < 2; ++s) acc = dot_row<NP, R>(Dg[s], sV + (s * DIM * NG + kb) * NPP, acc);
             if (gl) {
                 const int k = kb / NG, b = kb % NG;
                 sG[((k * DIM + gl_l) * NG + b) * NP + gl_m] = acc;
@@ -216,11 +241,7 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
             const int k = kb / NG, b = kb % NG;
             R acc = 0;
 #pragma unroll
-            for (int l = 0; l < DIM; ++l) {
-                const R* hr = sH + (symc<DIM>(k, l) * NG + b) * NPP;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc = fma(Ds[l][m], hr[m], acc);
-            }
+            for (int l = 0; l < DIM; ++l) acc = dot_row<NP, R>(Ds[l], sH + (symc<DIM>(k, l) * NG + b) * NPP, acc);
             if (write) atomicAdd(&y[(int64_t)es * NVS + kb * NP + sc_n], acc);
         }
         __syncwarp();
@@ -246,10 +267,12 @@ struct FaceTma {
     static constexpr int SZ_T = round_up(NS * NG * NP, 4);
     static constexpr int SZ_H = round_up(NS * NG * NP, 4);
     static constexpr int PER_WARP = round_up(2 * STAGE + SZ_G + SZ_T + SZ_H, 16 / (int)sizeof(R));
+    // resident blocks of 4 warps requested per SM: a register cap where it costs no spills
+    static constexpr int MIN_BLOCKS = (DIM == 2 && NP == 6) ? 6 : (DIM == 2 && NP == 10) ? 6 : 1;
 };
 
 template <int DIM, int NP, int NG, typename R>
-__global__ void __launch_bounds__(128) face_apply_tma_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+__global__ void __launch_bounds__(128, (FaceTma<DIM, NP, NG, R>::MIN_BLOCKS)) face_apply_tma_kernel(int64_t n_face, const int32_t* __restrict__ fl,
                                                              const int32_t* __restrict__ fr, const R* __restrict__ D,
                                                              const R* __restrict__ lamf, const R* __restrict__ muf,
                                                              const RefTables* __restrict__ rtp, const R* __restrict__ x,
@@ -344,11 +367,7 @@ __global__ void __launch_bounds__(128) face_apply_tma_kernel(int64_t n_face, con
         for (int kb = 0; kb < DIM * NG; ++kb) {
             R acc = 0;
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const R* vr = sV + s * XR + kb * NP;
-#pragma unroll
-                for (int n = 0; n < NP; ++n) acc = fma(Dg[s][n], vr[n], acc);
-            }
+            for (int s = 0; s < 2; ++s) acc = dot_row<NP, R>(Dg[s], sV + s * XR + kb * NP, acc);
             if (gl) sG[((kb / NG * DIM + gl_l) * NG + kb % NG) * NP + gl_m] = acc;
         }
         __syncwarp();
@@ -394,11 +413,7 @@ __global__ void __launch_bounds__(128) face_apply_tma_kernel(int64_t n_face, con
             const int k = kb / NG, b = kb % NG;
             R acc = 0;
 #pragma unroll
-            for (int l = 0; l < DIM; ++l) {
-                const R* hr = sH + (symc<DIM>(k, l) * NG + b) * NP;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc = fma(Ds[l][m], hr[m], acc);
-            }
+            for (int l = 0; l < DIM; ++l) acc = dot_row<NP, R>(Ds[l], sH + (symc<DIM>(k, l) * NG + b) * NP, acc);
             if (write) atomicAdd(&y[(int64_t)es * NVS + kb * NP + sc_n], acc);
         }
         __syncwarp();   // stage st is free for the copy issued in the next iteration
