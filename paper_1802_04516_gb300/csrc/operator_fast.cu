@@ -95,16 +95,6 @@ struct FaceReg {
     static constexpr int PER_WARP = SZ_V + SZ_G + SZ_T + SZ_H;
 };
 
-// d = a * b + c on two FP32 lanes at once (Blackwell's packed FP32 FMA)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
-        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-
 // acc + sum_{n<NP} a[n] row[n] for a broadcast shared-memory row.  FP32 with NP even: the
 // row starts on an 8-byte boundary, so pairs (n, n+1) come in one 8-byte load and go through
 // one packed FMA (even and odd partial sums, added at the end).

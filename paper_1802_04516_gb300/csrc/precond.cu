@@ -13,8 +13,10 @@
 // (all pairs of a round rotate concurrently), in FP64.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "stdg_internal.h"
+#include "tma.h"
 
 namespace stdg {
 
@@ -293,7 +295,8 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
     const R* r = r0;
     constexpr int N = DIM * NP;
     static_assert(N <= 32, "register-blocked block-Jacobi apply needs d*N_phi <= 32");
-    __shared__ R s_r[4][N * NG], s_w[4][N * NG];
+    __shared__ __align__(16) R s_r[4][N * NG];
+    __shared__ __align__(16) R s_w[4][N * NG];
     if (ridx) r += (int64_t)(*ridx) * ld_vec;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     R* sr = s_r[warp];
@@ -328,8 +331,18 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
         for (int a = 0; a < NG; ++a) u[a] = 0;
 #pragma unroll
         for (int row = 0; row < N; ++row)
+            if constexpr (std::is_same<R, float>::value && NG % 2 == 0) {   // time-node pairs, packed FMA
+                const float2* s2 = reinterpret_cast<const float2*>(sr + row * NG);
 #pragma unroll
-            for (int a = 0; a < NG; ++a) u[a] = fma(Vc[row], sr[row * NG + a], u[a]);
+                for (int a = 0; a < NG; a += 2) {
+                    const float2 p = ffma2(make_float2(Vc[row], Vc[row]), s2[a / 2], make_float2(u[a], u[a + 1]));
+                    u[a] = p.x;
+                    u[a + 1] = p.y;
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < NG; ++a) u[a] = fma(Vc[row], sr[row * NG + a], u[a]);
+            }
         if (act) {
 #pragma unroll
             for (int a = 0; a < NG; ++a) {
@@ -346,8 +359,18 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
         for (int a = 0; a < NG; ++a) acc[a] = 0;
 #pragma unroll
         for (int qq = 0; qq < N; ++qq)
+            if constexpr (std::is_same<R, float>::value && NG % 2 == 0) {
+                const float2* w2 = reinterpret_cast<const float2*>(sw + qq * NG);
 #pragma unroll
-            for (int a = 0; a < NG; ++a) acc[a] = fma(Vr[qq], sw[qq * NG + a], acc[a]);
+                for (int a = 0; a < NG; a += 2) {
+                    const float2 p = ffma2(make_float2(Vr[qq], Vr[qq]), w2[a / 2], make_float2(acc[a], acc[a + 1]));
+                    acc[a] = p.x;
+                    acc[a + 1] = p.y;
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < NG; ++a) acc[a] = fma(Vr[qq], sw[qq * NG + a], acc[a]);
+            }
         if (act) {
             const int k = q / NP, n = q % NP;
             R* ze = z + e * (int64_t)(N * NG);

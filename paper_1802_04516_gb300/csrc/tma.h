@@ -1,5 +1,6 @@
-// Inline-PTX helpers for one-warp TMA pipelines: bulk global->shared copies
-// (cp.async.bulk) completing on shared-memory mbarriers, with bounded waits.
+// Inline-PTX helpers: bulk global->shared copies (cp.async.bulk) completing on
+// shared-memory mbarriers, with bounded waits, for one-warp TMA pipelines; and the packed
+// FP32 FMA of sm_100-class GPUs.
 #pragma once
 #include <cstdint>
 
@@ -30,6 +31,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long li
         if (ok) return true;
     }
     return false;
+}
+
+// d = a * b + c on two FP32 lanes at once (Blackwell's packed FP32 FMA)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
 }
 
 }  // namespace stdg
