@@ -170,9 +170,7 @@ def e2e_steps(torch, s, w, steps, stream):
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
 # 16,384-triangle copy of the 2D p = p_gamma = 3 construction (profiles/traffic_face_pre2_c2_16k.md),
 # scaled by the units one launch processes.  Valid for that shape only.
-# The face kernel has changed since its counters were taken (packed FP32 FMA), so it reports
-# no traffic until it is measured again.
-TRAFFIC_PER_UNIT = {"pre2_local_fp32": (429950208 + 2902016) / 16384}
+TRAFFIC_PER_UNIT = {"face_fp32": (50544128 + 4608) / 24768, "pre2_local_fp32": (429949184 + 2444032) / 16384}
 
 
 def _traffic(w, key, units):
