@@ -17,8 +17,9 @@
 //
 // Solvers
 //   CG        (Crank-Nicolson)  r = b - A x; standard recurrences; FP64 dots.
-//   GMRES(m)  (space-time DG)   restarted, classical Gram-Schmidt with one
-//                               re-orthogonalisation pass, Givens rotations on the device,
+//   GMRES(m)  (space-time DG)   restarted, classical Gram-Schmidt with a second
+//                               pass only where the first one cancelled more than 99%
+//                               of ||w||^2, Givens rotations on the device,
 //                               true residual checked at every restart.
 //   Mixed     FP64 iterative refinement around an FP32 CG / GMRES: r = b - A64 x in FP64,
 //             solve A32 d = r/|r| to inner_tol, x += |r| d, stop at rel_tol in FP64.
@@ -47,6 +48,7 @@ struct ShotScalars {
     double red[3];                                // reduced sums handed between warps
     int jj;            // basis columns this shot uses in the current cycle
     int active;        // still iterating in the current cycle / CG solve
+    int reorth;        // this Arnoldi step needs the second Gram-Schmidt pass
     int converged, zero_x;                        // zero_x: b_s = 0, so x_s = 0
     // FP64 refinement level (mixed precision)
     double ir_bnorm, ir_tol_abs, ir_rnorm, ir_scale;
@@ -449,11 +451,16 @@ __global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t nvec, int64_t ldv,
     const int J = sc->j;
     for (int k0 = 0; k0 <= J; k0 += kDotChunk) {
         Acc<R> acc[kDotChunk];
+        Acc<R> ww;                                // ||w||^2, first chunk only
         const int kn = min(kDotChunk, J + 1 - k0);
         seg_loop<R>(nvec,
             [&](int64_t i) {
                 R wv[VW];
                 VL<R>::ld(w + i, wv);
+                if (k0 == 0) {
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) ww.add(wv[u], wv[u]);
+                }
 #pragma unroll
                 for (int kk = 0; kk < kDotChunk; ++kk)
                     if (kk < kn) {
@@ -464,6 +471,7 @@ __global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t nvec, int64_t ldv,
                     }
             },
             [&](int64_t i) {
+                if (k0 == 0) ww.add(w[i], w[i]);
 #pragma unroll
                 for (int kk = 0; kk < kDotChunk; ++kk)
                     if (kk < kn) acc[kk].add(V[(int64_t)(k0 + kk) * ldv + i], w[i]);
@@ -471,6 +479,7 @@ __global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t nvec, int64_t ldv,
 #pragma unroll
         for (int kk = 0; kk < kDotChunk; ++kk)   // constant bound keeps acc[] in registers
             if (kk < kn) put_partial(part, k0 + kk, acc[kk].value());   // kn is uniform over the block
+        if (k0 == 0) put_partial(part, J + 1, ww.value());
     }
 }
 
@@ -482,6 +491,7 @@ __global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t nvec, int64_
                                                             R* __restrict__ w, double* __restrict__ part) {
     constexpr int VW = VL<R>::W;
     const int J = sc->j;
+    if (!ss[blockIdx.y].reorth) return;           // this shot's first pass was enough
     __shared__ R h[kMaxRestart + 2];
     for (int k = threadIdx.x; k <= J; k += blockDim.x) h[k] = (R)ss[blockIdx.y].hpass[k];
     __syncthreads();
@@ -527,17 +537,35 @@ __global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t nvec, int64_
 }
 
 // hpass_s[k] = reduced slot k (k = 0..j); pass 0 starts the Hessenberg column, pass 1 adds
+// Pass 0 also decides, per shot, whether the second pass is needed: one classical
+// Gram-Schmidt pass leaves w orthogonal to the basis to about eps ||w|| / ||w - V h||, so the
+// pass is repeated when that ratio would exceed 10, i.e. when
+// ||w - V h||^2 = ||w||^2 - |h|^2 < 1e-2 ||w||^2 (V orthonormal; the dots are FP64-accurate).
 __global__ void __launch_bounds__(kFinThreads) gm_mdot_final_kernel(const DevScalars* sc, ShotScalars* ss,
                                                                     const double* part, int ns, int G, int pass) {
     const int J = sc->j;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int q = warp; q < (J + 1) * ns; q += nw) {
+    const int nk = pass == 0 ? J + 2 : J + 1;    // pass 0: slot J+1 holds ||w||^2
+    for (int q = warp; q < nk * ns; q += nw) {
         const int k = q / ns, s = q % ns;
+        if (pass == 1 && !ss[s].reorth) continue;
         const double v = warp_sum(slot(part, k, s, ns, G), G);
         if ((threadIdx.x & 31) == 0) {
-            ss[s].hpass[k] = v;
-            ss[s].hcol[k] = pass == 0 ? v : ss[s].hcol[k] + v;
+            if (k <= J) {
+                ss[s].hpass[k] = v;
+                ss[s].hcol[k] = pass == 0 ? v : ss[s].hcol[k] + v;
+            } else {
+                ss[s].red[0] = v;
+            }
         }
+    }
+    if (pass != 0) return;
+    __syncthreads();
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        ShotScalars& t = ss[s];
+        double h2 = 0.0;
+        for (int k = 0; k <= J; ++k) h2 += t.hcol[k] * t.hcol[k];
+        t.reorth = t.red[0] - h2 < 1e-2 * t.red[0];
     }
 }
 
@@ -983,7 +1011,8 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
                           } else {
                               F.check(apply_idx(V, &sc->j, w));
                           }
-                          // classical Gram-Schmidt twice, in three passes over the basis
+                          // classical Gram-Schmidt: dots and ||w||^2; a second pass (with the first
+                          // subtraction fused in) only for the shots that need it; subtraction + norm
                           gm_mdot_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, sc, V, w, part); note_launch(c);
                           gm_mdot_final_kernel<<<1, kFinThreads, 0, c->stream>>>(sc, ss, part, ns, G, 0); note_launch(c);
                           gm_orth_fused_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, sc, ss, V, w, part); note_launch(c);
