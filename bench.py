@@ -104,6 +104,21 @@ def peaks():
         return {}
 
 
+def max_over_ranks(torch, dist, x):
+    """This rank's x -> the maximum over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_shot_offset(rank):
+    """x-shift of this rank's Ricker shot: with N ranks every rank runs its own independent
+    shot (weak scaling, no collective on the data path)."""
+    return 0.01 * rank
+
+
 def build_solver(w, precision, stream, shot_offset=0.0, restart=20, inner_tol=1e-4, use_graph=True, pre=2):
     from paper_1802_04516_gb300.binding import Solver
     s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=restart,
@@ -136,11 +151,8 @@ def time_steps(torch, s, w, steps, warmup, stream, dist):
         launches += s.query(11)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(torch, dist, e0.elapsed_time(e1))
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     return ms, iters, launches, st
 
@@ -278,11 +290,7 @@ def adjoint_section(torch, args, stream, dist, world):
     t0 = time.perf_counter()
     loss, gl, gm, gr, st = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=20)
     torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([sec], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        sec = float(tt.item())
+    sec = max_over_ranks(torch, dist, time.perf_counter() - t0)
     s.close()
     return {"workload": "c5_adjoint: %d triangles, p=p_gamma=2, %d shots, %d receivers, %d slabs%s, dt=%.4g, "
                         "checkpoint every 20" % (w.n_elem, w.n_shots, len(w.receivers), w.n_steps,
@@ -406,7 +414,7 @@ def main():
     stream = torch.cuda.Stream()
     pk = peaks()
     with torch.cuda.stream(stream):
-        s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=0.01 * rank, restart=args.restart,
+        s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=rank_shot_offset(rank), restart=args.restart,
                          inner_tol=args.inner_tol, use_graph=not args.host_loop, pre=args.pre)
         n_face = s.n_face
         dofs = dofs_per_slab(w, n_face)
@@ -422,10 +430,11 @@ def main():
             per_iter["pre2_local"] = 1
         roof = dominant_roofline(cands, per_iter)
         e2e_ms, h2d, d2h = e2e_steps(torch, s, w, max(1, args.steps // 2), stream)
+        e2e_ms = max_over_ranks(torch, dist, e2e_ms)
         e2e_value = dofs * max(1, args.steps // 2) / (e2e_ms * 1e-3) * world
         fp64 = None
         if not args.no_fp64 and args.fp64_steps > 0:
-            s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=0.01 * rank, restart=args.restart,
+            s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=rank_shot_offset(rank), restart=args.restart,
                                use_graph=not args.host_loop, pre=args.pre)
             ms64, it64, _, _ = time_steps(torch, s64, w, args.fp64_steps, 1, stream, dist)
             fp64 = {"value": world * dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
