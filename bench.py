@@ -36,6 +36,9 @@ FP64_PEAK_TFLOPS = 1.25          # nominal dense FP64 of one GB300 (no measured 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
+METRIC = "space-time DOF-steps/s (velocity+stress) at 1e-8 rel residual, mixed FP32/FP64"
+
+
 def dofs_per_slab(w, n_face):
     from math import comb
     nphi = comb(w.p + w.dim, w.dim)
@@ -357,7 +360,7 @@ def run_reference(args, rank, world):
         return
     steps = max(1, args.steps)
     cb = cpu_baseline(max_seconds=max(5.0, 4.0 * steps), steps=max(steps + args.warmup, 3))
-    line = {"impl": "reference", "metric": "space-time DOF-steps/s (velocity+stress) at 1e-8 rel residual",
+    line = {"impl": "reference", "metric": METRIC,
             "value": cb["value"], "unit": "DOF-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": "c2_layered_slivers_p3 (scaled copy, CPU oracle)",
@@ -448,7 +451,7 @@ def main():
         return
     cb = None if args.no_cpu_baseline else cpu_baseline()
     line = {
-        "metric": "space-time DOF-steps/s (velocity+stress) at 1e-8 rel residual, mixed FP32/FP64",
+        "metric": METRIC,
         "value": value, "unit": "DOF-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 operator/Krylov + f64 refinement", "data": "synthetic",
