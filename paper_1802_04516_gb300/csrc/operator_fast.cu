@@ -1,13 +1,15 @@
-// Face kernel of the Schur velocity operator with compile-time sizes (dimension d,
+// Face kernels of the Schur velocity operator with compile-time sizes (dimension d,
 // N_phi, N_gamma) for the production shapes; other shapes use the generic kernel in
 // kernels.cu.  Same arithmetic as the generic kernel (Eq. velocity.sys with Q~ = -D^T
 // and the orthonormalised dual basis):
 //   g = sum_side D~_side^T v_side,  t = E_j : g,  h = scale * S t,  y_side += D~_side h.
-// One warp per face.  The face's D~ blocks are staged in shared memory twice, as D~ and
-// as its transpose, each row padded to a multiple of 16 bytes, so that every inner
-// product of the gather (rows of D~^T against rows of v) and of the scatter (rows of D~
-// against rows of h) runs on 128-bit shared-memory loads; all loop bounds and index
-// decompositions are compile-time constants.
+// One warp per face.  Lanes hold one column (gather) and one row (scatter) of the face's
+// D~ blocks in registers; the rows of v and h they multiply are read by all lanes at once
+// from shared memory (broadcast), in adjacent pairs through one 8-byte load and one packed
+// FP32 FMA.  Two variants: a register kernel that loops over the shots of a stacked
+// multi-shot vector with D~ kept in registers, and a single-shot kernel that streams the
+// next face's D~ block and element rows into shared memory with cp.async.bulk while the
+// warp computes the current face.
 #include <algorithm>
 #include <cstdint>
 #include <type_traits>
@@ -21,58 +23,7 @@ template <typename R> struct Vec;
 template <> struct Vec<float> { using T = float4; static constexpr int W = 4; };
 template <> struct Vec<double> { using T = double2; static constexpr int W = 2; };
 
-template <typename R>
-__device__ __forceinline__ R dotv(const R* __restrict__ a, const R* __restrict__ b, int nv);
-template <>
-__device__ __forceinline__ float dotv<float>(const float* __restrict__ a, const float* __restrict__ b, int nv) {
-    float s = 0.f;
-    const float4* A = reinterpret_cast<const float4*>(a);
-    const float4* B = reinterpret_cast<const float4*>(b);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if (i < nv) {
-            const float4 x = A[i], y = B[i];
-            s = fmaf(x.x, y.x, s);
-            s = fmaf(x.y, y.y, s);
-            s = fmaf(x.z, y.z, s);
-            s = fmaf(x.w, y.w, s);
-        }
-    }
-    return s;
-}
-template <>
-__device__ __forceinline__ double dotv<double>(const double* __restrict__ a, const double* __restrict__ b, int nv) {
-    double s = 0.0;
-    const double2* A = reinterpret_cast<const double2*>(a);
-    const double2* B = reinterpret_cast<const double2*>(b);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        if (i < nv) {
-            const double2 x = A[i], y = B[i];
-            s = fma(x.x, y.x, s);
-            s = fma(x.y, y.y, s);
-        }
-    }
-    return s;
-}
-
 __host__ __device__ constexpr int round_up(int v, int w) { return (v + w - 1) / w * w; }
-
-template <int DIM, int NP, int NG, typename R>
-struct FaceFast {
-    static constexpr int NS = DIM == 2 ? 3 : 6;
-    static constexpr int W = Vec<R>::W;
-    static constexpr int NPP = (NP + W - 1) / W * W;     // padded row length
-    static constexpr int NV = NPP / W;                   // vectors per row
-    static constexpr int RD = 2 * DIM * NP;              // rows of D~ (s,l,n) and of D~^T (s,l,m)
-    static constexpr int NVS = DIM * NG * NP;            // values per element
-    static constexpr int SZ_D = RD * NPP;
-    static constexpr int SZ_V = 2 * DIM * NG * NPP;      // rows (s,k,b)
-    static constexpr int SZ_G = round_up(DIM * DIM * NG * NP, W);   // [k][l][b][m]
-    static constexpr int SZ_T = round_up(NS * NG * NP, W);          // [c][b][m]
-    static constexpr int SZ_H = NS * NG * NPP;           // rows (c,b)
-    static constexpr int PER_WARP = 2 * SZ_D + SZ_V + SZ_G + SZ_T + SZ_H;
-};
 
 template <int DIM>
 __device__ __forceinline__ int symc(int a, int b) {
