@@ -20,6 +20,7 @@ int dev_alloc(stdg_ctx* c, void** p, size_t bytes) {
         return e == cudaErrorMemoryAllocation ? STDG_ENOMEM : STDG_ECUDA;
     }
     c->allocs.push_back(*p);
+    c->alloc_bytes.push_back(bytes);
     c->bytes += bytes;
     return STDG_OK;
 }
@@ -27,7 +28,12 @@ int dev_alloc(stdg_ctx* c, void** p, size_t bytes) {
 void dev_release(stdg_ctx* c, void* p) {
     if (!p) return;
     auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
-    if (it != c->allocs.end()) c->allocs.erase(it);
+    if (it != c->allocs.end()) {
+        const size_t k = (size_t)(it - c->allocs.begin());
+        c->bytes -= c->alloc_bytes[k];
+        c->allocs.erase(it);
+        c->alloc_bytes.erase(c->alloc_bytes.begin() + (int64_t)k);
+    }
     cudaFree(p);
 }
 
@@ -36,6 +42,7 @@ static void dev_free(stdg_ctx* c, void* p) { dev_release(c, p); }
 void dev_free_all(stdg_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    c->alloc_bytes.clear();
     c->bytes = 0;
 }
 
@@ -83,6 +90,10 @@ static int alloc_state(stdg_ctx* c, int n_shots) {
         if ((rc = dev_alloc(c, &c->d_p2y, sizeof(double) * c->nvel * n_shots)) != STDG_OK) return rc;
         if ((rc = dev_alloc(c, &c->d_p2t, sizeof(double) * c->nvel * n_shots)) != STDG_OK) return rc;
     }
+    // the receiver records are laid out per shot: start them over for the new shot count
+    dev_free(c, c->d_records);
+    c->d_records = nullptr;
+    c->rec_cap_steps = 0;
     c->n_shots = n_shots;
     c->rec_steps = 0;
     solver_invalidate_graph(c);
@@ -262,14 +273,34 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     void* keep_rt = c->d_rt;
     void* keep_gl = c->d_gl8;
     void* keep_err = c->d_err;
-    for (void* p : c->allocs)
-        if (p != keep_rt && p != keep_gl && p != keep_err) cudaFree(p);
-    c->allocs.assign({keep_rt, keep_gl, keep_err});
+    {
+        std::vector<void*> keep_p;
+        std::vector<size_t> keep_b;
+        c->bytes = 0;
+        for (size_t k = 0; k < c->allocs.size(); ++k) {
+            void* p = c->allocs[k];
+            if (p == keep_rt || p == keep_gl || p == keep_err) {
+                keep_p.push_back(p);
+                keep_b.push_back(c->alloc_bytes[k]);
+                c->bytes += c->alloc_bytes[k];
+            } else {
+                cudaFree(p);
+            }
+        }
+        c->allocs.swap(keep_p);
+        c->alloc_bytes.swap(keep_b);
+    }
     c->d_face_l = c->d_face_r = nullptr;
     c->d_elem_face = nullptr;
     c->d_preV = c->d_preLam = c->d_preB = nullptr;
     c->d_preV32 = c->d_preB32 = nullptr;
+    c->d_pre2 = nullptr;
+    c->d_pre2_32 = nullptr;
+    c->d_p2y = c->d_p2t = nullptr;
+    c->d_p2status = nullptr;
     c->pre_dt = -1.0;
+    c->rec_cap_steps = 0;
+    c->rec_steps = 0;
     c->d_X = c->d_Jinv = c->d_detJ = c->d_faceX = c->d_shift = c->d_normal = c->d_xc = c->d_hj = nullptr;
     c->d_D = c->d_L = c->d_Mdual = nullptr;
     c->d_D32 = nullptr;

@@ -146,6 +146,7 @@ struct stdg_ctx {
     int64_t last_launches = 0;   // kernel executions of the last stdg_step call    // kernels recorded per open loop-body scope (launch counting)
     size_t bytes = 0;
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_bytes;   // size of each entry of allocs
 };
 
 // Launch counting: every kernel launch of the library adds one to the innermost open

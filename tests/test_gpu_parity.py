@@ -358,3 +358,31 @@ def test_stencil_preconditioned_mixed_solves_converge_on_the_inversion_medium():
         assert st["status"] == 0
         worst = max(worst, st["iters_max"])
     assert worst < 400, worst
+
+
+def test_context_reuse_after_new_mesh_and_new_shot_count():
+    # one context re-meshed, then given more shots (receivers kept): the same states and
+    # records as fresh contexts
+    need_gpu()
+    w1 = synth.scaled("c4", ny=6, steps=2, n_shots=1)
+    w2 = synth.scaled("c2", ny=6, steps=2, p=2)
+    s = gpu_solver(w1, precision="mixed", rel_tol=1e-12, max_iters=20000, preconditioner=2)
+    s.step(w1.dt, 2)
+    s.set_mesh(w2.xyz, w2.elem_vert, w2.period)
+    s.set_material(w2.lam, w2.mu, w2.rho)
+    s.set_sources(w2.shots_xs, w2.shots_dir, w2.f0, w2.t_delay, w2.a1)
+    s.set_receivers(w2.receivers)
+    s.step(w2.dt, 2)
+    f = gpu_solver(w2, precision="mixed", rel_tol=1e-12, max_iters=20000, preconditioner=2)
+    f.step(w2.dt, 2)
+    assert rel_l2(s.get_state()[0], f.get_state()[0]) < 1e-10
+    xs = np.array([w2.shots_xs[0], w2.shots_xs[0] + [0.3, 0.0], w2.shots_xs[0] + [-0.3, -0.1]])
+    dirs = np.tile([0.0, 1.0], (3, 1))
+    s.set_sources(xs, dirs, w2.f0, w2.t_delay, w2.a1)
+    s.step(w2.dt, 3)
+    f.set_sources(xs, dirs, w2.f0, w2.t_delay, w2.a1)
+    f.set_receivers(w2.receivers)
+    f.step(w2.dt, 3)
+    ra, rb = s.read_receivers(), f.read_receivers()
+    assert ra.shape == rb.shape == (3, 3, len(w2.receivers), 2)
+    assert np.abs(ra - rb).max() <= 1e-10 * np.abs(rb).max()
