@@ -43,7 +43,9 @@ struct FaceReg {
     static constexpr int SZ_G = round_up(DIM * DIM * NG * NP, W);   // g[k][l][b][m]
     static constexpr int SZ_T = round_up(NS * NG * NP, W);          // t[c][b][m]
     static constexpr int SZ_H = NS * NG * NPP;           // rows (c,b) of h
-    static constexpr int PER_WARP = SZ_V + SZ_G + SZ_T + SZ_H;
+    static constexpr int PER_WARP = SZ_V + SZ_G + SZ_T + SZ_H;   // per shot in flight
+    // several shots: two per warp (one per half-warp) when a column and a row of D~ fit in 16 lanes
+    static constexpr int HALVES = (DIM * NP <= 16 && 2 * NP <= 16) ? 2 : 1;
 };
 
 // acc + sum_{n<NP} a[n] row[n] for a broadcast shared-memory row.  FP32 with NP even: the
@@ -68,7 +70,7 @@ __device__ __forceinline__ R dot_row(const R (&a)[NP], const R* row, R acc) {
 // values each, in registers); scatter lanes own a row (s, n) of D~_s (all l, m).  The rows
 // of v and h they multiply are read by all lanes at once from shared memory (broadcast), so
 // almost every instruction of the inner products is an FMA.
-template <int DIM, int NP, int NG, typename R>
+template <int DIM, int NP, int NG, typename R, int HALVES>
 __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, const int32_t* __restrict__ fl,
                                                               const int32_t* __restrict__ fr, const R* __restrict__ D,
                                                               const R* __restrict__ lamf, const R* __restrict__ muf,
@@ -78,6 +80,8 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
     using F = FaceReg<DIM, NP, NG, R>;
     const R* x = x0;
     constexpr int NS = F::NS, NPP = F::NPP, NVS = F::NVS;
+    constexpr int LANES = 32 / HALVES;
+    static_assert(HALVES == 1 || (DIM * NP <= 16 && 2 * NP <= 16), "two shots per warp need d*N_phi <= 16");
     static_assert(DIM * NP <= 32 && 2 * NP <= 32, "register-blocked face kernel needs d*N_phi <= 32");
     extern __shared__ __align__(16) unsigned char smraw[];
     R* sm = reinterpret_cast<R*>(smraw);
@@ -85,16 +89,18 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     __shared__ R sS[NG * NG];
     for (int t = threadIdx.x; t < NG * NG; t += blockDim.x) sS[t] = (R)rtp->S[t];
-    R* sV = sm + warp * F::PER_WARP;   // [s][k][b][n] rows padded
+    // with HALVES = 2 each half-warp works on its own shot (same D~ registers, own buffers)
+    const int hv = lane / LANES, li = lane % LANES;
+    R* sV = sm + (warp * HALVES + hv) * F::PER_WARP;   // [s][k][b][n] rows padded
     R* sG = sV + F::SZ_V;              // [k][l][b][m]
     R* sT = sG + F::SZ_G;              // [c][b][m]
     R* sH = sT + F::SZ_T;              // [c][b][m] rows padded
-    for (int t = lane; t < F::PER_WARP; t += 32) sV[t] = (R)0;   // padding stays zero
+    for (int t = li; t < F::PER_WARP; t += LANES) sV[t] = (R)0;   // padding stays zero
     __syncthreads();
-    const bool gl = lane < DIM * NP;          // gather lane: column (gl_l, gl_m)
-    const int gl_l = gl ? lane / NP : 0, gl_m = gl ? lane % NP : 0;
-    const bool sc = lane < 2 * NP;            // scatter lane: row (sc_s, sc_n)
-    const int sc_s = sc ? lane / NP : 0, sc_n = sc ? lane % NP : 0;
+    const bool gl = li < DIM * NP;            // gather lane: column (gl_l, gl_m)
+    const int gl_l = gl ? li / NP : 0, gl_m = gl ? li % NP : 0;
+    const bool sc = li < 2 * NP;              // scatter lane: row (sc_s, sc_n)
+    const int sc_s = sc ? li / NP : 0, sc_n = sc ? li % NP : 0;
     constexpr int DFACE = 2 * DIM * NP * NP;
     for (int64_t f = blockIdx.x * (int64_t)wpb + warp; f < n_face; f += (int64_t)gridDim.x * wpb) {
         const int el = fl[f], er = fr[f];
@@ -111,18 +117,20 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
             for (int m = 0; m < NP; ++m) Ds[l][m] = sc ? Df[((sc_s * DIM + l) * NP + sc_n) * NP + m] : (R)0;
         const R lam = lamf[f], mu = muf[f];
         // D~ stays in registers for every shot of the batch
-        for (int shot = 0; shot < nshots; ++shot) {
+        for (int s0 = 0; s0 < nshots; s0 += HALVES) {
+        const bool valid = s0 + hv < nshots;
+        const int shot = valid ? s0 + hv : s0;
         R* y = y0 + (int64_t)shot * nvec;
         // ---- neighbours' values, rows (s,k,b) padded
         const R* xl = x + (int64_t)shot * nvec + (int64_t)el * NVS;
         const R* xr = x + (int64_t)shot * nvec + (int64_t)(er >= 0 ? er : el) * NVS;
 #pragma unroll
-        for (int e0 = 0; e0 < NVS; e0 += 32) {
-            const int e = e0 + lane;
+        for (int e0 = 0; e0 < NVS; e0 += LANES) {
+            const int e = e0 + li;
             if (e < NVS) {
                 const int row = e / NP, n = e % NP;
-                sV[row * NPP + n] = xl[e];
-                sV[(DIM * NG + row) * NPP + n] = er >= 0 ? xr[e] : (R)0;
+                sV[row * NPP + n] = valid ? xl[e] : (R)0;
+                sV[(DIM * NG + row) * NPP + n] = valid && er >= 0 ? xr[e] : (R)0;
             }
         }
         __syncwarp();
@@ -141,8 +149,8 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
         // ---- t = E_j : g
         constexpr int NT_OUT = NS * NG * NP;
 #pragma unroll
-        for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
-            const int e = e0 + lane;
+        for (int e0 = 0; e0 < NT_OUT; e0 += LANES) {
+            const int e = e0 + li;
             if (e < NT_OUT) {
                 const int c = e / (NG * NP);
                 const int bm = e % (NG * NP);
@@ -163,8 +171,8 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
         __syncwarp();
         // ---- h = scale * S t  (rows (c,b), padded)
 #pragma unroll
-        for (int e0 = 0; e0 < NT_OUT; e0 += 32) {
-            const int e = e0 + lane;
+        for (int e0 = 0; e0 < NT_OUT; e0 += LANES) {
+            const int e = e0 + li;
             if (e < NT_OUT) {
                 const int c = e / (NG * NP), b = (e / NP) % NG, m = e % NP;
                 R acc = 0;
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
         __syncwarp();
         // ---- scatter: y_s[k][b][n] += sum_l sum_m D~_s[l][n][m] h[(k,l)][b][m]
         const int es = sc_s == 0 ? el : er;
-        const bool write = sc && es >= 0;
+        const bool write = sc && es >= 0 && valid;
 #pragma unroll
         for (int kb = 0; kb < DIM * NG; ++kb) {
             const int k = kb / NG, b = kb % NG;
@@ -380,11 +388,21 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
     }
     using F = FaceReg<DIM, NP, NG, R>;
     const int wpb = 4;
-    const size_t smem = sizeof(R) * (size_t)wpb * F::PER_WARP;
-    cudaFuncSetAttribute(face_apply_fast_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 1 << 30);
-    face_apply_fast_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
-        c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, nshots, c->nvel);
+    if (F::HALVES == 2 && nshots >= 2) {
+        constexpr int H = F::HALVES;
+        const size_t smem = sizeof(R) * (size_t)wpb * H * F::PER_WARP;
+        cudaFuncSetAttribute(face_apply_fast_kernel<DIM, NP, NG, R, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        face_apply_fast_kernel<DIM, NP, NG, R, H><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
+            c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, nshots, c->nvel);
+    } else {
+        const size_t smem = sizeof(R) * (size_t)wpb * F::PER_WARP;
+        cudaFuncSetAttribute(face_apply_fast_kernel<DIM, NP, NG, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        face_apply_fast_kernel<DIM, NP, NG, R, 1><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
+            c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, nshots, c->nvel);
+    }
     note_launch(c);
     return cudaGetLastError();
 }
