@@ -1,4 +1,4 @@
-"""The sliver-element study of Sec. 6 (Table NT5.1) on the GPU, on meshes of our own: GMRES
+"""The sliver-element study of Sec. 6.5 (Table NT5.1) on the GPU, on meshes of our own: GMRES
 iterations per slab without preconditioner, with the block-Jacobi Pre1 and with the
 stencil Pre2, (p, p_gamma) = (4, 2) as in the paper, on a jittered layered mesh without
 and with 1% sliver elements (incircle reduced ~70x), the same plane P wave and slab size
