@@ -7,7 +7,8 @@
 // D~ blocks in registers; the rows of v and h they multiply are read by all lanes at once
 // from shared memory (broadcast), in adjacent pairs through one 8-byte load and one packed
 // FP32 FMA.  Two variants: a register kernel that loops over the shots of a stacked
-// multi-shot vector with D~ kept in registers, and a single-shot kernel that streams the
+// multi-shot vector with D~ kept in registers (two shots at a time, one per half-warp, when
+// a column and a row of D~ fit in 16 lanes: 2D with p <= 2), and a single-shot kernel that streams the
 // next face's D~ block and element rows into shared memory with cp.async.bulk while the
 // warp computes the current face.
 #include <algorithm>
@@ -69,7 +70,8 @@ __device__ __forceinline__ R dot_row(const R (&a)[NP], const R* row, R acc) {
 // Register-blocked face kernel.  Gather lanes own a column (l, m) of D~_s (both sides, N_phi
 // values each, in registers); scatter lanes own a row (s, n) of D~_s (all l, m).  The rows
 // of v and h they multiply are read by all lanes at once from shared memory (broadcast), so
-// almost every instruction of the inner products is an FMA.
+// almost every instruction of the inner products is an FMA.  HALVES = 2: both half-warps
+// hold the same D~ registers and work on shots s0 and s0 + 1, each with its own shared rows.
 template <int DIM, int NP, int NG, typename R, int HALVES>
 __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, const int32_t* __restrict__ fl,
                                                               const int32_t* __restrict__ fr, const R* __restrict__ D,
