@@ -30,7 +30,8 @@ Layouts: velocity  [elem][component][time node][space node];
 Pins (tests/test_oracle_operators.py): Q~ = -D^T (Theorem 1 proof), symmetry and
 positive definiteness of the Crank-Nicolson matrix by brute force (Theorems 1, 2),
 zero momentum forcing by a constant stress, the linear-velocity patch test, and
-invariance under element renumbering.
+invariance under element renumbering; for the paper's 2D tensor dual basis
+(dual="quad"), tests/test_oracle_quad_dual.py.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -67,21 +68,65 @@ def compliance_apply(sig, lam, mu, dim):
     return (sig - (coef * tr)[..., None, None] * np.eye(dim)) / (2.0 * np.asarray(mu)[..., None, None])
 
 
+def bilinear_inverse(P, x, iters=40):
+    """Reference coordinates (u, v) in [0, 1]^2 of points x (..., q, 2) under the bilinear map
+    F(u, v) = (1-u)(1-v) P0 + u(1-v) P1 + u v P2 + (1-u) v P3 of the quadrilaterals P (..., 4, 2),
+    by Newton's method from the centre (the map is one-to-one on a convex quadrilateral)."""
+    P0, P1, P2, P3 = (P[..., k, None, :] for k in range(4))
+    a, b, c = P1 - P0, P3 - P0, P0 - P1 + P2 - P3          # F = P0 + u a + v b + u v c
+    u = np.full(x.shape[:-1], 0.5)
+    v = np.full(x.shape[:-1], 0.5)
+    for _ in range(iters):
+        r = P0 + u[..., None] * a + v[..., None] * b + (u * v)[..., None] * c - x
+        Fu = a + v[..., None] * c
+        Fv = b + u[..., None] * c
+        det = Fu[..., 0] * Fv[..., 1] - Fu[..., 1] * Fv[..., 0]
+        du = (r[..., 0] * Fv[..., 1] - r[..., 1] * Fv[..., 0]) / det
+        dv = (Fu[..., 0] * r[..., 1] - Fu[..., 1] * r[..., 0]) / det
+        u, v = u - du, v - dv
+    r = P0 + u[..., None] * a + v[..., None] * b + (u * v)[..., None] * c - x
+    scale = np.abs(P - P.mean(axis=-2, keepdims=True)).max()
+    if np.abs(r).max() > 1e-12 * scale:
+        raise ValueError("bilinear inverse did not converge (non-convex dual quadrilateral?)")
+    return np.stack([u, v], axis=-1)
+
+
 class Discretization:
-    def __init__(self, mesh, p, p_gamma, lam, mu, rho, quad_n=None):
+    """Blocks of Sec. 4 on a DualMesh.  dual="taylor": the dual basis is the rescaled
+    monomials of total degree <= p in physical space (the paper's 3D choice, used in 2D as
+    well).  dual="quad" (2D, meshes without boundary faces): the paper's 2D choice of Sec. 3
+    (paragraph on space-time basis functions), the (p+1)^2 tensor-product space on the unit
+    square carried to the dual quadrilateral (b_l, face vertex 0, b_r, face vertex 1) by its
+    bilinear map, spanned here by u^a v^b, 0 <= a, b <= p (the same space as the tensor
+    nodal basis).  The discrete solution depends on the space only, not on the basis."""
+
+    def __init__(self, mesh, p, p_gamma, lam, mu, rho, quad_n=None, dual="taylor"):
         d = self.dim = mesh.dim
         self.mesh, self.p, self.p_gamma = mesh, p, p_gamma
         self.lam_e = np.asarray(lam, dtype=np.float64)
         self.mu_e = np.asarray(mu, dtype=np.float64)
         self.rho = np.asarray(rho, dtype=np.float64)
         self.ref = RefBasis(d, p)
-        self.exps = monomial_exponents(d, p)
+        self.dual = dual
+        if dual == "taylor":
+            self.exps = monomial_exponents(d, p)
+        elif dual == "quad":
+            if d != 2 or not mesh.interior.all():
+                raise ValueError("the tensor dual basis needs a 2D mesh without boundary faces")
+            self.exps = np.array([(a, b) for b in range(p + 1) for a in range(p + 1)], dtype=np.int64)
+            # quadrilateral (b_l, n_0, b_r, n_1) of every dual cell, in the frame of l(j)
+            self.quad = np.stack([mesh.bary[mesh.face_l], mesh.face_X[:, 0],
+                                  mesh.bary[mesh.face_r] + mesh.shift, mesh.face_X[:, 1]], axis=1)
+        else:
+            raise ValueError("dual must be 'taylor' or 'quad'")
         self.Nphi, self.Npsi = self.ref.n, self.exps.shape[0]
         self.tb = TimeBasis(p_gamma)
         self.Ng = self.tb.n
         self.tm = self.tb.matrices()
         self.s = 3 if d == 2 else 6
-        n = quad_n or (p + 3)
+        # the tensor basis has degree 2p in the reference square (rational in x on a
+        # non-parallelogram cell): more points
+        n = quad_n or (p + 3 if dual == "taylor" else 2 * p + 3)
         self.vol_rule = ref_simplex_rule(d, n)
         self.face_rule = ref_simplex_rule(d - 1, n)
         self._element_mass()
@@ -101,6 +146,8 @@ class Discretization:
     def psi(self, j, x_lframe):
         """Dual basis (..., Npsi) of face j at points given in the frame of l(j)."""
         m = self.mesh
+        if self.dual == "quad":
+            return monomials(bilinear_inverse(self.quad[j], x_lframe), self.exps)
         y = (x_lframe - m.xc[j][..., None, :]) / m.hj[j][..., None, None]
         return monomials(y, self.exps)
 

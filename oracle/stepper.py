@@ -61,11 +61,11 @@ def plane_wave_fields(x, t, kind, n, pol, amp, lam, mu, rho):
 class Simulation:
     """One mesh, one medium, n_shots right-hand sides; direct solves."""
 
-    def __init__(self, xyz, elem_vert, period, lam, mu, rho, p, p_gamma, scheme, dt):
+    def __init__(self, xyz, elem_vert, period, lam, mu, rho, p, p_gamma, scheme, dt, dual="taylor"):
         if scheme == "cn" and p_gamma != 0:
             raise ValueError("Crank-Nicolson needs p_gamma = 0")
         self.mesh = DualMesh(xyz, elem_vert, period)
-        self.disc = Discretization(self.mesh, p, p_gamma, lam, mu, rho)
+        self.disc = Discretization(self.mesh, p, p_gamma, lam, mu, rho, dual=dual)
         self.scheme, self.dt = scheme, dt
         self.A = self.disc.assemble(dt, scheme)
         self._lu = None
