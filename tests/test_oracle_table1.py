@@ -8,11 +8,15 @@ the unit normal in the eigenvectors (the reading of Eq. NT2.2), alpha = 0.1,
 h = 0.1264 sqrt(1760 / N_i), to t_end = 3 sqrt(2), where the exact state equals the
 initial one.  Our meshes are structured (n x n cells x 2, N_i = 1800 for the table's
 1760), the paper's are unstructured and its 2D dual basis is the (p+1)^2 tensor basis
-(ours: P_p monomials), so the comparison is of magnitude: the L2 error of the whole
-state (velocity and stress, projection error included) must lie within a factor 4 of
-the paper's.  A dropped term or a wrong sign in the operator gives errors of the size
-of the solution itself at p = 2 (about 1), far outside that band.
+(ours: P_p monomials; the paper's is available as dual="quad"), so magnitudes are
+compared loosely: the L2 error of the whole state (velocity and stress, projection error
+included) must lie within a factor 4 of the paper's.  The convergence rates from
+N_i = 1800 to 3872 (p = 2) must match the printed ones to 0.15 per component.  A
+dropped term or a wrong sign in the operator gives errors of the size of the solution
+itself at p = 2 (about 1), far outside that band, and changes the rates.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -36,7 +40,8 @@ def _exact_amplitudes():
     return np.array([v[0], v[1], s[0, 0], s[1, 1], s[0, 1]])
 
 
-def paper_setup_errors(p, n):
+@functools.lru_cache(maxsize=None)
+def paper_setup_errors(p, n, dual="taylor"):
     """L2 errors of (u, v, s_xx, s_yy, s_xy) at t_end on an n x n x 2 periodic mesh."""
     xyz, ev, per = synth.tri_grid(n, n, 3.0, 3.0, periodic=True)
     xyz = xyz - 1.5
@@ -45,7 +50,7 @@ def paper_setup_errors(p, n):
     h = 0.1264 * np.sqrt(1760.0 / ne)
     t_end = 3.0 * np.sqrt(2.0)
     steps = int(round(t_end / (0.112 * h)))
-    sim = Simulation(xyz, ev, per, lam, mu, rho, p, p, "stdg", t_end / steps)
+    sim = Simulation(xyz, ev, per, lam, mu, rho, p, p, "stdg", t_end / steps, dual=dual)
     sim.set_plane_wave(0, np.array([1.0, 1.0]), None, ALPHA)
     vp, sp = sim.v_tr.copy(), sim.sig_tr.copy()
     sim.set_plane_wave(1, np.array([1.0, 1.0]), None, ALPHA)
@@ -68,10 +73,21 @@ def paper_setup_errors(p, n):
     return np.sqrt(np.array(err2)), ne
 
 
+@pytest.mark.parametrize("dual", ["taylor", "quad"])
 @pytest.mark.parametrize("p", [2])   # at p = 1 the table's own errors are of the solution's size
-def test_state_error_magnitude_matches_table1(p):
-    errs, ne = paper_setup_errors(p, 30)
+def test_state_error_magnitude_matches_table1(p, dual):
+    errs, ne = paper_setup_errors(p, 30, dual)
     row = next(r for r in load_table1() if r["p"] == p and r["n"] == 1760)
     ratio = np.linalg.norm(errs) / np.linalg.norm(row["err"])
-    print("p", p, "N_i", ne, "errors", errs, "paper", row["err"], "ratio", ratio)
+    print("p", p, dual, "N_i", ne, "errors", errs, "paper", row["err"], "ratio", ratio)
     assert 0.25 < ratio < 4.0, (errs, row["err"], ratio)
+
+
+def test_rates_match_table1():
+    # p = 2 from N_i = 1800 to 3872 against the printed rates from 1760 to 3960: every
+    # component, including the lower rate of u and the order p + 2 of the others
+    (e0, n0), (e1, n1) = paper_setup_errors(2, 30), paper_setup_errors(2, 44)
+    rates = np.log(e0 / e1) / (0.5 * np.log(n1 / n0))
+    printed = next(r for r in load_table1() if r["p"] == 2 and r["n"] == 3960)["rate"]
+    print("rates", rates, "printed", printed)
+    assert np.all(np.abs(rates - printed) <= 0.15), (rates, printed)
