@@ -163,6 +163,18 @@ int stdg_query(stdg_ctx* ctx, int what, int64_t* out);
 /* Face table as built by stdg_set_mesh: l(j), r(j) (-1 on the boundary). */
 int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);
 
+/* The same face table built on the host alone, with no context and no GPU (the mesh
+ * connectivity of Sec. 3: faces by sorted vertex tuples, periodic faces through the
+ * period, l(j) the smaller and r(j) the larger element index, -1 on the boundary).
+ * Arguments as for stdg_set_mesh (dim 2 or 3).  On entry *n_face holds the capacity of
+ * face_l / face_r (0 with NULL arrays asks for the count only); on return it holds the
+ * number of faces, also when the capacity was too small (then STDG_EINVAL and nothing
+ * written).  Returns STDG_OK, STDG_EINVAL (bad argument, vertex index out of range,
+ * non-finite coordinate) or STDG_EMESH (inverted element, a face shared by more than two
+ * elements, an element adjacent to itself).  The caller owns every array. */
+int stdg_mesh_faces(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
+                    const double* period, int64_t* n_face, int32_t* face_l, int32_t* face_r);
+
 /* z = P^{-1} r with the context's preconditioner (Pre1 or Pre2) for slab size dt
  * (canonical velocity layout, one shot, FP64, host pointers).  Requires preconditioner
  * 1 or 2; with 2, the shots must be set (stdg_set_shots or a source / state call). */

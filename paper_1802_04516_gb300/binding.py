@@ -58,6 +58,7 @@ SIGNATURES = {
     "stdg_apply_operator_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
     "stdg_query": (C.c_int, [_P, C.c_int, _I64]),
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
+    "stdg_mesh_faces": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, _D, _I64, _I32, _I32]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
     "stdg_time_kernel": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
     "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
@@ -102,6 +103,28 @@ def _d(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def mesh_faces(xyz, elem_vert, period=None):
+    """Face table (l(j), r(j), r = -1 on the boundary) of a mesh, built on the host by the
+    library's mesh code with no context and no GPU.  Raises StdgError on a bad mesh."""
+    lib = load()
+    xyz = _f64(xyz)
+    ev = np.ascontiguousarray(elem_vert, dtype=np.int32)
+    dim = ev.shape[1] - 1
+    per = None if period is None else _f64(period)
+    per_p = None if per is None else _d(per)
+    n = C.c_int64(0)
+    args = (dim, xyz.shape[0], _d(xyz), ev.shape[0], ev.ctypes.data_as(_I32), per_p)
+    rc = lib.stdg_mesh_faces(*args, C.byref(n), None, None)
+    if rc != 0:
+        raise StdgError(rc, "stdg_mesh_faces")
+    fl = np.zeros(n.value, dtype=np.int32)
+    fr = np.zeros(n.value, dtype=np.int32)
+    rc = lib.stdg_mesh_faces(*args, C.byref(n), fl.ctypes.data_as(_I32), fr.ctypes.data_as(_I32))
+    if rc != 0:
+        raise StdgError(rc, "stdg_mesh_faces")
+    return fl, fr
 
 
 class Solver:

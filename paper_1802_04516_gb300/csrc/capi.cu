@@ -708,6 +708,25 @@ int stdg_get_faces(stdg_ctx* c, int32_t* face_l, int32_t* face_r) {
     return STDG_OK;
 }
 
+int stdg_mesh_faces(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
+                    const double* period, int64_t* n_face, int32_t* face_l, int32_t* face_r) {
+    if (dim != 2 && dim != 3) return STDG_EINVAL;
+    if (!n_face || !xyz || !elem_vert || n_vert < dim + 1 || n_elem < 1 || n_elem > (int64_t)INT32_MAX / 8)
+        return STDG_EINVAL;
+    if (period && !all_finite(period, dim)) return STDG_EINVAL;
+    const int64_t cap = *n_face;
+    HostMesh hm;
+    std::string err;
+    const int rc = build_host_mesh(dim, n_vert, xyz, n_elem, elem_vert, period, &hm, &err);
+    if (rc != STDG_OK) return rc;
+    *n_face = hm.n_face;
+    if (!face_l && !face_r) return STDG_OK;
+    if (cap < hm.n_face) return STDG_EINVAL;
+    if (face_l) std::memcpy(face_l, hm.face_l.data(), sizeof(int32_t) * hm.n_face);
+    if (face_r) std::memcpy(face_r, hm.face_r.data(), sizeof(int32_t) * hm.n_face);
+    return STDG_OK;
+}
+
 int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z) {
     CHECK_CTX(c);
     NEED_ALL(c);

@@ -1,0 +1,82 @@
+"""Row a1 (mesh connectivity, Sec. 3) on CPU: the library's host-side face builder
+(stdg_mesh_faces, the code stdg_set_mesh runs) against the oracle's DualMesh, bit for bit,
+on small 2D/3D, periodic and bounded meshes and on the full 200,704-triangle benchmark
+mesh; and its rejections of bad meshes."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.mesh import DualMesh
+
+
+def _faces(xyz, ev, per):
+    from paper_1802_04516_gb300 import build
+    from paper_1802_04516_gb300.binding import load, mesh_faces
+    load(build.build())
+    return mesh_faces(xyz, ev, per)
+
+
+CASES = {
+    "2d_periodic_jittered": lambda: synth.tri_grid(5, 4, 1.0, 0.8, periodic=True, jitter=0.25, seed=1),
+    "2d_bounded": lambda: synth.tri_grid(6, 3, 2.0, 1.0, periodic=False, jitter=0.2, seed=2),
+    "3d_periodic": lambda: synth.tet_kuhn(3, 1.0, periodic=True, jitter=0.15, seed=3),
+    "3d_bounded": lambda: synth.tet_kuhn(3, 1.0, periodic=False, jitter=0.1, seed=4),
+    "2d_sliver_layers": lambda: (lambda w: (w.xyz, w.elem_vert, w.period))(synth.scaled("c2", ny=10, steps=1)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_face_table_matches_oracle(name):
+    xyz, ev, per = CASES[name]()
+    m = DualMesh(xyz, ev, per)
+    fl, fr = _faces(xyz, ev, per)
+    assert np.array_equal(fl, m.face_l) and np.array_equal(fr, m.face_r)
+
+
+def test_face_table_matches_oracle_on_the_benchmark_mesh():
+    w = synth.c2_layered_slivers()
+    m = DualMesh(w.xyz, w.elem_vert, w.period)
+    fl, fr = _faces(w.xyz, w.elem_vert, w.period)
+    assert len(fl) == m.n_face == 301728
+    assert np.array_equal(fl, m.face_l) and np.array_equal(fr, m.face_r)
+
+
+def _rc(xyz, ev, per=None, cap=None, arrays=True):
+    from paper_1802_04516_gb300 import build
+    from paper_1802_04516_gb300.binding import load
+    lib = load(build.build())
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    per_p = None if per is None else np.ascontiguousarray(per, dtype=np.float64).ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double))
+    n = ctypes.c_int64(cap if cap is not None else 0)
+    fl = np.zeros(max(cap or 0, 1), dtype=np.int32)
+    fr = np.zeros(max(cap or 0, 1), dtype=np.int32)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    rc = lib.stdg_mesh_faces(ev.shape[1] - 1, xyz.shape[0], xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             ev.shape[0], ev.ctypes.data_as(i32), per_p, ctypes.byref(n),
+                             fl.ctypes.data_as(i32) if arrays else None, fr.ctypes.data_as(i32) if arrays else None)
+    return rc, n.value
+
+
+def test_rejections():
+    xyz, ev, _ = synth.tri_grid(3, 3, 1.0, 1.0, periodic=False)
+    rc, n = _rc(xyz, ev, arrays=False)
+    assert rc == 0 and n == DualMesh(xyz, ev, None).n_face
+    assert _rc(xyz, ev, cap=n) == (0, n)
+    assert _rc(xyz, ev, cap=n - 1) == (-1, n)                  # capacity too small: count still set
+    bad = ev.copy()
+    bad[4] = bad[4, [0, 2, 1]]                                 # one element turned clockwise
+    assert _rc(xyz, bad)[0] == -2
+    bad = ev.copy()
+    bad[0, 1] = xyz.shape[0]                                   # vertex index out of range
+    assert _rc(xyz, bad)[0] == -1
+    nan = xyz.copy()
+    nan[ev[2, 0], 0] = np.nan
+    assert _rc(nan, ev)[0] == -1
+    # a face shared by three triangles
+    tri3 = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0], [0.5, -1.0], [0.6, 2.0]])
+    ev3 = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], dtype=np.int32)
+    assert _rc(tri3, ev3)[0] == -2
