@@ -583,7 +583,6 @@ int stdg_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* out) {
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 0) STDG_FAIL(c, STDG_EINVAL, "dt must be > 0 and n_steps >= 0");
     if (out) std::memset(out, 0, sizeof(*out));
     if (n_steps == 0) return STDG_OK;
-    if (c->n_rec > 0 && c->rec_steps == 0 && c->rec_cap_steps == 0) { /* first use */ }
     int rc = ensure_records(c, n_steps);
     if (rc != STDG_OK) return rc;
     return solver_step(c, dt, n_steps, out);
