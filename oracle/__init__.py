@@ -14,7 +14,9 @@ Modules
   mesh       faces Gamma_j, l(j)/r(j), normals n_j, dual cells R_j = T_{l,j} u T_{r,j}
              (Sec. 3, "Two space dimensions" / "Three space dimensions")
   operators  M_j, Mbar_i, D_{i,j}, Q_{i,j}, time matrices (Eqs. MD_2 - SD_1), the
-             Schur velocity system (Eq. velocity.sys, Eq. velocity.sys.cn)
+             Schur velocity system (Eq. velocity.sys, Eq. velocity.sys.cn); the dual
+             basis is the Taylor space or, in 2D, the paper's (p+1)^2 tensor space on the
+             bilinearly mapped dual quadrilateral (dual="quad")
   precond    Appendix A preconditioners on the assembled system: block Jacobi (Eq. pre1)
              and the stencil-local inverse (Eqs. APPRE1 / APPRE2)
   adjoint    receiver misfit and its exact discrete gradient w.r.t. per-element lambda, mu,
@@ -24,6 +26,8 @@ Modules
              sources (Sec. 6.3)
 
 Parity status of every function is pinned by ``tests/test_oracle_*.py`` against
-closed forms, theorems of the paper and brute-force checks; see each module header.
+closed forms, theorems of the paper and brute-force checks, and by the values the paper
+prints (``tests/golden/``: its convergence table, reproduced in rate by
+``tests/test_oracle_table1.py``); see each module header.
 """
 from . import adjoint, basis, quadrature, mesh, operators, precond, stepper  # noqa: F401
