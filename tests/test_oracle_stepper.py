@@ -127,3 +127,39 @@ def test_receiver_at_node_reads_nodal_value():
     xi = np.linalg.solve(sim.mesh.J[7], x - sim.mesh.X[7, 0])
     phi = sim.disc.ref.values(xi[None])[0]
     np.testing.assert_allclose(val, sim.v_tr[7] @ phi, rtol=1e-13)
+
+
+@pytest.mark.parametrize("kind,n,pol", [(0, [1.0, 1.0], None), (1, [1.0, 1.0], None), (1, [0.6, -0.8], None),
+                                        (0, [1.0, 0.0, 0.0], None), (1, [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]),
+                                        (1, [1.0, 2.0, 2.0], [2.0, -1.0, 0.0])])
+def test_plane_wave_fields_solve_the_elastic_wave_equations(kind, n, pol):
+    # Eqs. NT2.1-NT2.2 (unit normal, reading of the paper's eigenvectors): the exact P and S
+    # waves satisfy rho dv/dt = div sigma and dsigma/dt = lam tr(grad v) I + mu (grad v + grad v^T),
+    # checked by central differences at random points (Eq. 1 of the velocity-stress system)
+    from oracle.stepper import plane_wave_fields
+    lam, mu, rho, amp = 2.0, 1.0, 1.3, 0.7
+    d = len(n)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-1, 1, size=(7, d))
+    t, h = 0.37, 1e-5
+
+    def f(xx, tt):
+        return plane_wave_fields(xx, tt, kind, n, pol, amp, lam, mu, rho)
+
+    v_t = (f(x, t + h)[0] - f(x, t - h)[0]) / (2 * h)
+    s_t = (f(x, t + h)[1] - f(x, t - h)[1]) / (2 * h)
+    grad_v = np.zeros((7, d, d))      # [q, k, l] = d v_k / d x_l
+    div_s = np.zeros((7, d))
+    for l in range(d):
+        e = np.zeros(d)
+        e[l] = h
+        vp, sp = f(x + e, t)
+        vm, sm = f(x - e, t)
+        grad_v[:, :, l] = (vp - vm) / (2 * h)
+        div_s += (sp[:, :, l] - sm[:, :, l]) / (2 * h)
+    scale = amp * 2 * np.pi * np.linalg.norm(n) * (lam + 2 * mu)
+    assert np.abs(rho * v_t - div_s).max() < 1e-7 * scale
+    strain_rate = lam * np.trace(grad_v, axis1=1, axis2=2)[:, None, None] * np.eye(d) + mu * (
+        grad_v + np.swapaxes(grad_v, 1, 2))
+    assert np.abs(s_t - strain_rate).max() < 1e-7 * scale
+    assert np.abs(f(x, t)[0]).max() > 1e-3 * amp                 # not the zero solution
