@@ -163,3 +163,25 @@ def test_plane_wave_fields_solve_the_elastic_wave_equations(kind, n, pol):
         grad_v + np.swapaxes(grad_v, 1, 2))
     assert np.abs(s_t - strain_rate).max() < 1e-7 * scale
     assert np.abs(f(x, t)[0]).max() > 1e-3 * amp                 # not the zero solution
+
+
+def test_source_vector_is_the_slab_integral_of_the_wavelet():
+    # Sec. 6.3 point source: (rho S)_i = d phi(x_s) dt int_0^1 gamma_a(tau) S(t0 + tau dt) dtau in the
+    # source element only.  Against an adaptive quadrature of the same integral (scipy) and the
+    # partition of unity of the nodal basis (the phi(x_s) sum to 1)
+    from scipy.integrate import quad
+    w = synth.scaled("c2", ny=6, steps=2)
+    sim = Simulation.from_workload(w)
+    sim.set_source(w.shots_xs[0], w.shots_dir[0], w.f0, w.t_delay, w.a1)
+    dz = sim.disc
+    e_s = sim.sources["elem"]
+    for t0 in (0.5 * w.t_delay, w.t_delay - 0.3 * sim.dt, 1.7 * w.t_delay):
+        sv = sim.source_vector(t0).reshape(sim.mesh.n_elem, dz.dim, dz.Ng, dz.Nphi)
+        assert np.abs(np.delete(sv, e_s, axis=0)).max() == 0.0
+        for a in range(dz.Ng):
+            def integrand(tau, a=a):
+                return dz.tb.values(tau)[0, a] * ricker(t0 + tau * sim.dt, w.f0, w.t_delay, w.a1)
+            ref = sim.dt * quad(integrand, 0.0, 1.0, epsabs=1e-15, epsrel=1e-13)[0]
+            for k in range(dz.dim):
+                got = sv[e_s, k, a].sum()
+                assert abs(got - w.shots_dir[0][k] * ref) <= 1e-11 * sim.dt * w.a1, (t0, a, k, got, ref)
