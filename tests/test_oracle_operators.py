@@ -98,3 +98,27 @@ def test_renumbering_invariance():
     nb = A.shape[0] // ev.shape[0]
     idx = (perm[:, None] * nb + np.arange(nb)).ravel()
     np.testing.assert_allclose(Ap, A[np.ix_(idx, idx)], atol=1e-14 * np.abs(A).max())
+
+
+def test_point_location_reading():
+    # reading: the element whose barycentric coordinates are all >= -1e-12, the lowest index on
+    # ties (edges, vertices); periodic images fold back into the element's frame
+    xyz, ev, per = _mesh2d(n=4, periodic=True)
+    m = DualMesh(xyz, ev, per)
+    for i in range(m.n_elem):
+        c = m.X[i].mean(axis=0)
+        j, y = m.locate(c)
+        assert j == i and np.allclose(y, c)
+        j, y = m.locate(c + per * np.array([1.0, -2.0]))            # a periodic image
+        assert j == i and np.allclose(y, c, atol=1e-12)
+    for f in range(m.n_face):
+        mid = m.face_X[f].mean(axis=0)
+        j, _ = m.locate(mid)
+        assert j == min(m.face_l[f], m.face_r[f])
+    vert = m.X[5, 1]
+    touching = [i for i in range(m.n_elem) if np.any(np.all(np.abs(
+        (m.X[i] - vert + per / 2) % per - per / 2) < 1e-12, axis=1))]
+    assert m.locate(vert)[0] == min(touching)
+    xyz_b, ev_b, _ = _mesh2d(n=3, periodic=False)
+    with pytest.raises(ValueError):
+        DualMesh(xyz_b, ev_b, None).locate(np.array([1.5, 0.5]))
