@@ -105,6 +105,19 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _need(a, n, name):
+    """The library reads (or writes) exactly n values through the pointer: check first."""
+    if a.size != n:
+        raise ValueError("%s has %d values, the context needs %d" % (name, a.size, n))
+    return a
+
+
+def _out(a, n, name):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("%s must be a C-contiguous float64 array" % name)
+    return _need(a, n, name)
+
+
 def mesh_faces(xyz, elem_vert, period=None):
     """Face table (l(j), r(j), r = -1 on the boundary) of a mesh, built on the host by the
     library's mesh code with no context and no GPU.  Raises StdgError on a bad mesh."""
@@ -177,14 +190,16 @@ class Solver:
                                          None if per is None else _d(per)))
 
     def set_material(self, lam, mu, rho):
-        lam, mu, rho = _f64(lam), _f64(mu), _f64(rho)
+        ne = self.n_elem
+        lam, mu, rho = (_need(_f64(a), ne, k) for a, k in ((lam, "lambda"), (mu, "mu"), (rho, "rho")))
         self._chk(self.lib.stdg_set_material(self.h, _d(lam), _d(mu), _d(rho)))
 
     def set_shots(self, n):
         self._chk(self.lib.stdg_set_shots(self.h, n))
 
     def set_state(self, v_tr, sig_tr, shot=0):
-        v, s = _f64(v_tr), _f64(sig_tr)
+        v = _need(_f64(v_tr), self.n_elem * self.dim * self.Nphi, "v_tr")
+        s = _need(_f64(sig_tr), self.n_face * self.n_sig * self.Npsi, "sig_tr")
         self._chk(self.lib.stdg_set_state(self.h, shot, _d(v), _d(s)))
 
     def get_state(self, shot=0, out=None):
@@ -193,27 +208,35 @@ class Solver:
             v = np.zeros((self.n_elem, self.dim, self.Nphi))
             s = np.zeros((self.n_face, self.n_sig, self.Npsi))
         else:
-            v, s = out
+            v = _out(out[0], self.n_elem * self.dim * self.Nphi, "out[0]")
+            s = _out(out[1], self.n_face * self.n_sig * self.Npsi, "out[1]")
         self._chk(self.lib.stdg_get_state(self.h, shot, _d(v), _d(s)))
         return v, s
 
     def set_plane_wave(self, kind, n, pol=None, amp=1.0, t=0.0, shot=0):
-        n = _f64(n)
-        pol = None if pol is None else _f64(pol)
+        n = _need(_f64(n), self.dim, "n")
+        pol = None if pol is None else _need(_f64(pol), self.dim, "pol")
         self._chk(self.lib.stdg_set_plane_wave(self.h, shot, kind, _d(n), None if pol is None else _d(pol), amp, t))
 
     def set_sources(self, xs, direction, f0, t_delay, a1):
         xs, dr = _f64(np.atleast_2d(xs)), _f64(np.atleast_2d(direction))
+        _need(xs, xs.shape[0] * self.dim, "xs")
+        _need(dr, xs.shape[0] * self.dim, "direction")
         self._chk(self.lib.stdg_set_sources(self.h, xs.shape[0], _d(xs), _d(dr), f0, t_delay, a1))
 
     def set_point_sources(self, xs, direction, f0, t_delay, a1, n_shots=1):
         """Several point sources per shot: xs, direction of shape (n_shots * per_shot, dim)."""
         xs, dr = _f64(np.atleast_2d(xs)), _f64(np.atleast_2d(direction))
+        if n_shots < 1 or xs.shape[0] % n_shots:
+            raise ValueError("%d sources do not split into %d shots" % (xs.shape[0], n_shots))
+        _need(xs, xs.shape[0] * self.dim, "xs")
+        _need(dr, xs.shape[0] * self.dim, "direction")
         per = xs.shape[0] // n_shots
         self._chk(self.lib.stdg_set_point_sources(self.h, n_shots, per, _d(xs), _d(dr), f0, t_delay, a1))
 
     def set_receivers(self, xr):
         xr = _f64(np.atleast_2d(xr))
+        _need(xr, xr.shape[0] * self.dim, "xr")
         self.n_rec = xr.shape[0]
         self._chk(self.lib.stdg_set_receivers(self.h, xr.shape[0], _d(xr)))
 
@@ -249,7 +272,7 @@ class Solver:
         return buf[: self.n_shots * k * n_rec * self.dim].reshape(self.n_shots, k, n_rec, self.dim)
 
     def apply_operator(self, dt, x):
-        x = _f64(x).ravel()
+        x = _need(_f64(x).ravel(), self.nvel, "x")
         y = np.zeros_like(x)
         self._chk(self.lib.stdg_apply_operator(self.h, dt, _d(x), _d(y)))
         return y
@@ -258,7 +281,7 @@ class Solver:
         self._chk(self.lib.stdg_apply_operator_device(self.h, dt, _P(x_ptr), _P(y_ptr), 1 if fp32 else 0))
 
     def apply_preconditioner(self, dt, r):
-        r = _f64(r).ravel()
+        r = _need(_f64(r).ravel(), self.nvel, "r")
         z = np.zeros_like(r)
         self._chk(self.lib.stdg_apply_preconditioner(self.h, dt, _d(r), _d(z)))
         return z
@@ -272,7 +295,7 @@ class Solver:
     def misfit_grad(self, dt, n_steps, data, checkpoint_every=20, grad=True):
         """(loss, g_lambda, g_mu, g_rho, stats) of n_steps slabs from the current states;
         data: (n_shots, n_steps, n_rec, dim).  grad=False: the loss only (forward run)."""
-        data = _f64(data)
+        data = _need(_f64(data), self.n_shots * n_steps * getattr(self, "n_rec", 0) * self.dim, "data")
         loss = C.c_double(0.0)
         g = [np.zeros(self.n_elem) for _ in range(3)] if grad else [None, None, None]
         st = stdg_stats()
