@@ -175,6 +175,15 @@ int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);
 int stdg_mesh_faces(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
                     const double* period, int64_t* n_face, int32_t* face_l, int32_t* face_r);
 
+/* Elements containing n_pts points (n_pts x dim, row-major), located on the host with no
+ * context and no GPU by the code that places sources and receivers: the element whose
+ * barycentric coordinates are all >= -1e-12, the lowest index on ties (edges, vertices),
+ * periodic images folded into the element's frame; -1 for a point outside the mesh.
+ * Mesh arguments as for stdg_set_mesh; elem_out (n_pts entries) is owned by the caller.
+ * Returns STDG_OK, STDG_EINVAL (bad argument, non-finite point) or STDG_EMESH. */
+int stdg_locate_points(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
+                       const double* period, int64_t n_pts, const double* pts, int64_t* elem_out);
+
 /* z = P^{-1} r with the context's preconditioner (Pre1 or Pre2) for slab size dt
  * (canonical velocity layout, one shot, FP64, host pointers).  Requires preconditioner
  * 1 or 2; with 2, the shots must be set (stdg_set_shots or a source / state call). */

@@ -59,6 +59,7 @@ SIGNATURES = {
     "stdg_query": (C.c_int, [_P, C.c_int, _I64]),
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
     "stdg_mesh_faces": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, _D, _I64, _I32, _I32]),
+    "stdg_locate_points": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, _D, C.c_int64, _D, _I64]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
     "stdg_time_kernel": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
     "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
@@ -138,6 +139,23 @@ def mesh_faces(xyz, elem_vert, period=None):
     if rc != 0:
         raise StdgError(rc, "stdg_mesh_faces")
     return fl, fr
+
+
+def locate_points(xyz, elem_vert, points, period=None):
+    """Element of each point (-1 outside), located on the host by the library's code for
+    sources and receivers, with no context and no GPU.  Raises StdgError on a bad mesh."""
+    lib = load()
+    xyz = _f64(xyz)
+    ev = np.ascontiguousarray(elem_vert, dtype=np.int32)
+    dim = ev.shape[1] - 1
+    pts = _need(_f64(np.atleast_2d(points)), np.atleast_2d(points).shape[0] * dim, "points")
+    per = None if period is None else _need(_f64(period), dim, "period")
+    out = np.zeros(pts.shape[0], dtype=np.int64)
+    rc = lib.stdg_locate_points(dim, xyz.shape[0], _d(xyz), ev.shape[0], ev.ctypes.data_as(_I32),
+                                None if per is None else _d(per), pts.shape[0], _d(pts), out.ctypes.data_as(_I64))
+    if rc != 0:
+        raise StdgError(rc, "stdg_locate_points")
+    return out
 
 
 class Solver:

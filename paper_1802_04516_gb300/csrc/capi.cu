@@ -726,6 +726,25 @@ int stdg_mesh_faces(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, 
     return STDG_OK;
 }
 
+int stdg_locate_points(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
+                       const double* period, int64_t n_pts, const double* pts, int64_t* elem_out) {
+    if (dim != 2 && dim != 3) return STDG_EINVAL;
+    if (!xyz || !elem_vert || n_vert < dim + 1 || n_elem < 1 || n_elem > (int64_t)INT32_MAX / 8 || n_pts < 0 ||
+        (n_pts > 0 && (!pts || !elem_out)))
+        return STDG_EINVAL;
+    if (period && !all_finite(period, dim)) return STDG_EINVAL;
+    if (n_pts > 0 && !all_finite(pts, n_pts * dim)) return STDG_EINVAL;
+    HostMesh hm;
+    std::string err;
+    const int rc = build_host_mesh(dim, n_vert, xyz, n_elem, elem_vert, period, &hm, &err);
+    if (rc != STDG_OK) return rc;
+    for (int64_t k = 0; k < n_pts; ++k) {
+        double y[3];
+        elem_out[k] = locate_point(hm, pts + k * dim, y);
+    }
+    return STDG_OK;
+}
+
 int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z) {
     CHECK_CTX(c);
     NEED_ALL(c);

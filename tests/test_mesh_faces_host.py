@@ -1,7 +1,8 @@
-"""Row a1 (mesh connectivity, Sec. 3) on CPU: the library's host-side face builder
-(stdg_mesh_faces, the code stdg_set_mesh runs) against the oracle's DualMesh, bit for bit,
-on small 2D/3D, periodic and bounded meshes and on the full 200,704-triangle benchmark
-mesh; and its rejections of bad meshes."""
+"""The library's host-side mesh code on CPU, bit for bit against the oracle: row a1 (mesh
+connectivity, Sec. 3: stdg_mesh_faces, the code stdg_set_mesh runs) on small 2D/3D,
+periodic and bounded meshes and on the full 200,704-triangle benchmark mesh, with its
+rejections of bad meshes; and the location of sources and receivers (rows a8/a9:
+stdg_locate_points, the code the source and receiver calls run)."""
 import ctypes
 
 import numpy as np
@@ -80,3 +81,46 @@ def test_rejections():
     tri3 = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0], [0.5, -1.0], [0.6, 2.0]])
     ev3 = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], dtype=np.int32)
     assert _rc(tri3, ev3)[0] == -2
+
+
+def _locate_lib(xyz, ev, pts, per):
+    from paper_1802_04516_gb300 import build
+    from paper_1802_04516_gb300.binding import load, locate_points
+    load(build.build())
+    return locate_points(xyz, ev, pts, per)
+
+
+def _locate_oracle(m, pts):
+    out = []
+    for x in pts:
+        try:
+            out.append(m.locate(x)[0])
+        except ValueError:
+            out.append(-1)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name", ["2d_periodic_jittered", "2d_bounded", "3d_periodic", "3d_bounded"])
+def test_point_location_matches_oracle(name):
+    # rows a8/a9 (receivers, point sources): the element of every point, bit for bit, with the
+    # reading's ties -- element centroids, face midpoints, vertices, random and outside points
+    xyz, ev, per = CASES[name]()
+    m = DualMesh(xyz, ev, per)
+    rng = np.random.default_rng(8)
+    lo, hi = xyz.min(axis=0), xyz.max(axis=0)
+    pts = np.concatenate([m.X.mean(axis=1), m.face_X.mean(axis=1), m.X[::3, 0],
+                          rng.uniform(lo, hi, size=(60, xyz.shape[1])),
+                          rng.uniform(lo - 0.5, hi + 0.5, size=(20, xyz.shape[1]))])
+    got = _locate_lib(xyz, ev, pts, per)
+    want = _locate_oracle(m, pts)
+    assert np.array_equal(got, want)
+    assert (want >= 0).sum() > len(pts) // 2
+
+
+def test_workload_sources_and_receivers_match_oracle():
+    for w in (synth.scaled("c2", ny=10, steps=1), synth.scaled("c4", ny=8, steps=1, n_shots=16),
+              synth.scaled("c5", ny=10, steps=1)):
+        m = DualMesh(w.xyz, w.elem_vert, w.period)
+        pts = np.concatenate([w.shots_xs, w.receivers])
+        got = _locate_lib(w.xyz, w.elem_vert, pts, w.period)
+        assert np.array_equal(got, _locate_oracle(m, pts)) and (got >= 0).all()
