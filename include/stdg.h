@@ -184,6 +184,19 @@ int stdg_mesh_faces(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, 
 int stdg_locate_points(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, const int32_t* elem_vert,
                        const double* period, int64_t n_pts, const double* pts, int64_t* elem_out);
 
+/* The reference tables every kernel uses, computed on the host with no context (Sec. 3
+ * bases, Eqs. MD_2 - MD_2_3 time factors): Mref (N_phi x N_phi, row-major) =
+ * int over the reference simplex of phi_k phi_m for the nodal P_p basis; for the
+ * Lagrange time basis on the N_gamma = p_gamma + 1 Gauss-Legendre points of [0, 1]:
+ * W (N_gamma, the diagonal of int gamma_a gamma_b), T (N_gamma x N_gamma) =
+ * gamma(1) gamma(1)^T - K with K_ab = int gamma_a' gamma_b, S = W T^{-1} W (the time factor
+ * of the Schur term), kappa = gamma(1)^T T^{-1} gamma(0) and u = gamma(1)^T T^{-1} W
+ * (N_gamma; the stress-trace update sigma <- kappa sigma - dt sum_b u_b (E:g)_b).  Any
+ * output may be NULL.  Returns STDG_OK or STDG_EINVAL (dim not 2 or 3, p outside 1..4 in
+ * 2D or 1..3 in 3D, p_gamma outside 0..3). */
+int stdg_reference_tables(int dim, int p, int p_gamma, double* Mref, double* W, double* T, double* S, double* kappa,
+                          double* u);
+
 /* z = P^{-1} r with the context's preconditioner (Pre1 or Pre2) for slab size dt
  * (canonical velocity layout, one shot, FP64, host pointers).  Requires preconditioner
  * 1 or 2; with 2, the shots must be set (stdg_set_shots or a source / state call). */

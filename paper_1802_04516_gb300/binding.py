@@ -60,6 +60,7 @@ SIGNATURES = {
     "stdg_get_faces": (C.c_int, [_P, _I32, _I32]),
     "stdg_mesh_faces": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, _D, _I64, _I32, _I32]),
     "stdg_locate_points": (C.c_int, [C.c_int, C.c_int64, _D, C.c_int64, _I32, _D, C.c_int64, _D, _I64]),
+    "stdg_reference_tables": (C.c_int, [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
     "stdg_time_kernel": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
     "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
@@ -155,6 +156,20 @@ def locate_points(xyz, elem_vert, points, period=None):
                                 None if per is None else _d(per), pts.shape[0], _d(pts), out.ctypes.data_as(_I64))
     if rc != 0:
         raise StdgError(rc, "stdg_locate_points")
+    return out
+
+
+def reference_tables(dim, p, p_gamma):
+    """The library's reference tables (dict: Mref, W, T, S, kappa, u), computed on the host."""
+    from math import comb
+    n, g = comb(p + dim, dim), p_gamma + 1
+    out = dict(Mref=np.zeros((n, n)), W=np.zeros(g), T=np.zeros((g, g)), S=np.zeros((g, g)), u=np.zeros(g))
+    kappa = C.c_double(0.0)
+    rc = load().stdg_reference_tables(dim, p, p_gamma, _d(out["Mref"]), _d(out["W"]), _d(out["T"]), _d(out["S"]),
+                                      C.byref(kappa), _d(out["u"]))
+    if rc != 0:
+        raise StdgError(rc, "stdg_reference_tables")
+    out["kappa"] = kappa.value
     return out
 
 

@@ -745,6 +745,22 @@ int stdg_locate_points(int dim, int64_t n_vert, const double* xyz, int64_t n_ele
     return STDG_OK;
 }
 
+int stdg_reference_tables(int dim, int p, int p_gamma, double* Mref, double* W, double* T, double* S, double* kappa,
+                          double* u) {
+    if (dim != 2 && dim != 3) return STDG_EINVAL;
+    if (p < 1 || p > (dim == 2 ? 4 : 3) || p_gamma < 0 || p_gamma > 3) return STDG_EINVAL;
+    RefTables rt;
+    build_ref_tables(dim, p, p_gamma, &rt);
+    const int n = rt.Nphi, g = rt.Ng;
+    if (Mref) std::memcpy(Mref, rt.Mref, sizeof(double) * n * n);
+    if (W) std::memcpy(W, rt.W, sizeof(double) * g);
+    if (T) std::memcpy(T, rt.T, sizeof(double) * g * g);
+    if (S) std::memcpy(S, rt.S, sizeof(double) * g * g);
+    if (kappa) *kappa = rt.kappa;
+    if (u) std::memcpy(u, rt.u_tr, sizeof(double) * g);
+    return STDG_OK;
+}
+
 int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z) {
     CHECK_CTX(c);
     NEED_ALL(c);

@@ -1,8 +1,9 @@
 """The library's host-side mesh code on CPU, bit for bit against the oracle: row a1 (mesh
 connectivity, Sec. 3: stdg_mesh_faces, the code stdg_set_mesh runs) on small 2D/3D,
 periodic and bounded meshes and on the full 200,704-triangle benchmark mesh, with its
-rejections of bad meshes; and the location of sources and receivers (rows a8/a9:
-stdg_locate_points, the code the source and receiver calls run)."""
+rejections of bad meshes; the location of sources and receivers (rows a8/a9:
+stdg_locate_points, the code the source and receiver calls run); and the reference mass
+matrix and time factors of row a2 (stdg_reference_tables)."""
 import ctypes
 
 import numpy as np
@@ -124,3 +125,25 @@ def test_workload_sources_and_receivers_match_oracle():
         pts = np.concatenate([w.shots_xs, w.receivers])
         got = _locate_lib(w.xyz, w.elem_vert, pts, w.period)
         assert np.array_equal(got, _locate_oracle(m, pts)) and (got >= 0).all()
+
+
+@pytest.mark.parametrize("dim,p,pg", [(2, 1, 1), (2, 2, 2), (2, 3, 3), (2, 4, 2), (3, 1, 0), (3, 2, 2), (3, 3, 1)])
+def test_reference_tables_match_oracle(dim, p, pg):
+    # row a2 on the host: the reference mass matrix of the nodal basis and the time factors
+    # (Eqs. MD_2 - MD_2_3) that every kernel uses, against the oracle's own bases and rules
+    from oracle.basis import RefBasis, TimeBasis
+    from oracle.quadrature import ref_simplex_rule
+    from paper_1802_04516_gb300 import build
+    from paper_1802_04516_gb300.binding import load, reference_tables
+    load(build.build())
+    lib = reference_tables(dim, p, pg)
+    rp, rw = ref_simplex_rule(dim, p + 3)
+    phi = RefBasis(dim, p).values(rp)
+    Mref = np.einsum("q,qk,qm->km", rw, phi, phi)
+    tm = TimeBasis(pg).matrices()
+    W, T, g0, g1 = tm["W"], tm["T"], tm["g0"], tm["g1"]
+    Tinv = np.linalg.inv(T)
+    ref = dict(Mref=Mref, W=np.diag(W), T=T, S=W @ Tinv @ W, kappa=g1 @ Tinv @ g0, u=g1 @ Tinv @ W)
+    assert np.abs(W - np.diag(np.diag(W))).max() < 1e-15          # the nodal time basis is orthogonal
+    for k, v in ref.items():
+        assert np.allclose(lib[k], v, rtol=1e-12, atol=1e-13 * np.abs(v).max()), k
