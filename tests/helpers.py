@@ -68,3 +68,46 @@ def oracle_rounding_spread(sim, w):
     A2 = d2.assemble(w.dt, w.scheme)
     x = np.random.default_rng(11).normal(size=A2.shape[0])
     return rel_l2(A2 @ x, sim.A @ x)
+
+
+def face_neighbours(elem_vert):
+    """Face neighbours of every element of a mesh without periodic faces: (n_elem, d+1)
+    array, -1 where the face is on the boundary (faces matched by sorted vertex tuples)."""
+    ev = np.asarray(elem_vert)
+    ne, nv = ev.shape
+    faces = np.concatenate([np.sort(np.delete(ev, k, axis=1), axis=1) for k in range(nv)])   # (nv*ne, d)
+    owner = np.tile(np.arange(ne), nv)
+    local = np.repeat(np.arange(nv), ne)
+    _, inv, cnt = np.unique(faces, axis=0, return_inverse=True, return_counts=True)
+    inv = inv.ravel()
+    order = np.argsort(inv, kind="stable")
+    nb = np.full((ne, nv), -1, dtype=np.int64)
+    first = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    for g in np.where(cnt == 2)[0]:
+        a, b = order[first[g]], order[first[g] + 1]
+        nb[owner[a], local[a]] = owner[b]
+        nb[owner[b], local[b]] = owner[a]
+    return nb
+
+
+def patch_operator_rows(w, elems, x, nb=None, quad_n=None):
+    """(A x)_i for the sampled elements i of a large mesh, each from the oracle's assembled
+    operator on the patch {i and its face neighbours}: row i of A couples only those
+    elements, through the faces of i, whose dual cells and E_j the patch reproduces (the
+    patch numbers its elements differently, which changes l(j)/r(j) but not A).  Meshes
+    without periodic faces only.  Returns (len(elems), d * N_gamma * N_phi)."""
+    from oracle.mesh import DualMesh
+    from oracle.operators import Discretization
+    assert w.period is None
+    nb = face_neighbours(w.elem_vert) if nb is None else nb
+    xe = np.asarray(x).reshape(w.n_elem, -1)
+    rows = []
+    for i in elems:
+        P = np.concatenate([[i], np.sort(nb[i][nb[i] >= 0])])
+        verts, ev = np.unique(w.elem_vert[P], return_inverse=True)
+        ev = ev.reshape(len(P), -1).astype(np.int32)
+        dz = Discretization(DualMesh(w.xyz[verts], ev, None), w.p, w.p_gamma, w.lam[P], w.mu[P], w.rho[P],
+                            quad_n=quad_n)
+        A = dz.assemble(w.dt, w.scheme)
+        rows.append((A @ xe[P].ravel()).reshape(len(P), -1)[0])
+    return np.array(rows)
