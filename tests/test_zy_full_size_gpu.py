@@ -6,7 +6,9 @@ tests/helpers.py checks this against the full assembly on CPU).  Sampled rows: 1
 drawn at random and 12 slivers.  FP64 (the FP64 path's face and mass kernels) within 20x
 the oracle's own rounding spread on those rows, never worse than 1e-10 where the spread
 allows it (the rule of the small-mesh operator tests); FP32 (the single-shot TMA face
-kernel and mass kernel of the mixed path's inner solve) within 1e-4 on the random rows."""
+kernel and mass kernel of the mixed path's inner solve) within 1e-6 on the random rows
+(measured on a GB300: FP64 8.5e-13 and 2.7e-10 against bars of 2.3e-11 and 9.9e-9, FP32
+9.3e-8)."""
 import numpy as np
 import pytest
 
@@ -59,4 +61,4 @@ def test_full_size_operator_rows_match_oracle():
     m.close()
     err32 = rel_l2(y32[groups[0]], refs[0])
     print("FP32 rows: error %.3g" % err32)
-    assert err32 < 1e-4
+    assert err32 < 1e-6
