@@ -47,7 +47,7 @@ def pre1(A, ne):
     blocks = []
     for e in range(ne):
         sl = slice(e * nb, (e + 1) * nb)
-        blocks.append(np.linalg.inv(A[sl, sl].toarray()))
+        blocks.append(sp.csr_matrix(np.linalg.inv(A[sl, sl].toarray())))
     return sp.block_diag(blocks, format="csr")
 
 

@@ -9,7 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def header_functions():
-    text = open(os.path.join(ROOT, "include", "stdg.h")).read()
+    with open(os.path.join(ROOT, "include", "stdg.h")) as f:
+        text = f.read()
     return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(stdg_\w+)\s*\(", text, re.M)))
 
 

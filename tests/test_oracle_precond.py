@@ -85,7 +85,7 @@ def test_pre2_reduces_to_pre1_without_coupling():
     sim = _sim(2, 2, 1, "stdg", True)
     A, ne = sim.A.tocsr(), sim.mesh.n_elem
     nb = A.shape[0] // ne
-    Abd = sp.block_diag([A[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb].toarray() for e in range(ne)], format="csr")
+    Abd = sp.block_diag([A[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb] for e in range(ne)], format="csr")
     P1 = pre1(Abd, ne).toarray()
     P2 = pre2(Abd, ne, sim.mesh.elem_nbr).toarray()
     assert np.abs(P1 - P2).max() < 1e-12 * np.abs(P1).max()
