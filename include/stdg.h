@@ -88,21 +88,28 @@ const char* stdg_last_error(const stdg_ctx* ctx);
  * periodic) or NULL.  On a periodic axis vertices are identified, not duplicated.
  * Every boundary face is a free surface (sigma . n = 0).  Builds faces, l(j)/r(j),
  * normals, dual cells R_j and, on the device, the blocks D_{i,j} (Eq. MD_3) and the
- * inverse dual mass matrices M_j^{-1} (Eq. MD_2).  Returns STDG_EMESH for an
- * inverted element, a face shared by more than two elements or an element that is
- * its own neighbour. */
+ * Cholesky factors L_j of the dual mass matrices M_j = L_j L_j^T (Eq. MD_2); the kernels
+ * use the orthonormalised blocks D_{i,j} L_j^{-T} and never form M_j^{-1}.  Replaces any
+ * previous mesh (states, sources and receivers are dropped).  Returns STDG_EMESH for an
+ * inverted element, a face shared by more than two elements, an element that is its own
+ * neighbour or a dual mass matrix that is not positive definite; STDG_EINVAL for a bad
+ * size, a vertex index out of range or a non-finite coordinate or period. */
 int stdg_set_mesh(stdg_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_elem,
                   const int32_t* elem_vert, const double* period);
 
-/* Per-element Lame parameters and density (Eq. 5, Eq. NM1): rho_i constant per
- * element; E_j constant per dual cell, the sub-cell-measure-weighted mean of its
- * two elements.  All > 0 (lambda > -2mu/dim is not accepted: lambda must be >= 0). */
+/* Per-element Lame parameters and density (Eq. 5, Eq. NM1), n_elem values each: rho_i
+ * constant per element; E_j constant per dual cell, the sub-cell-measure-weighted mean
+ * of its two elements.  Requires lambda >= 0, mu > 0, rho > 0, all finite (else
+ * STDG_EINVAL); STDG_ESTATE before stdg_set_mesh.  Also sets up the preconditioner. */
 int stdg_set_material(stdg_ctx* ctx, const double* lambda, const double* mu, const double* rho);
 
 /* Number of shots (right-hand sides).  Resets states to zero.  Default 1. */
 int stdg_set_shots(stdg_ctx* ctx, int n_shots);
 
-/* Carried state of one shot: the t^{n,-} traces (Eq. NM13). */
+/* Carried state of one shot: the t^{n,-} traces (Eq. NM13), v_tr n_elem*d*N_phi and
+ * sig_tr n_face*s*N_psi values in the layouts above (stress in the Taylor-monomial dual
+ * basis; the library converts to its orthonormal coordinates).  STDG_EINVAL for a shot
+ * outside 0..n_shots-1 or a non-finite value. */
 int stdg_set_state(stdg_ctx* ctx, int shot, const double* v_tr, const double* sig_tr);
 int stdg_get_state(stdg_ctx* ctx, int shot, double* v_tr, double* sig_tr);
 
@@ -113,9 +120,10 @@ int stdg_get_state(stdg_ctx* ctx, int shot, double* v_tr, double* sig_tr);
 int stdg_set_plane_wave(stdg_ctx* ctx, int shot, int kind, const double* n, const double* pol,
                         double amp, double t);
 
-/* Point sources (Sec. 6.3): shot k has force direction dir[k] at xs[k] and the Ricker
- * time function S(t) = a1 (0.5 + a2 tau^2) exp(a2 tau^2), tau = t - t_delay,
- * a2 = -(pi f0)^2.  Sets n_shots (resets states). */
+/* Point sources (Sec. 6.3): shot k has force direction dir[k] at xs[k] (n_shots x dim
+ * each) and the Ricker time function S(t) = a1 (0.5 + a2 tau^2) exp(a2 tau^2),
+ * tau = t - t_delay, a2 = -(pi f0)^2.  Sets n_shots (resets states and records).
+ * STDG_EINVAL for a source outside the mesh or a non-finite argument. */
 int stdg_set_sources(stdg_ctx* ctx, int n_shots, const double* xs, const double* dir,
                      double f0, double t_delay, double a1);
 
@@ -126,7 +134,9 @@ int stdg_set_sources(stdg_ctx* ctx, int n_shots, const double* xs, const double*
 int stdg_set_point_sources(stdg_ctx* ctx, int n_shots, int per_shot, const double* xs, const double* dir,
                            double f0, double t_delay, double a1);
 
-/* Receivers: velocity v_h(x_r, t^{n+1,-}) is recorded after every step. */
+/* Receivers (n_rec x dim positions): velocity v_h(x_r, t^{n+1,-}) is recorded after
+ * every step; earlier records are dropped.  STDG_EINVAL for a position outside the mesh
+ * (located as by stdg_locate_points) or a non-finite one. */
 int stdg_set_receivers(stdg_ctx* ctx, int n_rec, const double* xr);
 
 /* Advances every shot by n_steps slabs of size dt (Eq. velocity.sys + NM26, or the
