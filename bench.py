@@ -47,6 +47,13 @@ def dofs_per_slab(w, n_face):
     return w.n_elem * w.dim * nphi * ng + n_face * s * nphi * ng
 
 
+def velocity_dofs_per_slab(w):
+    """Velocity space-time DOFs alone (d N_phi N_gamma per element): the count that compares
+    with the paper's, whose 2D dual basis carries more stress DOFs than ours."""
+    from math import comb
+    return w.n_elem * w.dim * comb(w.p + w.dim, w.dim) * (w.p_gamma + 1)
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -454,6 +461,7 @@ def main():
         "metric": METRIC,
         "value": value, "unit": "DOF-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "velocity_dof_steps_per_s": value * velocity_dofs_per_slab(w) / dofs,
         "dtype": "f32 operator/Krylov + f64 refinement", "data": "synthetic",
         "config": {"workload": "c2_layered_slivers_p3: %d triangles (448x224x2, 1%% slivers), p=p_gamma=3, "
                                "1 Ricker shot/GPU, 16 receivers, dt=%.4g (10x CFL)" % (w.n_elem, w.dt),

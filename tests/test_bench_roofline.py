@@ -68,3 +68,10 @@ def test_dofs_per_slab():
     w = types.SimpleNamespace(dim=2, p=3, p_gamma=3, n_elem=N_ELEM)
     # velocity d N_phi N_gamma per element + stress s N_psi N_gamma per face (N_psi = N_phi)
     assert bench.dofs_per_slab(w, N_FACE) == N_ELEM * 2 * 10 * 4 + N_FACE * 3 * 10 * 4 == 52263680
+
+
+def test_velocity_dofs_per_slab():
+    w = types.SimpleNamespace(dim=2, p=3, p_gamma=3, n_elem=N_ELEM)
+    assert bench.velocity_dofs_per_slab(w) == N_ELEM * 2 * 10 * 4 == 16056320
+    w3 = types.SimpleNamespace(dim=3, p=2, p_gamma=2, n_elem=1000)
+    assert bench.velocity_dofs_per_slab(w3) == 1000 * 3 * 10 * 3
