@@ -113,3 +113,24 @@ def _plane_wave_error(n, p):
 def test_plane_wave_order_with_the_tensor_dual_basis(p):
     e1, e2 = _plane_wave_error(6, p), _plane_wave_error(12, p)
     assert np.log2(e1 / e2) > p + 1 - 0.35, (e1, e2)
+
+
+@pytest.mark.parametrize("p,pg", [(1, 1), (2, 2), (2, 1)])
+def test_space_time_energy_identity_with_the_tensor_dual_basis(p, pg):
+    # Theorem 4 (eq. stsum4) with the paper's 2D dual space: the energy lost over a slab
+    # equals the time-jump terms, which are non-negative
+    xyz, ev, per = _mesh(n=4, jitter=0.2, seed=8)
+    n = ev.shape[0]
+    rng = np.random.default_rng(4)
+    sim = Simulation(xyz, ev, per, rng.uniform(1, 3, n), rng.uniform(.5, 1.5, n), rng.uniform(.7, 1.4, n),
+                     p, pg, "stdg", 0.21, dual="quad")
+    sim.set_state(rng.normal(size=sim.v_tr.shape), rng.normal(size=sim.sig_tr.shape))
+    e = [sim.energy()]
+    jumps = []
+    for _ in range(3):
+        sim.step(1)
+        e.append(sim.energy())
+        jumps.append(sim.jump_dissipation())
+    e, jumps = np.array(e), np.array(jumps)
+    assert (jumps >= 0).all() and (np.diff(e) <= 1e-14 * e[0]).all()
+    np.testing.assert_allclose(e[:-1] - e[1:], jumps, rtol=1e-9, atol=1e-13 * e[0])
