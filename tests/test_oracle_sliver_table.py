@@ -10,7 +10,9 @@ longest edge towards it.  Right-preconditioned GMRES(30) to 1e-8 from a zero gue
 first three slabs' systems, with none, the block-Jacobi Pre1 and the stencil Pre2 of
 Appendix A (oracle/precond.py).  Checked against the table: on both meshes none > Pre1 >
 Pre2, and the sliver factor (mesh 2 / mesh 1) falls from none to Pre1 to Pre2.  Not
-reproduced: the table's factor 1.00 for Pre2 (ours about 3), see the design notes.
+reproduced: the table's factor 1.00 for Pre2 (ours about 3, with Pre2 built as printed;
+our sliver construction also deforms the sliver's neighbours, which the stencil contains
+only in part).
 """
 import functools
 
