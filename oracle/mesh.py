@@ -1,7 +1,7 @@
 """Primary mesh, faces and face-based dual cells (Sec. 3, "Two space dimensions",
 "Three space dimensions").
 
-Readings of what the paper leaves open (each listed in the design notes):
+Readings of what the paper leaves open (the library implements the same ones):
   * l(j), r(j) are "assigned arbitrarily": here l(j) is the smaller element index,
     r(j) the larger; n_j is the unit normal of Gamma_j pointing from l(j) to r(j),
     and outward of l(j) on a boundary face.
