@@ -12,7 +12,9 @@
  * Error behaviour: every int-returning call returns STDG_OK (0) or a negative
  * STDG_E* code; a human-readable message is then available from
  * stdg_last_error().  A failed call leaves the context usable unless the code is
- * STDG_ECUDA (a CUDA error: the context should be destroyed).
+ * STDG_ECUDA from a CUDA error proper (the context should then be destroyed).  One kind of
+ * STDG_ECUDA leaves it usable: a kernel's bounded wait for a bulk copy that gave up (the
+ * message says so); that call's results are invalid and the error is reported once.
  *
  * Layouts (row-major, contiguous):
  *   velocity, one slab      [elem][component d][time node N_gamma][space node N_phi]
@@ -45,6 +47,9 @@ extern "C" {
 #define STDG_ECUDA    (-4)  /* CUDA runtime error                                   */
 #define STDG_ENOTCONV (-5)  /* Krylov hit max_iters; the state is still advanced    */
 #define STDG_ESTATE   (-6)  /* call out of order (e.g. step before set_mesh)        */
+#define STDG_ENONFINITE (-7) /* a residual norm became NaN or Inf (e.g. an input that
+                                overflows); the solve stopped, the state is advanced but
+                                holds non-finite values                                 */
 
 enum stdg_scheme { STDG_SCHEME_CN = 0, STDG_SCHEME_STDG = 1 };
 enum stdg_precision { STDG_FP64 = 0, STDG_MIXED_FP32 = 1 };
@@ -75,7 +80,7 @@ typedef struct {
     int iters_max;          /* largest per-step count                                 */
     int refinements;        /* FP64 refinement sweeps (mixed precision)               */
     double final_rel_res;   /* ||b - A x|| / ||b|| of the last step (FP64)            */
-    int status;             /* STDG_OK or STDG_ENOTCONV                               */
+    int status;             /* STDG_OK, STDG_ENOTCONV or STDG_ENONFINITE              */
 } stdg_stats;
 
 /* Context.  `cuda_stream` is a cudaStream_t (may be NULL). */
@@ -141,7 +146,9 @@ int stdg_set_receivers(stdg_ctx* ctx, int n_rec, const double* xr);
 
 /* Advances every shot by n_steps slabs of size dt (Eq. velocity.sys + NM26, or the
  * Crank-Nicolson Eqs. velocity.sys.cn + NM26.cn).  `out` may be NULL.  Returns
- * STDG_ENOTCONV if some solve hit max_iters (the state is still advanced). */
+ * STDG_ENOTCONV if some solve hit max_iters (the state is still advanced, stats filled),
+ * STDG_ENONFINITE if a residual norm became NaN or Inf (the solve stops at once instead
+ * of running to max_iters). */
 int stdg_step(stdg_ctx* ctx, double dt, int n_steps, stdg_stats* out);
 
 /* Simulation time of the carried state. */
@@ -161,7 +168,9 @@ int stdg_read_receivers(stdg_ctx* ctx, double* out, int64_t cap);
 int stdg_apply_operator(stdg_ctx* ctx, double dt, const double* x, double* y);
 
 /* Same on device buffers owned by the caller (FP64; or FP32 when fp32 != 0, using
- * the FP32 copy of the blocks). */
+ * the FP32 copy of the blocks).  Asynchronous on the context stream in FP64; the FP32
+ * path synchronises the stream to check the bounded waits of its face kernel and returns
+ * STDG_ECUDA if one gave up (y is then invalid; the context stays usable). */
 int stdg_apply_operator_device(stdg_ctx* ctx, double dt, const void* x_dev, void* y_dev, int fp32);
 
 /* Sizes: what = 0 n_elem, 1 n_face, 2 N_phi, 3 N_psi, 4 N_gamma, 5 stress comps s,
@@ -223,7 +232,11 @@ int stdg_apply_preconditioner(stdg_ctx* ctx, double dt, const double* r, double*
  * that loads it until exit); velocity vectors longer than 2^28 values are rejected with
  * STDG_EINVAL.  The first call on a device looks up that array's device address, so make
  * it before any stream capture.  Calls share the array: calls that overlap on the GPU race
- * and must be ordered by the caller.  Asynchronous on the context stream. */
+ * and must be ordered by the caller.  r_dev must not be x_dev or b_dev (STDG_EINVAL):
+ * A x is written into r_dev while x_dev is still being read.  The device address of the
+ * array is looked up once per device and kept for the life of the process, so it assumes
+ * the device's primary context is not reset (cudaDeviceReset) in between.  Asynchronous
+ * on the context stream. */
 int stdg_residual_noalloc(stdg_ctx* ctx, double dt, const double* x_dev, const double* b_dev,
                           double* r_dev, double* out_dev);
 
@@ -256,6 +269,13 @@ int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out
  * the kernels run on zero vectors in buffers allocated for the call.  No counterpart in
  * the paper. */
 int stdg_time_kernel(stdg_ctx* ctx, double dt, int which, int fp32, int n, double* ms_out);
+
+/* Failure-path testing (no counterpart in the paper): sets the context's device error word
+ * exactly as a face kernel whose bounded wait for a bulk copy gave up would.  The next call
+ * that checks the word (stdg_step, stdg_misfit_grad, the FP32 stdg_apply_operator_device,
+ * stdg_time_kernel) returns STDG_ECUDA once and clears it; stdg_step still advances the time
+ * and the receiver records, since the graph ran.  No kernel is made to fail. */
+int stdg_inject_wait_error(stdg_ctx* ctx);
 
 #ifdef __cplusplus
 }

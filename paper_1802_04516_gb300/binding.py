@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libstdg.so")
 
 STDG_OK, STDG_EINVAL, STDG_EMESH, STDG_ENOMEM, STDG_ECUDA, STDG_ENOTCONV, STDG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+STDG_ENONFINITE = -7
 SCHEME = {"cn": 0, "stdg": 1}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
 
@@ -66,6 +67,7 @@ SIGNATURES = {
     "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
     "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_residual_noalloc": (C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
+    "stdg_inject_wait_error": (C.c_int, [_P]),
 }
 
 _lib = None
@@ -345,6 +347,10 @@ class Solver:
         ms = C.c_double(0.0)
         self._chk(self.lib.stdg_time_kernel(self.h, dt, int(which), 1 if fp32 else 0, n, C.byref(ms)))
         return ms.value
+
+    def inject_wait_error(self):
+        """Set the device error word as a timed-out bulk-copy wait would (failure-path tests)."""
+        self._chk(self.lib.stdg_inject_wait_error(self.h))
 
     def time_operator(self, dt, fp32=False, n=20):
         ms = C.c_double()

@@ -381,10 +381,10 @@ int misfit_grad_impl(stdg_ctx* c, double dt, int N, const double* data, int K, d
     ADJ_CUDA(cudaMemsetAsync(glf, 0, sizeof(double) * c->n_face, c->stream));
     ADJ_CUDA(cudaMemsetAsync(gmf, 0, sizeof(double) * c->n_face, c->stream));
     ADJ_CUDA(cudaMemsetAsync(grho, 0, sizeof(double) * c->n_elem, c->stream));
-    const unsigned egrid = (unsigned)std::min<int64_t>((ns * nvel + 255) / 256, 152 * 32);
+    const unsigned egrid = (unsigned)std::min<int64_t>((ns * nvel + 255) / 256, c->n_sm * 32);
     auto residual_into_av = [&](int n) {   // a_v += R^T (rec^n - d^n), n = 1..N
         const int64_t tot = (int64_t)ns * NR * d * NP;
-        adj_receivers_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 8), 256, 0, c->stream>>>(
+        adj_receivers_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, c->n_sm * 8), 256, 0, c->stream>>>(
             ns, NR, d, NP, ntr, c->d_rec_elem, c->d_rec_phi, c->d_records + (rec0 + n - 1) * per_rec,
             c->rec_cap_steps * per_rec, d_data + (int64_t)(n - 1) * per_rec, (int64_t)N * per_rec, av);
         note_launch(c);
@@ -401,7 +401,7 @@ int misfit_grad_impl(stdg_ctx* c, double dt, int N, const double* data, int K, d
         cudaFuncSetAttribute(adj_face_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
         cudaFuncSetAttribute(adj_rhs_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
     }
-    const unsigned fgrid = (unsigned)std::min<int64_t>((c->n_face + 3) / 4, 152 * 16);
+    const unsigned fgrid = (unsigned)std::min<int64_t>((c->n_face + 3) / 4, c->n_sm * 16);
     // seed: a_v^N = R^T (rec^N - d^N), a_s^N = 0
     residual_into_av(N);
     for (int seg = nseg - 1; seg >= 0; --seg) {

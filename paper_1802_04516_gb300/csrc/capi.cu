@@ -197,6 +197,22 @@ int precond_for_dt(stdg_ctx* c, double dt) {
 
 using namespace stdg;
 
+namespace stdg {
+int take_device_error(stdg_ctx* c) {
+    c->wait_gave_up = false;
+    if (!c->d_err) return STDG_OK;
+    int e = 0;
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    STDG_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return STDG_OK;
+    STDG_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    c->wait_gave_up = true;
+    STDG_FAIL(c, STDG_ECUDA, e == 1 ? "a device-side wait gave up (bounded mbarrier wait); results of this call are invalid"
+                                    : "a device-side wait gave up and a copy in flight could not be drained; results of "
+                                      "this call are invalid");
+}
+}  // namespace stdg
+
 #define CHECK_CTX(c) do { if (!(c)) return STDG_EINVAL; } while (0)
 #define NEED_MESH(c) do { if (!(c)->have_mesh) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_mesh first"); } while (0)
 #define NEED_ALL(c) do { NEED_MESH(c); if (!(c)->have_material) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_material first"); } while (0)
@@ -225,6 +241,16 @@ int stdg_create(stdg_ctx** out, int dim, const stdg_options* opt, void* cuda_str
         cudaError_t e = cudaStreamCreate(&c->stream);   // blocking: ordered with the legacy stream
         if (e != cudaSuccess) { delete c; return STDG_ECUDA; }
         c->own_stream = true;
+    }
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+            if (c->own_stream) cudaStreamDestroy(c->stream);
+            delete c;
+            return STDG_ECUDA;
+        }
+        c->n_sm = nsm;
     }
     build_ref_tables(dim, opt->p, opt->p_gamma, &c->rt);
     c->Nphi = c->rt.Nphi;
@@ -672,6 +698,7 @@ int stdg_apply_operator_device(stdg_ctx* c, double dt, const void* x_dev, void* 
         if (rc != STDG_OK) return rc;
         if ((rc = upload_material32(c)) != STDG_OK) return rc;
         STDG_CUDA(c, launch_apply32(c, dt, (const float*)x_dev, (float*)y_dev, 1.0));
+        return take_device_error(c);   // the FP32 face kernel's bounded waits
     } else {
         STDG_CUDA(c, launch_apply(c, dt, (const double*)x_dev, (double*)y_dev, 1.0));
     }
@@ -830,6 +857,15 @@ int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double*
     dev_free(c, dx);
     dev_free(c, dy);
     dev_free(c, dw);
+    return take_device_error(c);
+}
+
+int stdg_inject_wait_error(stdg_ctx* c) {
+    CHECK_CTX(c);
+    if (!c->d_err) STDG_FAIL(c, STDG_ESTATE, "no device error word");
+    const int one = 1;
+    STDG_CUDA(c, cudaMemcpyAsync(c->d_err, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    STDG_CUDA(c, cudaStreamSynchronize(c->stream));
     return STDG_OK;
 }
 

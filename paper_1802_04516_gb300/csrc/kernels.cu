@@ -539,7 +539,7 @@ static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* m
     const int NG = c->Ng;
     if (mass) {
         const int64_t rows = c->n_elem * nshots * c->dim * NG;
-        mass_kernel<NP, R><<<(unsigned)std::min<int64_t>((rows + 127) / 128, 152 * 64), 128, 0, c->stream>>>(
+        mass_kernel<NP, R><<<(unsigned)std::min<int64_t>((rows + 127) / 128, c->n_sm * 64), 128, 0, c->stream>>>(
             c->n_elem * nshots, c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
     }
     if (!face) return cudaGetLastError();
@@ -706,7 +706,7 @@ __global__ void rhs_source_kernel(int dim, int NP, int NG, const RefTables* __re
 template <int NP>
 static void rhs_mass_stdg(stdg_ctx* c, const double* vtr, double* b) {
     const int64_t rows = c->n_elem * c->dim;
-    rhs_mass_stdg_kernel<NP><<<(unsigned)std::min<int64_t>((rows + 127) / 128, 152 * 64), 128, 0, c->stream>>>(
+    rhs_mass_stdg_kernel<NP><<<(unsigned)std::min<int64_t>((rows + 127) / 128, c->n_sm * 64), 128, 0, c->stream>>>(
         c->n_elem, c->dim, c->Ng, c->d_rt, c->d_rhoJ, vtr, b); note_launch(c);
 }
 
@@ -816,7 +816,7 @@ __global__ void traces_kernel(int64_t nrows, int NP, int NG, const RefTables* __
 
 cudaError_t launch_traces(stdg_ctx* c, int shot, const double* x) {
     const int64_t rows = c->n_elem * c->dim;
-    traces_kernel<<<(unsigned)std::min<int64_t>((rows * c->Nphi + 255) / 256, 152 * 32), 256, 0, c->stream>>>(
+    traces_kernel<<<(unsigned)std::min<int64_t>((rows * c->Nphi + 255) / 256, c->n_sm * 32), 256, 0, c->stream>>>(
         rows, c->Nphi, c->Ng, c->d_rt, x, c->d_vtr + shot * c->ntr); note_launch(c);
     return cudaGetLastError();
 }
@@ -831,7 +831,7 @@ __global__ void initial_guess_kernel(int64_t nrows, int NP, int NG, const double
 
 cudaError_t launch_initial_guess(stdg_ctx* c, int shot, double* x) {
     const int64_t rows = c->n_elem * c->dim;
-    initial_guess_kernel<<<(unsigned)std::min<int64_t>((rows * c->Ng * c->Nphi + 255) / 256, 152 * 32), 256, 0, c->stream>>>(
+    initial_guess_kernel<<<(unsigned)std::min<int64_t>((rows * c->Ng * c->Nphi + 255) / 256, c->n_sm * 32), 256, 0, c->stream>>>(
         rows, c->Nphi, c->Ng, c->d_vtr + shot * c->ntr, x); note_launch(c);
     return cudaGetLastError();
 }
@@ -906,10 +906,10 @@ __global__ void energy_kernel(int64_t n_elem, int64_t n_face, int NP, const RefT
 cudaError_t launch_energy(stdg_ctx* c, int shot, double* d_out) {
     cudaMemsetAsync(d_out, 0, sizeof(double), c->stream);
     if (c->dim == 2) {
-        energy_kernel<2><<<152 * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
+        energy_kernel<2><<<c->n_sm * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
                                                          c->d_lamf, c->d_muf, c->d_sigtr + shot * c->nsig, d_out);
     } else {
-        energy_kernel<3><<<152 * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
+        energy_kernel<3><<<c->n_sm * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
                                                          c->d_lamf, c->d_muf, c->d_sigtr + shot * c->nsig, d_out);
     }
     note_launch(c);

@@ -118,6 +118,9 @@ extern "C" int stdg_residual_noalloc(stdg_ctx* c, double dt, const double* x_dev
     if (!c) return STDG_EINVAL;
     if (!c->have_mesh || !c->have_material) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_mesh and stdg_set_material first");
     if (!x_dev || !b_dev || !r_dev || !out_dev || !(dt > 0)) STDG_FAIL(c, STDG_EINVAL, "bad residual arguments");
+    // A x is written into r while the operator still reads x, and the kernels take b and r
+    // as non-aliasing pointers
+    if (r_dev == x_dev || r_dev == b_dev) STDG_FAIL(c, STDG_EINVAL, "r_dev must differ from x_dev and b_dev");
     const int64_t n = c->nvel;
     if (n > (int64_t)kParts * kChunk)
         STDG_FAIL(c, STDG_EINVAL, "velocity vector of " + std::to_string(n) + " values exceeds the residual scratch limit of " +

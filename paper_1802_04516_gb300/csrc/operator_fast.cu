@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
 // copied into shared memory by cp.async.bulk (one elected lane, completion on a per-warp
 // mbarrier) while the warp computes the current face.  Register/broadcast arithmetic as
 // above.  Every wait on an mbarrier is bounded; on timeout the kernel records the error
-// in *err and the warp stops.
+// in *err and the warp stops after draining its copies in flight (bounded too).
 // ---------------------------------------------------------------------------------
 template <int DIM, int NP, int NG, typename R>
 struct FaceTma {
@@ -284,8 +284,11 @@ __global__ void __launch_bounds__(128, (FaceTma<DIM, NP, NG, R>::MIN_BLOCKS)) fa
         if (fn < n_face && lane == 0) issue(fn, st ^ 1);
         if (!mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit)) {
             if (lane == 0) atomicExch(err, 1);
-            // drain the copy issued for fn before leaving (bounded as well)
-            if (fn < n_face) mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit);
+            // before the CTA leaves, both stages' copies must have landed: the late one for f and
+            // the one issued for fn (both waits bounded); if either does not, record code 2
+            bool drained = mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit);
+            if (fn < n_face) drained = mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit) && drained;
+            if (!drained && lane == 0) atomicExch(err, 2);
             break;
         }
         if (st) ph1 ^= 1u; else ph0 ^= 1u;
@@ -382,7 +385,7 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
         const int wpb = 4;
         const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
         cudaFuncSetAttribute(face_apply_tma_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 152 * 16);
+        const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, (int64_t)c->n_sm * 16);
         face_apply_tma_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
             c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, c->d_err);
         note_launch(c);

@@ -408,7 +408,7 @@ cudaError_t launch_pre1_setup(stdg_ctx* c, const double* d_Rinv, const int32_t* 
                                           2 * (kMaxN / 2 + 1)) +
                         sizeof(int) * 2 * (kMaxN / 2 + 1);
     cudaFuncSetAttribute(pre1_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = (int)std::min<int64_t>(c->n_elem, 152 * 16);
+    const int grid = (int)std::min<int64_t>(c->n_elem, c->n_sm * 16);
     pre1_setup_kernel<<<grid, kPreThreads, smem, c->stream>>>(c->n_elem, c->dim, c->d_rt, d_elem_face, c->d_face_l, c->d_D,
                                                               c->d_lamf, c->d_muf, c->d_rhoJ, d_Rinv, c->d_preV, c->d_preLam,
                                                               d_status); note_launch(c);

@@ -263,7 +263,7 @@ cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status) {
     const double cfac = c->opt.scheme == STDG_SCHEME_CN ? 0.25 : 1.0;
     const size_t smem = pre2_setup_smem(c->dim, c->Nphi, c->Ng);
     cudaFuncSetAttribute(pre2_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = (int)std::min<int64_t>(c->n_elem, 152 * 8);
+    const int grid = (int)std::min<int64_t>(c->n_elem, c->n_sm * 8);
     pre2_setup_kernel<<<grid, kP2Threads, smem, c->stream>>>(c->n_elem, c->dim, c->d_rt, c->d_elem_face, c->d_face_l,
                                                              c->d_face_r, c->d_D, c->d_lamf, c->d_muf, c->d_rhoJ, c->d_preV,
                                                              c->d_preB, cfac * dt * dt, c->d_pre2, c->d_pre2_32,

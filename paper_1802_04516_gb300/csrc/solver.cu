@@ -32,7 +32,6 @@
 namespace stdg {
 
 constexpr int kMaxRestart = 64;
-constexpr int kRedBlocks = 1216;    // 8 x 152 SMs
 constexpr int kRedThreads = 256;
 constexpr int kFinThreads = 1024;   // single-block reduction / control kernels
 constexpr int kDotChunk = 16;       // basis vectors per pass of the multi-dot kernels
@@ -60,7 +59,7 @@ struct DevScalars {
     int j, iters, flag_outer, flag_inner, max_iters, m;
     int ir_flag, ir_count, ir_max;
     // statistics, reset by the host before a batch of steps
-    int st_total, st_max, st_refine, st_notconv;
+    int st_total, st_max, st_refine, st_notconv, st_nonfinite;
     double st_final_rel, st_iters_sum;
     unsigned long long launches;      // kernel executions since the last reset
 };
@@ -70,7 +69,8 @@ struct Workspace {
     int ns = 1;                   // shots
     int64_t nvec = 0;             // values per shot (velocity DOFs)
     int64_t n = 0, ldv = 0;       // stacked length, basis leading dimension
-    unsigned G = kRedBlocks;      // blocks per shot of the streaming kernels (grid G x ns)
+    unsigned G = 1;               // blocks per shot of the streaming kernels (grid G x ns)
+    unsigned red_blocks = 1;      // blocks of the single-vector streaming kernels: 8 per SM
     DevScalars* sc = nullptr;
     ShotScalars* ss = nullptr;    // [ns]
     double* partials = nullptr;   // [slot][shot][block], (kMaxRestart + 2) slots
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kFinThreads) cg_init_final_kernel(DevScalars* 
         t.tol_abs = rel_tol * t.bnorm;
         t.zero_x = active && t.bnorm == 0.0;
         t.converged = !active || sqrt(t.rr) <= t.tol_abs;
-        t.active = !t.converged;
+        t.active = !t.converged && isfinite(t.rr) && isfinite(t.bnorm);   // a NaN/Inf residual stops the shot
         t.alpha = t.beta = 0.0;
         any |= t.active;
     }
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kFinThreads) cg_beta_kernel(DevScalars* sc, Sh
             t.pq = rz;
             t.rr = t.red[0];
             t.converged = sqrt(t.rr) <= t.tol_abs;
-            t.active = !t.converged;
+            t.active = !t.converged && isfinite(t.rr);
         }
         if (!t.active) t.beta = 0.0;
         any |= t.active;
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kFinThreads) gm_cycle_start_kernel(DevScalars*
         t.resid = beta;
         t.jj = 0;
         if (!t.converged) t.converged = beta <= t.tol_abs;
-        t.active = !t.converged;
+        t.active = !t.converged && isfinite(beta) && isfinite(t.tol_abs);   // a NaN/Inf residual stops the shot
         for (int k = 0; k <= m; ++k) t.g[k] = 0.0;
         t.g[0] = beta;
         any |= t.active;
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kFinThreads) gm_givens_kernel(DevScalars* sc, 
             t.g[J] = cs * t.g[J];
             t.resid = fabs(t.g[J + 1]);
             t.jj = J + 1;
-            if (t.resid <= t.tol_abs || den == 0.0) t.active = 0;
+            if (t.resid <= t.tol_abs || den == 0.0 || !isfinite(t.resid)) t.active = 0;
         }
         any |= t.active;
     }
@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(kFinThreads) ir_init_kernel(DevScalars* sc, Sh
         t.ir_rnorm = t.ir_bnorm;
         t.ir_zero = t.ir_bnorm == 0.0;
         t.ir_conv = t.ir_zero;
-        any |= !t.ir_conv;
+        any |= !t.ir_conv && isfinite(t.ir_bnorm);
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(kFinThreads) ir_check_kernel(DevScalars* sc, S
         t.ir_rnorm = sqrt(t.red[0]);
         t.ir_conv = t.ir_zero || t.ir_rnorm <= t.ir_tol_abs;
         t.ir_scale = !t.ir_conv && t.ir_rnorm > 0.0 ? 1.0 / t.ir_rnorm : 0.0;
-        any |= !t.ir_conv;
+        any |= !t.ir_conv && isfinite(t.ir_rnorm) && isfinite(t.ir_bnorm);   // no refinement of a NaN/Inf residual
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) sc->ir_flag = any && sc->ir_count < sc->ir_max && sc->st_total < max_total;
@@ -835,16 +835,18 @@ __global__ void ir_end_kernel(DevScalars* sc, cudaGraphConditionalHandle h, int 
 __global__ void __launch_bounds__(kFinThreads) solve_stats_kernel(DevScalars* sc, const ShotScalars* ss, int ns, int mode) {
     __shared__ double worst[kFinThreads];
     double rel = 0.0;
-    int notconv = 0;
+    int notconv = 0, nonfinite = 0;
     for (int s = threadIdx.x; s < ns; s += blockDim.x) {
         const ShotScalars& t = ss[s];
         double r, bn;
         if (mode == 2) { r = t.ir_zero ? 0.0 : t.ir_rnorm; bn = t.ir_bnorm; notconv |= !t.ir_conv; }
         else { r = t.zero_x ? 0.0 : mode == 1 ? sqrt(t.rr) : t.resid; bn = t.bnorm; notconv |= !t.converged; }
+        nonfinite |= !isfinite(r) || !isfinite(bn);
         rel = fmax(rel, bn > 0 ? r / bn : 0.0);
     }
     worst[threadIdx.x] = rel;
     notconv = __syncthreads_or(notconv);
+    nonfinite = __syncthreads_or(nonfinite);
     if (threadIdx.x != 0) return;
     for (int i = 1; i < (int)blockDim.x; ++i) rel = fmax(rel, worst[i]);
     int it;
@@ -856,6 +858,7 @@ __global__ void __launch_bounds__(kFinThreads) solve_stats_kernel(DevScalars* sc
         it = sc->iters;
     }
     if (notconv) sc->st_notconv = 1;
+    if (nonfinite) sc->st_nonfinite = 1;
     sc->st_final_rel = rel;
     sc->st_max = max(sc->st_max, it);
     sc->st_iters_sum += (double)it;
@@ -959,7 +962,7 @@ static void solve_cg(Flow& F, Apply apply, Prec prec, bool use_prec, const R* b,
                dot_partial_kernel<R, R><<<grid, kRedThreads, 0, c->stream>>>(nv, r, zz, ws->partials, 2); note_launch(c);
                cg_init_final_kernel<<<1, kFinThreads, 0, c->stream>>>(ws->sc, ws->ss, ws->partials, ns, G, rel_tol, max_iters,
                                                                       bnorm_given, gate_ir, h, use); note_launch(c);
-               copy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, zz, p); note_launch(c);
+               copy_kernel<R><<<ws->red_blocks, kRedThreads, 0, c->stream>>>(n, zz, p); note_launch(c);
            },
            [&](cudaGraphConditionalHandle h, int use) {
                F.check(apply(p, q));
@@ -1027,7 +1030,7 @@ static void solve_gmres(Flow& F, Apply apply, ApplyIdx apply_idx, Prec prec, boo
                if (use_prec) {   // x += P^{-1} (V y)
                    gm_combine_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, ss, V, tbuf, 0); note_launch(c);
                    F.check(prec(tbuf, zbuf, nullptr, 0));
-                   axpy_kernel<R><<<kRedBlocks, kRedThreads, 0, c->stream>>>(n, x, zbuf); note_launch(c);
+                   axpy_kernel<R><<<ws->red_blocks, kRedThreads, 0, c->stream>>>(n, x, zbuf); note_launch(c);
                } else {
                    gm_combine_kernel<R><<<grid, kRedThreads, 0, c->stream>>>(nv, ldv, ss, V, x, 1); note_launch(c);
                }
@@ -1127,7 +1130,8 @@ int solver_setup(stdg_ctx* c) {
     ws->ns = c->n_shots;
     ws->nvec = c->nvel;
     ws->n = c->nvel * (int64_t)c->n_shots;
-    ws->G = (unsigned)std::max(1, kRedBlocks / ws->ns);
+    ws->red_blocks = (unsigned)(8 * c->n_sm);
+    ws->G = (unsigned)std::max(1, (int)ws->red_blocks / ws->ns);
     const int64_t n = ws->n;
     const bool cn = c->opt.scheme == STDG_SCHEME_CN && c->opt.preconditioner != 2;   // CG workspace
     const bool mixed = c->opt.precision != STDG_FP64;
@@ -1206,7 +1210,7 @@ static void record_solve_only(Flow& F, double dt) {
 // cached CUDA graph per kind and dt, or from the host loop; then reads the statistics.
 static int run_body_n(stdg_ctx* c, double dt, int n, int kind, stdg_stats* st) {
     Workspace* ws = W(c);
-    STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_total, 0, sizeof(int) * 4, c->stream));
+    STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_total, 0, sizeof(int) * 5, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->st_final_rel, 0, sizeof(double) * 2, c->stream));
     STDG_CUDA(c, cudaMemsetAsync(&ws->sc->launches, 0, sizeof(unsigned long long), c->stream));
     auto record = [&](Flow& F) {
@@ -1253,14 +1257,14 @@ static int run_body_n(stdg_ctx* c, double dt, int n, int kind, stdg_stats* st) {
         st->iters_max = h.st_max;
         st->refinements = h.st_refine;
         st->final_rel_res = h.st_final_rel;
-        st->status = h.st_notconv ? STDG_ENOTCONV : STDG_OK;
+        st->status = h.st_nonfinite ? STDG_ENONFINITE : h.st_notconv ? STDG_ENOTCONV : STDG_OK;
     }
     c->last_launches = (int64_t)h.launches;
-    if (c->d_err) {
-        int e = 0;
-        STDG_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) STDG_FAIL(c, STDG_ECUDA, "a device-side wait gave up (bounded mbarrier wait)");
+    {
+        const int rc = take_device_error(c);
+        if (rc != STDG_OK) return rc;
     }
+    if (h.st_nonfinite) STDG_FAIL(c, STDG_ENONFINITE, "a residual or right-hand-side norm is NaN or Inf (input overflow?)");
     if (h.st_notconv) STDG_FAIL(c, STDG_ENOTCONV, "Krylov solve reached max_iters");
     return STDG_OK;
 }
@@ -1278,8 +1282,11 @@ int solver_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* st) {
         double stepidx = (double)c->rec_steps;
         STDG_CUDA(c, cudaMemcpyAsync(ws->dparams + 2, &stepidx, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     }
+    c->wait_gave_up = false;
     const int rc = run_body_n(c, dt, n_steps, 0, st);
-    if (rc == STDG_OK || rc == STDG_ENOTCONV) {   // the state advanced either way
+    // the state advanced when the solve did not converge and when a bounded wait gave up
+    // (then with invalid values); a CUDA error proper leaves time and records where they were
+    if (rc == STDG_OK || rc == STDG_ENOTCONV || rc == STDG_ENONFINITE || c->wait_gave_up) {
         c->t = t0 + n_steps * dt;
         c->rec_steps += n_steps;
     }

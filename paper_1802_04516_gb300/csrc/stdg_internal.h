@@ -135,8 +135,13 @@ struct stdg_ctx {
     void *d_p2y = nullptr, *d_p2t = nullptr;   // P_1 r and A P_1 r, stacked over shots (FP64-sized)
     int* d_p2status = nullptr;
 
-    // ---- device error word: set by kernels whose bounded waits ran out (checked after each call)
+    // ---- device error word: set by kernels whose bounded waits ran out (1: a copy did not
+    // arrive in time; 2: a copy still in flight could not be drained).  Read and cleared by
+    // take_device_error after every call that can launch such a kernel.
     int* d_err = nullptr;
+    bool wait_gave_up = false;   // the last take_device_error found the word set
+
+    int n_sm = 152;              // multiprocessors of the context's device (grid sizing)
 
     // ---- solver workspace (solver.cu)
     void* ws = nullptr;
@@ -163,6 +168,10 @@ inline void note_launch(stdg_ctx* c, long k = 1) {
     return e_ == cudaErrorMemoryAllocation ? STDG_ENOMEM : STDG_ECUDA; } } while (0)
 
 namespace stdg {
+// Synchronises the context stream, reads the device error word and clears it.  Returns
+// STDG_OK, or STDG_ECUDA with a message when a bounded wait gave up (the results of the
+// launches since the last check are then invalid; the context stays usable).
+int take_device_error(stdg_ctx* c);
 int dev_alloc(stdg_ctx* c, void** p, size_t bytes);
 void dev_release(stdg_ctx* c, void* p);   // frees one allocation made by dev_alloc
 void dev_free_all(stdg_ctx* c);
