@@ -112,3 +112,29 @@ def patch_operator_rows(w, elems, x, nb=None, quad_n=None):
         A = dz.assemble(w.dt, w.scheme)
         rows.append((A @ xe[P].ravel()).reshape(len(P), -1)[0])
     return np.array(rows)
+
+
+def extended_patch_rows(w, elems, x, nb=None, quad_n=None):
+    """(A x)_i for the sampled elements in extended precision (oracle/extended.py), each on
+    the patch {i and its face neighbours} as in patch_operator_rows.  Meshes without periodic
+    faces only.  Returns an np.longdouble array (len(elems), d * N_gamma * N_phi)."""
+    from oracle.extended import PatchOperator
+    assert w.period is None
+    nb = face_neighbours(w.elem_vert) if nb is None else nb
+    xe = np.asarray(x).reshape(w.n_elem, -1)
+    rows = []
+    for i in elems:
+        P = np.concatenate([[i], np.sort(nb[i][nb[i] >= 0])])
+        verts, ev = np.unique(w.elem_vert[P], return_inverse=True)
+        ev = ev.reshape(len(P), -1)
+        op = PatchOperator(w.xyz[verts], ev, w.lam[P], w.mu[P], w.rho[P], w.p, w.p_gamma, w.scheme, w.dt,
+                           quad_n=quad_n)
+        rows.append(op.row(0, xe[P].ravel()).ravel())
+    return np.array(rows)
+
+
+def rel_l2_ext(a, ref):
+    """rel_l2 with the reference kept in its own (extended) precision."""
+    ref = np.asarray(ref)
+    a = np.asarray(a).astype(ref.dtype)
+    return float(np.sqrt(np.sum((a - ref) ** 2)) / np.sqrt(np.sum(ref * ref)))
