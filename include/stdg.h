@@ -221,6 +221,16 @@ int stdg_reference_tables(int dim, int p, int p_gamma, double* Mref, double* W, 
  * 1 or 2; with 2, the shots must be set (stdg_set_shots or a source / state call). */
 int stdg_apply_preconditioner(stdg_ctx* ctx, double dt, const double* r, double* z);
 
+/* z_dev = P^{-1} r_dev for every shot of the context at once (stacked shot-major, n_shots x
+ * velocity values per slab, canonical layout), on device buffers owned by the caller (r_dev
+ * and z_dev distinct), slab size dt.  fp32 = 0: the FP64 preconditioner of the FP64 solver;
+ * fp32 != 0 (mixed-precision contexts only): the FP32 one of the inner solve -- for the stencil
+ * preconditioner with several shots and d N_phi N_gamma = 36, its element-local step runs on
+ * the tensor cores (kind::tf32 with S^{-1} rounded to TF32 and the vector split into two TF32
+ * terms).  Appendix A, Eq. pre1 (Pre1) or Eqs. APPRE1-APPRE2 (Pre2).  Synchronises the stream;
+ * STDG_ESTATE without a preconditioner or shots, STDG_ECUDA if a bounded wait gave up. */
+int stdg_apply_preconditioner_device(stdg_ctx* ctx, double dt, const void* r_dev, void* z_dev, int fp32);
+
 /* Residual of the velocity system without allocating: r_dev = b_dev - A x_dev for slab
  * size dt (A as in stdg_apply_operator, FP64, one shot, canonical layout) and
  * out_dev[0] = ||r|| / ||b|| (||r|| when b = 0), out_dev[1] = ||r||.  All four pointers
@@ -264,7 +274,9 @@ int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out
 /* Average device time of one launch of a single kernel, over n back-to-back launches on
  * the context's stream (CUDA events), for roofline figures.  which: 0 face term of the
  * operator (as stdg_time_operator), 1 block-Jacobi apply, 2 the element-local step of the
- * stencil preconditioner (z = S^{-1} (2 r - w)), 3 the whole operator (mass + face).
+ * stencil preconditioner (z = S^{-1} (2 r - w)), 3 the whole operator (mass + face), 4 the
+ * element-local step for all the context's shots at once (FP32 only; the tensor-core kernel
+ * where it applies).
  * fp32 selects the FP32 blocks (mixed-precision contexts only for 1 and 2).  Timing only:
  * the kernels run on zero vectors in buffers allocated for the call.  No counterpart in
  * the paper. */

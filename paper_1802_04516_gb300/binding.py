@@ -68,6 +68,7 @@ SIGNATURES = {
     "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_residual_noalloc": (C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
     "stdg_inject_wait_error": (C.c_int, [_P]),
+    "stdg_apply_preconditioner_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
 }
 
 _lib = None
@@ -320,6 +321,10 @@ class Solver:
         z = np.zeros_like(r)
         self._chk(self.lib.stdg_apply_preconditioner(self.h, dt, _d(r), _d(z)))
         return z
+
+    def apply_preconditioner_device(self, dt, r_ptr, z_ptr, fp32=False):
+        """z = P^{-1} r for all shots (stacked) on device buffers; synchronises the stream."""
+        self._chk(self.lib.stdg_apply_preconditioner_device(self.h, dt, _P(r_ptr), _P(z_ptr), 1 if fp32 else 0))
 
     def get_faces(self):
         fl = np.zeros(self.n_face, dtype=np.int32)

@@ -166,6 +166,9 @@ static int setup_pre1(stdg_ctx* c) {
             if ((rc = dev_alloc(c, (void**)&c->d_pre2, sizeof(double) * nS)) != STDG_OK) return rc;
             if (c->opt.precision != STDG_FP64 &&
                 (rc = dev_alloc(c, (void**)&c->d_pre2_32, sizeof(float) * ne * pre2_stride32(c))) != STDG_OK) return rc;
+            // tensor-core image of the FP32 blocks for batches of shots
+            if (c->opt.precision != STDG_FP64 && pre2_mma_supported(c) &&
+                (rc = dev_alloc(c, (void**)&c->d_pre2_mma, sizeof(float) * pre2_mma_image_floats(c))) != STDG_OK) return rc;
             if ((rc = dev_alloc(c, (void**)&c->d_p2status, sizeof(int))) != STDG_OK) return rc;
         }
     }
@@ -182,6 +185,7 @@ int precond_for_dt(stdg_ctx* c, double dt) {
     if (c->opt.preconditioner == 2) {
         STDG_CUDA(c, cudaMemsetAsync(c->d_p2status, 0, sizeof(int), c->stream));
         STDG_CUDA(c, launch_pre2_setup(c, dt, c->d_p2status));
+        if (c->d_pre2_mma) STDG_CUDA(c, launch_pre2_mma_image(c));
         int status = 0;
         STDG_CUDA(c, cudaMemcpyAsync(&status, c->d_p2status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         STDG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -322,12 +326,14 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     c->d_preV32 = c->d_preB32 = nullptr;
     c->d_pre2 = nullptr;
     c->d_pre2_32 = nullptr;
+    c->d_pre2_mma = nullptr;
     c->d_p2y = c->d_p2t = nullptr;
     c->d_p2status = nullptr;
     c->pre_dt = -1.0;
     c->rec_cap_steps = 0;
     c->rec_steps = 0;
     c->d_X = c->d_Jinv = c->d_detJ = c->d_faceX = c->d_shift = c->d_normal = c->d_xc = c->d_hj = nullptr;
+    c->d_frame = nullptr;
     c->d_D = c->d_L = c->d_Mdual = nullptr;
     c->d_D32 = nullptr;
     c->d_lamf = c->d_muf = c->d_rhoJ = nullptr;
@@ -363,6 +369,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     ALLOC(c->d_normal, sizeof(double) * nf * d);
     ALLOC(c->d_xc, sizeof(double) * nf * d);
     ALLOC(c->d_hj, sizeof(double) * nf);
+    ALLOC(c->d_frame, sizeof(double) * nf * d * d);
     ALLOC(c->d_D, sizeof(double) * nf * 2 * d * NP * NP);
     ALLOC(c->d_L, sizeof(double) * nf * NP * NP);
     ALLOC(c->d_Mdual, sizeof(double) * nf * NP * NP);
@@ -384,6 +391,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     UP(c->d_normal, c->hm.normal.data(), sizeof(double) * nf * d);
     UP(c->d_xc, c->hm.xc.data(), sizeof(double) * nf * d);
     UP(c->d_hj, c->hm.hj.data(), sizeof(double) * nf);
+    UP(c->d_frame, c->hm.frame.data(), sizeof(double) * nf * d * d);
     // blocks D_{i,j} and dual mass matrices, exact for degree 2p + 1 on every sub-cell
     Rule rv = simplex_rule(d, c->rt.p + 2), rf = simplex_rule(d - 1, c->rt.p + 2);
     std::vector<double> pv, pf;
@@ -809,10 +817,33 @@ int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z
     return STDG_OK;
 }
 
+int stdg_apply_preconditioner_device(stdg_ctx* c, double dt, const void* r_dev, void* z_dev, int fp32) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!c->opt.preconditioner || !c->d_preV) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
+    if (!r_dev || !z_dev || r_dev == z_dev || !(dt > 0)) STDG_FAIL(c, STDG_EINVAL, "bad preconditioner arguments");
+    if (fp32 && c->opt.precision == STDG_FP64) STDG_FAIL(c, STDG_ESTATE, "FP32 preconditioner blocks exist only in mixed precision");
+    int rc = precond_for_dt(c, dt);
+    if (rc != STDG_OK) return rc;
+    if (c->opt.preconditioner == 2 && !c->d_p2y) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_shots (or set a state) first");
+    if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
+    if (fp32 && (rc = upload_material32(c)) != STDG_OK) return rc;
+    const int ns = c->n_shots;
+    if (c->opt.preconditioner == 2)
+        STDG_CUDA(c, fp32 ? launch_pre2_apply32(c, (const float*)r_dev, (float*)z_dev, nullptr, 0, ns)
+                          : launch_pre2_apply(c, (const double*)r_dev, (double*)z_dev, nullptr, 0, ns));
+    else
+        STDG_CUDA(c, fp32 ? launch_pre1_apply32(c, (const float*)r_dev, (float*)z_dev, nullptr, 0, ns)
+                          : launch_pre1_apply(c, (const double*)r_dev, (double*)z_dev, nullptr, 0, ns));
+    return take_device_error(c);
+}
+
 int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double* ms_out) {
     CHECK_CTX(c);
     NEED_ALL(c);
-    if (n < 1 || !ms_out || which < 0 || which > 3) STDG_FAIL(c, STDG_EINVAL, "bad timing arguments");
+    if (n < 1 || !ms_out || which < 0 || which > 4) STDG_FAIL(c, STDG_EINVAL, "bad timing arguments");
+    if (which == 4 && (c->opt.preconditioner != 2 || !fp32))
+        STDG_FAIL(c, STDG_ESTATE, "the batched local step is timed for the FP32 stencil preconditioner");
     if (which == 1 && !c->opt.preconditioner) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
     if (which == 2 && c->opt.preconditioner != 2) STDG_FAIL(c, STDG_ESTATE, "context created without the stencil preconditioner");
     if (which == 2 && fp32 && !c->d_pre2_32) STDG_FAIL(c, STDG_ESTATE, "FP32 stencil blocks exist only in mixed precision");
@@ -820,11 +851,11 @@ int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double*
     int rc;
     if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
     if (fp32 && (rc = upload_material32(c)) != STDG_OK) return rc;
-    if (which == 1 || which == 2) {
+    if (which == 1 || which == 2 || which == 4) {
         if ((rc = precond_for_dt(c, dt)) != STDG_OK) return rc;
     }
     void *dx = nullptr, *dy = nullptr, *dw = nullptr;
-    const size_t bytes = (fp32 ? sizeof(float) : sizeof(double)) * c->nvel;
+    const size_t bytes = (fp32 ? sizeof(float) : sizeof(double)) * c->nvel * (which == 4 ? c->n_shots : 1);
     if ((rc = dev_alloc(c, &dx, bytes)) != STDG_OK) return rc;
     if ((rc = dev_alloc(c, &dy, bytes)) != STDG_OK) { dev_free(c, dx); return rc; }
     if ((rc = dev_alloc(c, &dw, bytes)) != STDG_OK) { dev_free(c, dx); dev_free(c, dy); return rc; }
@@ -837,6 +868,7 @@ int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double*
             case 1: return fp32 ? launch_pre1_apply32(c, (const float*)dx, (float*)dy, nullptr, 0)
                                 : launch_pre1_apply(c, (const double*)dx, (double*)dy, nullptr, 0);
             case 2: return launch_pre2_local(c, fp32, dx, dw, dy);
+            case 4: return launch_pre2_local_batch(c, (const float*)dx, (const float*)dw, (float*)dy);
             default: return fp32 ? launch_apply32(c, dt, (const float*)dx, (float*)dy, 1.0, nullptr, 0, 1)
                                  : launch_apply(c, dt, (const double*)dx, (double*)dy, 1.0, nullptr, 0, 1);
         }

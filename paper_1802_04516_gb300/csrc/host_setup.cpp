@@ -116,6 +116,15 @@ void build_ref_tables(int dim, int p, int pg, RefTables* rt) {
         }
     }
     rt->Nphi = rt->Npsi = n;
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < 3; ++r) {
+            int want[3] = {rt->exps[i][0], rt->exps[i][1], rt->exps[i][2]};
+            ++want[r];
+            rt->succ[i][r] = -1;
+            if (r < dim)
+                for (int j = 0; j < n; ++j)
+                    if (rt->exps[j][0] == want[0] && rt->exps[j][1] == want[1] && rt->exps[j][2] == want[2]) rt->succ[i][r] = j;
+        }
     // equispaced nodes, z outer, y, x fastest
     std::vector<std::array<double, 3>> nodes;
     if (dim == 2) {
@@ -287,6 +296,7 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, 
     m->normal.assign(nf * dim, 0.0);
     m->xc.assign(nf * dim, 0.0);
     m->hj.assign(nf, 0.0);
+    m->frame.assign(nf * dim * dim, 0.0);
     for (int64_t f = 0; f < nf; ++f) {
         const int64_t el = m->face_l[f];
         const int fl = m->face_fl[f];
@@ -353,6 +363,65 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz, int64_t n_elem, 
         upd(bl);
         if (er >= 0) upd(br);
         m->hj[f] = h;
+        // principal-axis frame of R_j: covariance of the dual cell about x_j (a simplex S has
+        // int_S v v^T = |S| / ((d+1)(d+2)) (sum_i v_i v_i^T + (sum_i v_i)(sum_i v_i)^T), v = x - x_j),
+        // B_j = Cov^{-1/2}.  Monomials of y' = B_j (x - x_j) span the same P_p(R_j) as the Taylor
+        // monomials but stay well conditioned on thin dual cells (slivers).
+        double cov[3][3] = {{0}}, meas = 0.0;
+        auto add_sub = [&](const double* bc, double detJ) {
+            const double sub = detJ / (dim == 2 ? 2.0 : 6.0) / nv;   // |T_{i,j}| = |T_i| / (d+1)
+            double v[4][3], sv[3] = {0, 0, 0};
+            for (int q2 = 0; q2 < nv; ++q2)
+                for (int a = 0; a < dim; ++a) {
+                    v[q2][a] = (q2 < dim ? F[q2 * dim + a] : bc[a]) - m->xc[f * dim + a];
+                    sv[a] += v[q2][a];
+                }
+            const double k = sub / ((dim + 1) * (dim + 2));
+            for (int a = 0; a < dim; ++a)
+                for (int b2 = 0; b2 < dim; ++b2) {
+                    double t = sv[a] * sv[b2];
+                    for (int q2 = 0; q2 < nv; ++q2) t += v[q2][a] * v[q2][b2];
+                    cov[a][b2] += k * t;
+                }
+            meas += sub;
+        };
+        add_sub(bl, m->detJ[el]);
+        if (er >= 0) add_sub(br, m->detJ[er]);
+        double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, A[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b2 = 0; b2 < 3; ++b2) A[a][b2] = a < dim && b2 < dim ? cov[a][b2] / meas : (a == b2 ? 1.0 : 0.0);
+        for (int sweep = 0; sweep < 30; ++sweep) {   // cyclic Jacobi on the symmetric covariance
+            double off = 0;
+            for (int a = 0; a < dim; ++a)
+                for (int b2 = a + 1; b2 < dim; ++b2) off += A[a][b2] * A[a][b2];
+            if (off <= 1e-30 * (A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2])) break;
+            for (int pp = 0; pp < dim; ++pp)
+                for (int qq = pp + 1; qq < dim; ++qq) {
+                    if (A[pp][qq] == 0.0) continue;
+                    const double th = 0.5 * (A[qq][qq] - A[pp][pp]) / A[pp][qq];
+                    const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                    const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                    for (int k2 = 0; k2 < 3; ++k2) {   // A <- A J
+                        const double x1 = A[k2][pp], x2 = A[k2][qq];
+                        A[k2][pp] = cs * x1 - sn * x2;
+                        A[k2][qq] = sn * x1 + cs * x2;
+                    }
+                    for (int k2 = 0; k2 < 3; ++k2) {   // A <- J^T A
+                        const double x1 = A[pp][k2], x2 = A[qq][k2];
+                        A[pp][k2] = cs * x1 - sn * x2;
+                        A[qq][k2] = sn * x1 + cs * x2;
+                    }
+                    for (int k2 = 0; k2 < 3; ++k2) {   // V <- V J
+                        const double x1 = V[k2][pp], x2 = V[k2][qq];
+                        V[k2][pp] = cs * x1 - sn * x2;
+                        V[k2][qq] = sn * x1 + cs * x2;
+                    }
+                }
+        }
+        for (int r = 0; r < dim; ++r) {   // B = Lambda^{-1/2} V^T
+            const double sc = 1.0 / std::sqrt(A[r][r]);
+            for (int a = 0; a < dim; ++a) m->frame[(f * dim + r) * dim + a] = sc * V[a][r];
+        }
     }
     return STDG_OK;
 }

@@ -71,7 +71,7 @@ __global__ void pair_blocks_kernel(const RefTables* __restrict__ rtp, int64_t n_
                                    const double* __restrict__ X, const double* __restrict__ Jinv,
                                    const double* __restrict__ faceX, const double* __restrict__ shift,
                                    const double* __restrict__ normal, const double* __restrict__ xc,
-                                   const double* __restrict__ hj, const double* __restrict__ rule_v, int nq_v,
+                                   const double* __restrict__ frame, const double* __restrict__ rule_v, int nq_v,
                                    const double* __restrict__ rule_f, int nq_f,
                                    double* __restrict__ D, double* __restrict__ Mdual) {
     extern __shared__ double sm[];
@@ -112,7 +112,9 @@ __global__ void pair_blocks_kernel(const RefTables* __restrict__ rtp, int64_t n_
         for (int q = 0; q < DIM; ++q) V[q][a] = faceX[(f * DIM + q) * DIM + a] - off[a];
         for (int r = 0; r < DIM; ++r) Ji[a][r] = Jinv[((int64_t)e * DIM + a) * DIM + r];
     }
-    const double hinv = 1.0 / hj[f];
+    double Bf[DIM][DIM];   // dual basis: monomials of y = B_j (x - x_j), the principal axes of R_j
+    for (int r = 0; r < DIM; ++r)
+        for (int a = 0; a < DIM; ++a) Bf[r][a] = frame[(f * DIM + r) * DIM + a];
     // |det| of the sub-simplex edge matrix (the reference rule's weights sum to 1/DIM!)
     // vertices ordered (V0..V_{DIM-1} face, V_DIM barycentre): edges V1-V0 .. V_DIM - V0
     double E[DIM][DIM];
@@ -159,10 +161,13 @@ __global__ void pair_blocks_kernel(const RefTables* __restrict__ rtp, int64_t n_
                 }
                 double xi[DIM], y[DIM];
                 for (int r = 0; r < DIM; ++r) {
-                    double s = 0.0;
-                    for (int a = 0; a < DIM; ++a) s += Ji[r][a] * (x[a] - X0[a]);
+                    double s = 0.0, t = 0.0;
+                    for (int a = 0; a < DIM; ++a) {
+                        s += Ji[r][a] * (x[a] - X0[a]);
+                        t += Bf[r][a] * (x[a] + off[a] - cen[a]);
+                    }
                     xi[r] = s;
-                    y[r] = (x[r] + off[r] - cen[r]) * hinv;
+                    y[r] = t;
                 }
                 double mono[kMaxNP], gm[kMaxNP * DIM], ps[kMaxNP];
                 eval_monomials<DIM>(rt, xi, mono, gm);
@@ -222,12 +227,12 @@ cudaError_t launch_precompute(stdg_ctx* c, const double* d_rule_v, const double*
     if (DIM == 2) {
         cudaFuncSetAttribute(pair_blocks_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pair_blocks_kernel<2><<<grid, 128, smem, c->stream>>>(c->d_rt, c->n_face, c->d_face_l, c->d_face_r, c->d_X, c->d_Jinv,
-                                                              c->d_faceX, c->d_shift, c->d_normal, c->d_xc, c->d_hj,
+                                                              c->d_faceX, c->d_shift, c->d_normal, c->d_xc, c->d_frame,
                                                               d_rule_v, nq_v, d_rule_f, nq_f, c->d_D, c->d_Mdual); note_launch(c);
     } else {
         cudaFuncSetAttribute(pair_blocks_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pair_blocks_kernel<3><<<grid, 128, smem, c->stream>>>(c->d_rt, c->n_face, c->d_face_l, c->d_face_r, c->d_X, c->d_Jinv,
-                                                              c->d_faceX, c->d_shift, c->d_normal, c->d_xc, c->d_hj,
+                                                              c->d_faceX, c->d_shift, c->d_normal, c->d_xc, c->d_frame,
                                                               d_rule_v, nq_v, d_rule_f, nq_f, c->d_D, c->d_Mdual); note_launch(c);
     }
     return cudaGetLastError();
@@ -288,36 +293,109 @@ cudaError_t launch_orthonormalize(stdg_ctx* c) {
     return e;
 }
 
-// Stress DOF conversion per face and component: dir 0: out = L^T in (monomial -> orthonormal),
-// dir 1: out = L^{-T} in (orthonormal -> monomial).
-__global__ void sig_convert_kernel(int64_t n_face, int NS, int NP, const double* __restrict__ L, const double* __restrict__ in,
-                                   double* __restrict__ out, int dir) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_face * NS) return;
-    const int64_t f = i / NS;
-    const double* Lf = L + f * NP * NP;
-    const double* a = in + i * NP;
-    double* b = out + i * NP;
-    if (dir == 0) {
-        for (int m = 0; m < NP; ++m) {
-            double s = 0;
-            for (int k = m; k < NP; ++k) s += Lf[k * NP + m] * a[k];
-            b[m] = s;
+// Stress DOF conversion at the API boundary.  The caller's dual basis is the Taylor
+// monomials psi_a = ((x - x_j)/h_j)^a; the library's internal one is psi'_b = (B_j (x - x_j))^b,
+// the monomials in the principal-axis coordinates of R_j (same space P_p(R_j), well conditioned
+// on thin dual cells), orthonormalised by L_j (dual mass matrix in psi', M'_j = L_j L_j^T).
+// With y = G y' (G = B_j^{-1} / h_j), psi_a = sum_b E(G)[b][a] psi'_b, E(G)[b][a] the coefficient
+// of y'^b in (G y')^a; the reverse substitution gives E(G^{-1}) = E(G)^{-1}.
+//   dir 0 (Taylor -> orthonormal): sigma~ = L^T E(G) sigma_T
+//   dir 1 (orthonormal -> Taylor): sigma_T = E(G^{-1}) L^{-T} sigma~
+template <int DIM>
+__device__ void substitution_matrix(const RefTables& rt, const double (&G)[DIM][DIM], double* E) {
+    const int NP = rt.Npsi;
+    for (int a = 0; a < NP; ++a) {
+        double poly[kMaxNP], nw[kMaxNP];
+        for (int b = 0; b < NP; ++b) poly[b] = 0.0;
+        poly[0] = 1.0;                       // exps[0] is the constant monomial
+        for (int r = 0; r < DIM; ++r)
+            for (int t = 0; t < rt.exps[a][r]; ++t) {   // multiply by the linear form y_r = sum_s G[r][s] y'_s
+                for (int b = 0; b < NP; ++b) nw[b] = 0.0;
+                for (int b = 0; b < NP; ++b) {
+                    if (poly[b] == 0.0) continue;
+                    for (int s2 = 0; s2 < DIM; ++s2) {
+                        const int k = rt.succ[b][s2];
+                        if (k >= 0) nw[k] += G[r][s2] * poly[b];
+                    }
+                }
+                for (int b = 0; b < NP; ++b) poly[b] = nw[b];
+            }
+        for (int b = 0; b < NP; ++b) E[b * NP + a] = poly[b];
+    }
+}
+
+template <int DIM>
+__global__ void sig_convert_kernel(int64_t n_face, const RefTables* __restrict__ rtp, const double* __restrict__ frame,
+                                   const double* __restrict__ hj, const double* __restrict__ L,
+                                   const double* __restrict__ in, double* __restrict__ out, int dir) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= n_face) return;
+    const RefTables& rt = *rtp;
+    const int NP = rt.Npsi, NS = rt.s;
+    double B[DIM][DIM], G[DIM][DIM];
+    for (int r = 0; r < DIM; ++r)
+        for (int a = 0; a < DIM; ++a) B[r][a] = frame[(f * DIM + r) * DIM + a];
+    const double h = hj[f];
+    if (dir == 0) {   // G = B^{-1} / h by cofactors
+        if (DIM == 2) {
+            const double det = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+            G[0][0] = B[1][1] / (det * h); G[0][1] = -B[0][1] / (det * h);
+            G[1][0] = -B[1][0] / (det * h); G[1][1] = B[0][0] / (det * h);
+        } else {
+            double cof[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int a = 0; a < 3; ++a) {
+                    const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+                    cof[r][a] = B[r1][a1] * B[r2][a2] - B[r1][a2] * B[r2][a1];
+                }
+            const double det = B[0][0] * cof[0][0] + B[0][1] * cof[0][1] + B[0][2] * cof[0][2];
+            for (int r = 0; r < 3; ++r)
+                for (int a = 0; a < 3; ++a) G[r][a] = cof[a][r] / (det * h);
         }
     } else {
-        double z[kMaxNP];
-        for (int m = NP - 1; m >= 0; --m) {
-            double s = a[m];
-            for (int k = m + 1; k < NP; ++k) s -= Lf[k * NP + m] * z[k];
-            z[m] = s / Lf[m * NP + m];
+        for (int r = 0; r < DIM; ++r)
+            for (int a = 0; a < DIM; ++a) G[r][a] = h * B[r][a];
+    }
+    double E[kMaxNP * kMaxNP];
+    substitution_matrix<DIM>(rt, G, E);
+    const double* Lf = L + f * NP * NP;
+    for (int c2 = 0; c2 < NS; ++c2) {
+        const double* a = in + (f * NS + c2) * NP;
+        double* b = out + (f * NS + c2) * NP;
+        double t[kMaxNP];
+        if (dir == 0) {
+            for (int m = 0; m < NP; ++m) {
+                double s = 0;
+                for (int k = 0; k < NP; ++k) s += E[m * NP + k] * a[k];
+                t[m] = s;
+            }
+            for (int m = 0; m < NP; ++m) {
+                double s = 0;
+                for (int k = m; k < NP; ++k) s += Lf[k * NP + m] * t[k];
+                b[m] = s;
+            }
+        } else {
+            for (int m = NP - 1; m >= 0; --m) {
+                double s = a[m];
+                for (int k = m + 1; k < NP; ++k) s -= Lf[k * NP + m] * t[k];
+                t[m] = s / Lf[m * NP + m];
+            }
+            for (int m = 0; m < NP; ++m) {
+                double s = 0;
+                for (int k = 0; k < NP; ++k) s += E[m * NP + k] * t[k];
+                b[m] = s;
+            }
         }
-        for (int m = 0; m < NP; ++m) b[m] = z[m];
     }
 }
 
 cudaError_t launch_sig_convert(stdg_ctx* c, const double* in, double* out, int dir) {
-    const int64_t n = c->n_face * c->s;
-    sig_convert_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(c->n_face, c->s, c->Nphi, c->d_L, in, out, dir); note_launch(c);
+    const unsigned g = (unsigned)((c->n_face + 127) / 128);
+    if (c->dim == 2)
+        sig_convert_kernel<2><<<g, 128, 0, c->stream>>>(c->n_face, c->d_rt, c->d_frame, c->d_hj, c->d_L, in, out, dir);
+    else
+        sig_convert_kernel<3><<<g, 128, 0, c->stream>>>(c->n_face, c->d_rt, c->d_frame, c->d_hj, c->d_L, in, out, dir);
+    note_launch(c);
     return cudaGetLastError();
 }
 
@@ -975,7 +1053,7 @@ template <int DIM>
 __global__ void project_sig_kernel(int64_t n_face, const RefTables* __restrict__ rtp, const int32_t* __restrict__ fl,
                                    const int32_t* __restrict__ fr, const double* __restrict__ X,
                                    const double* __restrict__ faceX, const double* __restrict__ shift,
-                                   const double* __restrict__ xc, const double* __restrict__ hj,
+                                   const double* __restrict__ xc, const double* __restrict__ frame,
                                    const double* __restrict__ Lc, PlaneWave pw, const double* __restrict__ rule, int nq,
                                    double* __restrict__ sigtr) {
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1011,7 +1089,11 @@ __global__ void project_sig_kernel(int64_t n_face, const RefTables* __restrict__
             for (int a = 0; a < DIM; ++a) {
                 x[a] = V[0][a];
                 for (int r = 0; r < DIM; ++r) x[a] += rp[r] * E[r][a];
-                y[a] = (x[a] + off[a] - xc[f * DIM + a]) / hj[f];
+            }
+            for (int r = 0; r < DIM; ++r) {   // principal-axis coordinates of R_j (the internal dual basis)
+                double t = 0.0;
+                for (int a = 0; a < DIM; ++a) t += frame[(f * DIM + r) * DIM + a] * (x[a] + off[a] - xc[f * DIM + a]);
+                y[r] = t;
             }
             double ps[kMaxNP];
             eval_monomials<DIM>(rt, y, ps, nullptr);
@@ -1074,11 +1156,11 @@ cudaError_t launch_project_plane_wave(stdg_ctx* c, int shot, int kind, const dou
     if (d == 2) {
         project_vel_kernel<2><<<ge, 128, 0, c->stream>>>(c->n_elem, c->d_rt, c->d_X, c->d_detJ, pw, d_rule, nq, vtr); note_launch(c);
         project_sig_kernel<2><<<gf, 128, 0, c->stream>>>(c->n_face, c->d_rt, c->d_face_l, c->d_face_r, c->d_X, c->d_faceX,
-                                                         c->d_shift, c->d_xc, c->d_hj, c->d_L, pw, d_rule, nq, sig); note_launch(c);
+                                                         c->d_shift, c->d_xc, c->d_frame, c->d_L, pw, d_rule, nq, sig); note_launch(c);
     } else {
         project_vel_kernel<3><<<ge, 128, 0, c->stream>>>(c->n_elem, c->d_rt, c->d_X, c->d_detJ, pw, d_rule, nq, vtr); note_launch(c);
         project_sig_kernel<3><<<gf, 128, 0, c->stream>>>(c->n_face, c->d_rt, c->d_face_l, c->d_face_r, c->d_X, c->d_faceX,
-                                                         c->d_shift, c->d_xc, c->d_hj, c->d_L, pw, d_rule, nq, sig); note_launch(c);
+                                                         c->d_shift, c->d_xc, c->d_frame, c->d_L, pw, d_rule, nq, sig); note_launch(c);
     }
     return cudaGetLastError();
 }

@@ -25,6 +25,7 @@
 // made the inner GMRES stagnate after 16 slabs; FP32 blocks converge there.)
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 
 #include "stdg_internal.h"
@@ -276,6 +277,10 @@ template <typename R, typename S>
 static cudaError_t pre2_local_t(stdg_ctx* c, const S* Sinv, int64_t es, const R* r, const int* ridx, int64_t ld,
                                 const R* w, R* z, int nshots) {
     const int N = c->dim * c->Nphi * c->Ng;
+    if constexpr (std::is_same<R, float>::value) {   // a batch of shots: one GEMM per element pair on the tensor cores
+        cudaError_t e;
+        if (nshots > 1 && launch_pre2_local_mma(c, r, ridx, ld, w, z, nshots, &e)) return e;
+    }
     const int wpb = 4;
     const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
     if (nshots == 1) {
@@ -296,6 +301,12 @@ cudaError_t launch_pre2_local(stdg_ctx* c, int fp32, const void* r, const void* 
         return pre2_local_t<float, float>(c, c->d_pre2_32, pre2_stride32(c), (const float*)r, nullptr, 0,
                                            (const float*)w, (float*)z, 1);
     return pre2_local_t<double, double>(c, c->d_pre2, N * N, (const double*)r, nullptr, 0, (const double*)w, (double*)z, 1);
+}
+
+// the element-local step alone for all the context's shots, FP32 (the tensor-core kernel
+// for a batch of shots where it applies)
+cudaError_t launch_pre2_local_batch(stdg_ctx* c, const float* r, const float* w, float* z) {
+    return pre2_local_t<float, float>(c, c->d_pre2_32, pre2_stride32(c), r, nullptr, 0, w, z, c->n_shots);
 }
 
 // z = P_2 r for nshots stacked shots: y = P_1 r, w = A y, z = S^{-1} (2 r - w).

@@ -19,6 +19,7 @@ constexpr int kMaxNG = 4;    // N_gamma <= 4
 struct RefTables {
     int dim, p, pg, Nphi, Npsi, Ng, s;
     int exps[kMaxNP][3];          // monomial exponents, graded-lex (dual basis and Vandermonde)
+    int succ[kMaxNP][3];          // index of exps[b] + unit exponent s (-1 beyond degree p)
     double coef[kMaxNP * kMaxNP]; // phi_k(xi) = sum_a coef[a*Nphi + k] xi^a
     double Mref[kMaxNP * kMaxNP]; // int_{ref simplex} phi_k phi_m
     double MrefInv[kMaxNP * kMaxNP];
@@ -59,6 +60,7 @@ struct HostMesh {
     std::vector<double> shift;    // r-frame -> l-frame translation [f][dim]
     std::vector<double> normal;   // unit, from l to r [f][dim]
     std::vector<double> xc, hj;   // dual-cell centre (l frame) and scale
+    std::vector<double> frame;    // [f][dim][dim] B_j: principal-axis coordinates y' = B_j (x - x_j) of R_j
     std::vector<double> period;   // dim entries (0 = not periodic), empty if none
 };
 
@@ -96,6 +98,7 @@ struct stdg_ctx {
     int32_t *d_face_l = nullptr, *d_face_r = nullptr;
     double *d_X = nullptr, *d_Jinv = nullptr, *d_detJ = nullptr;
     double *d_faceX = nullptr, *d_shift = nullptr, *d_normal = nullptr, *d_xc = nullptr, *d_hj = nullptr;
+    double* d_frame = nullptr;  // principal-axis frames B_j of the dual cells [face][dim][dim]
     double *d_D = nullptr;      // orthonormalised blocks D~_{i,j} [face][side][l][n][m] (FP64)
     double *d_L = nullptr;      // Cholesky factors of the dual mass matrices (lower, [face][m][m'])
     double *d_Mdual = nullptr;  // dual mass matrices (set-up workspace)
@@ -132,6 +135,7 @@ struct stdg_ctx {
     // ---- stencil preconditioner (precond2.cu): S_i^{-1} per element, column-major
     double* d_pre2 = nullptr;
     float* d_pre2_32 = nullptr;                // FP32 copy for the FP32 solver, pre2_stride32 apart
+    float* d_pre2_mma = nullptr;               // TF32-rounded tensor-core operand image (multi-shot, pre2_mma.cu)
     void *d_p2y = nullptr, *d_p2t = nullptr;   // P_1 r and A P_1 r, stacked over shots (FP64-sized)
     int* d_p2status = nullptr;
 
@@ -220,6 +224,13 @@ cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status);
 cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
 cudaError_t launch_pre2_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots = 1);
 cudaError_t launch_pre2_local(stdg_ctx* c, int fp32, const void* r, const void* w, void* z);
+cudaError_t launch_pre2_local_batch(stdg_ctx* c, const float* r, const float* w, float* z);
+// pre2_mma.cu: the element-local step for a batch of shots on the tensor cores (tcgen05)
+bool pre2_mma_supported(const stdg_ctx* c);
+int64_t pre2_mma_image_floats(const stdg_ctx* c);
+cudaError_t launch_pre2_mma_image(stdg_ctx* c);
+bool launch_pre2_local_mma(stdg_ctx* c, const float* r, const int* ridx, int64_t ld, const float* w, float* z,
+                           int nshots, cudaError_t* e);
 // (re)build the dt-dependent preconditioner blocks when dt changes (capi.cu)
 int precond_for_dt(stdg_ctx* c, double dt);
 

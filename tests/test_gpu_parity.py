@@ -468,3 +468,48 @@ def test_crank_nicolson_stacked_shots_match_oracle(precision, tol, rel_tol):
     w = synth.scaled("c4", ny=8, steps=3, n_shots=5)
     w = dataclasses.replace(w, p=1, p_gamma=0, scheme="cn", name="c4_cn_p1_5shots")
     _check_stacked_against_oracle(w, 3, precision, tol, rel_tol, 1)
+
+
+@pytest.mark.parametrize("n_shots", [9, 64])
+def test_tensor_core_stencil_preconditioner_matches_oracle_per_shot(n_shots):
+    # mixed precision with a batch of shots, d N_phi N_gamma = 36: the element-local step of
+    # Pre2 runs on the tensor cores (kind::tf32, S^{-1} rounded to TF32, the vector split into
+    # two TF32 terms, FP32 accumulation); every shot against the oracle's literal Pre2 (FP64).
+    # The bar is set by the TF32 rounding of S^{-1} (2^-11 per entry); a layout mistake in the
+    # operand tiles or the accumulator gives errors of order one.
+    torch = need_gpu()
+    from oracle.precond import pre2
+    w = synth.scaled("c4", ny=8, steps=1, n_shots=n_shots)
+    sim = oracle_sim(w)
+    n = sim.A.shape[0]
+    R = np.random.default_rng(13).normal(size=(n_shots, n))
+    P = pre2(sim.A, w.n_elem, sim.mesh.elem_nbr)
+    ref = np.array([P @ R[k] for k in range(n_shots)])
+    out = {}
+    for precision, fp32 in (("mixed", True), ("fp64", False)):
+        s = gpu_solver(w, precision=precision, with_receivers=False, preconditioner=2)
+        dt = torch.float32 if fp32 else torch.float64
+        rd = torch.tensor(R.ravel(), dtype=dt, device="cuda")
+        zd = torch.zeros_like(rd)
+        torch.cuda.synchronize()
+        s.apply_preconditioner_device(w.dt, rd.data_ptr(), zd.data_ptr(), fp32=fp32)
+        Z = zd.cpu().numpy().astype(np.float64).reshape(n_shots, n)
+        out[precision] = max(rel_l2(Z[k], ref[k]) for k in range(n_shots))
+    print("batched Pre2, %d shots: tensor-core FP32 %.3g, FP64 %.3g" % (n_shots, out["mixed"], out["fp64"]))
+    assert out["fp64"] < max(1e-9, 1e4 * oracle_rounding_spread(sim, w))
+    assert out["mixed"] < 2e-3
+
+
+def test_tensor_core_stencil_preconditioner_keeps_iteration_counts():
+    # the TF32 local step must not degrade the preconditioner: the stacked mixed-precision
+    # solve takes about as many iterations as the FP64 one (FP64 blocks, CUDA cores)
+    need_gpu()
+    w = synth.scaled("c4", ny=10, steps=3, n_shots=12)
+    its = {}
+    for precision in ("fp64", "mixed"):
+        s = gpu_solver(w, precision=precision, rel_tol=1e-10, max_iters=20000, preconditioner=2)
+        st = s.step(w.dt, 3)
+        assert st["status"] == 0
+        its[precision] = st["iters_max"]
+    print("stacked Pre2 iterations per slab (max): FP64 %d, mixed (tensor-core local step) %d" % (its["fp64"], its["mixed"]))
+    assert its["mixed"] <= 1.25 * its["fp64"] + 5
