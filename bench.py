@@ -32,8 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_PEAK_TFLOPS = 1.25          # nominal dense FP64 of one GB300 (no measured figure in the peaks file)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_NOMINAL_TFLOPS = 1.25       # nominal dense FP64 of one GB300: only if the probe below fails
 
 
 METRIC = "space-time DOF-steps/s (velocity+stress) at 1e-8 rel residual, mixed FP32/FP64"
@@ -201,7 +200,17 @@ def _traffic(w, key, units):
     return None
 
 
-def face_kernel_roofline(s, w, fp32, n_face, pk):
+def fp64_peak():
+    """The FP64 FMA rate this GPU sustains, from the library's own probe kernel
+    (stdg_measure_fma_peak: 8 independent FMA chains per thread on every SM)."""
+    from paper_1802_04516_gb300.binding import measure_fma_peak
+    try:
+        return measure_fma_peak(fp64=True), "measured FP64 FMA rate (stdg_measure_fma_peak)"
+    except Exception:
+        return FP64_NOMINAL_TFLOPS, "nominal FP64 1.25 TFLOP/s"
+
+
+def face_kernel_roofline(s, w, fp32, n_face, pk, fp64_pk=None):
     """Algorithmic bytes / FLOPs of one launch of the operator's face kernel, its measured
     average duration (CUDA events on the library stream) and the fraction of peak."""
     from math import comb
@@ -226,10 +235,11 @@ def face_kernel_roofline(s, w, fp32, n_face, pk):
                 "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
                 "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
     achieved = flops / (ms * 1e-3) / 1e12
+    peak, src = fp64_pk if fp64_pk else (FP64_NOMINAL_TFLOPS, "nominal FP64 1.25 TFLOP/s")
     return {"kernel": "face_apply_kernel<double>", "bound": "alu", "achieved": round(achieved, 4),
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+            "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
             "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
-            "peak_source": "nominal FP64 1.25 TFLOP/s"}
+            "peak_source": src}
 
 
 def multishot_section(torch, args, stream, dist, world):
@@ -242,6 +252,7 @@ def multishot_section(torch, args, stream, dist, world):
                      use_graph=not args.host_loop, pre=args.pre)
     n_face = s.n_face
     ms, iters, launches, st = time_steps(torch, s, w, args.ms_steps, 1, stream, dist)
+    local = pre2_local_batch_roofline(s, w, peaks()) if args.pre == 2 else None
     s.close()
     dofs_shot = dofs_per_slab(w, n_face)
     w1 = synth.c4_multishot(ny=args.ny, n_shots=1, steps=args.ms_steps)
@@ -258,7 +269,8 @@ def multishot_section(torch, args, stream, dist, world):
                                 "final_rel_res": st["final_rel_res"], "gpu_launches": launches},
             "fp64_single_shot": {"shot_steps_per_s": single, "dof_steps_per_s": single * dofs_shot,
                                  "ms_per_step": ms1 / args.ms_steps, "krylov_iters_per_step": it1},
-            "speedup_shot_steps": multi / single, "dofs_per_slab_per_shot": dofs_shot, "steps": args.ms_steps}
+            "speedup_shot_steps": multi / single, "dofs_per_slab_per_shot": dofs_shot, "steps": args.ms_steps,
+            "pre2_local_batch_roofline": local}
 
 
 def ragged_section(torch, args, stream, dist, world):
@@ -328,6 +340,54 @@ def pre2_local_roofline(s, w, pk):
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(w, "pre2_local_fp32", w.n_elem),
             "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(2 * w.n_elem * N * N),
             "ms_per_launch": round(ms, 4), "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
+
+
+def pre2_local_batch_roofline(s, w, pk):
+    """Element-local step of the stencil preconditioner for all shots of a stacked solve (FP32;
+    with d N_phi N_gamma = 36 the tensor-core kernel, kind::tf32): one (d N_phi N_gamma)^2 block
+    per element read once for all shots, r and w read and z written for every shot."""
+    from math import comb
+    nphi = comb(w.p + w.dim, w.dim)
+    N = w.dim * nphi * (w.p_gamma + 1)
+    ns = w.n_shots
+    nvel = w.n_elem * N
+    bytes_alg = w.n_elem * N * N * 4 + 3 * ns * nvel * 4
+    flops = 2 * w.n_elem * N * N * ns
+    ms = s.time_kernel(w.dt, 4, fp32=True, n=10)
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    achieved = bytes_alg / (ms * 1e-3) / 1e9
+    return {"kernel": "pre2_local_mma_kernel<36> (tcgen05.mma kind::tf32, TMEM accumulator)" if N == 36
+            else "pre2_local_kernel<float,float,4>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "shots": ns,
+            "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops),
+            "tensor_tflops_useful": round(flops / (ms * 1e-3) / 1e12, 2), "ms_per_launch": round(ms, 4),
+            "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
+
+
+def full_run(torch, w, args, stream):
+    """The whole 200-slab configuration once, untimed per slab, from rest: Krylov iterations of
+    every slab (the timed window covers a few slabs early in the run, before the Ricker pulse
+    has spread) and the whole run's DOF-steps/s from CUDA events around it."""
+    s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
+                     use_graph=not args.host_loop, pre=args.pre)
+    dofs = dofs_per_slab(w, s.n_face)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    its = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.full_slabs):
+        its.append(s.step(w.dt, 1)["iters_max"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    a = np.array(its, dtype=float)
+    return {"slabs": args.full_slabs, "ms": ms, "dof_steps_per_s": dofs * args.full_slabs / (ms * 1e-3),
+            "krylov_iters_per_slab": {"min": int(a.min()), "median": float(np.median(a)), "max": int(a.max()),
+                                      "mean": float(a.mean())},
+            "krylov_iters_by_decile": [float(x.mean()) for x in np.array_split(a, 10)],
+            "note": "first-slab graph capture included; per-slab host call (stdg_step with one slab)"}
 
 
 def dominant_roofline(cands, per_iter):
@@ -401,8 +461,9 @@ def main():
     ap.add_argument("--no-multishot", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--adj-steps", type=int, default=60,
-                    help="slabs of the misfit-gradient run (the workload has 300; 60 keeps the bench short)")
+    ap.add_argument("--adj-steps", type=int, default=300, help="slabs of the misfit-gradient run (the workload's 300)")
+    ap.add_argument("--full-slabs", type=int, default=200,
+                    help="slabs of the untimed-per-slab full run of the benchmark configuration (0: skip)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solver loops from the host instead of CUDA-graph while nodes (for kernel profilers)")
     args = ap.parse_args()
@@ -447,13 +508,16 @@ def main():
         e2e_ms, h2d, d2h = e2e_steps(torch, s, w, max(1, args.steps // 2), stream)
         e2e_ms = max_over_ranks(torch, dist, e2e_ms)
         e2e_value = dofs * max(1, args.steps // 2) / (e2e_ms * 1e-3) * world
+        full = full_run(torch, synth.c2_layered_slivers(ny=args.ny, steps=args.full_slabs), args, stream) \
+            if args.full_slabs > 0 else None
         fp64 = None
+        fp64_pk = fp64_peak()
         if not args.no_fp64 and args.fp64_steps > 0:
             s64 = build_solver(w, "fp64", stream.cuda_stream, shot_offset=rank_shot_offset(rank), restart=args.restart,
                                use_graph=not args.host_loop, pre=args.pre)
             ms64, it64, _, _ = time_steps(torch, s64, w, args.fp64_steps, 1, stream, dist)
             fp64 = {"value": world * dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
-                    "krylov_iters_per_step": it64, "roofline": face_kernel_roofline(s64, w, False, n_face, pk)}
+                    "krylov_iters_per_step": it64, "roofline": face_kernel_roofline(s64, w, False, n_face, pk, fp64_pk)}
             s64.close()
         s.close()
         multishot = None if args.no_multishot else multishot_section(torch, args, stream, dist, world)
@@ -481,6 +545,7 @@ def main():
         "roofline": roof,
         "kernels": cands,
         "e2e": {"value": e2e_value, "unit": "DOF-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "full_run": full,
         "fp64": fp64,
         "multishot": multishot,
         "ragged": ragged,

@@ -260,12 +260,17 @@ int stdg_residual_noalloc(stdg_ctx* ctx, double dt, const double* x_dev, const d
  * system on time-reversed vectors (A^T = J A J for the reversal J of the Gauss-Legendre
  * time nodes), with the context's solver, precision and preconditioner; states are
  * checkpointed every checkpoint_every slabs (<= 0: 20) and each segment is recomputed
- * once in the backward sweep.  Space-time DG only (STDG_EINVAL for Crank-Nicolson); needs
+ * once in the backward sweep.  g_src (may be NULL): the gradient with respect to the point
+ * sources of Sec. 6.3, n_shots x per_shot x (1 + 2 dim) values, for every source q (in the
+ * order of stdg_set_point_sources): dL/d(amplitude of source q), dL/d(force direction, dim
+ * values), dL/d(position, dim values; the source's element held fixed) -- the source enters the
+ * right-hand side only, so these are lam^T ds/dtheta summed over the slabs (zeros when the
+ * context has no point sources).  Space-time DG only (STDG_EINVAL for Crank-Nicolson); needs
  * receivers.  The context ends at the final time with the final states, as after
  * stdg_step; stats (may be NULL) sums the Krylov work of all forward and adjoint solves.
  * The paper has no adjoint: this is the gradient of the library's own discrete map. */
 int stdg_misfit_grad(stdg_ctx* ctx, double dt, int n_steps, const double* data, int checkpoint_every,
-                     double* loss, double* g_lambda, double* g_mu, double* g_rho, stdg_stats* stats);
+                     double* loss, double* g_lambda, double* g_mu, double* g_rho, double* g_src, stdg_stats* stats);
 
 /* Average device time of `n` launches of the operator's face kernel (fp32 != 0: the
  * FP32 one) on the context stream, measured with CUDA events: *ms_out. */
@@ -281,6 +286,13 @@ int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out
  * the kernels run on zero vectors in buffers allocated for the call.  No counterpart in
  * the paper. */
 int stdg_time_kernel(stdg_ctx* ctx, double dt, int which, int fp32, int n, double* ms_out);
+
+/* Arithmetic peak of this GPU (no counterpart in the paper): the FP64 (fp64 != 0) or FP32 FMA
+ * rate in TFLOP/s (2 flops per FMA) that the library's own probe kernel sustains -- 8 independent
+ * FMA chains per thread, 8 blocks of 256 threads per SM, timed with CUDA events on a private
+ * stream -- the denominator of the ALU-bound rooflines.  Needs no context; allocates and frees
+ * its own output buffer.  Returns STDG_OK, STDG_EINVAL (null out), STDG_ENOMEM or STDG_ECUDA. */
+int stdg_measure_fma_peak(int fp64, double* tflops);
 
 /* Failure-path testing (no counterpart in the paper): sets the context's device error word
  * exactly as a face kernel whose bounded wait for a bulk copy gave up would.  The next call

@@ -1,4 +1,5 @@
-"""Receiver misfit and its exact gradient with respect to per-element lambda, mu, rho.
+"""Receiver misfit and its exact gradient with respect to per-element lambda, mu, rho and the
+point sources (amplitude, force direction, position of each shot's source).
 
 TEST INFRASTRUCTURE ONLY (see the package header).
 
@@ -15,6 +16,8 @@ Backward recursion (a_v, a_s = dL/dv^n, dL/dsigma^n through all later slabs):
   a_x = Gam^T a_v^{n+1} + Cx^T a_s^{n+1};   A^T lam = a_x  (the same LU, trans='T')
   a_v^n = Bv^T lam + R^T (R v^n - d^n),     a_s^n = Bs^T lam + Cs^T a_s^{n+1}
   dL/dtheta += lam^T dBv/dtheta v^n - lam^T dA/dtheta x^{n+1} + a_s^{n+1 T} dCx/dtheta x^{n+1}.
+The point source enters the right-hand side only (Sec. 6.3): dL/dtheta_src += lam^T ds^n/dtheta_src,
+s^n linear in the amplitude and the force direction, polynomial in the position through phi(x_s).
 rho enters A and Bv through the element mass; lambda and mu enter A and Cx through E_j,
 which is linear in the dual-cell values (lambda_j, mu_j) = sub-cell-weighted means of the
 two elements' values (the dual-material reading).  Every transpose below is written out
@@ -23,8 +26,9 @@ finite differences with direct solves (tests/test_oracle_adjoint.py).
 """
 import numpy as np
 
+from .basis import gauss_legendre01
 from .operators import SYM, stiffness_tensor
-from .stepper import Simulation
+from .stepper import Simulation, ricker
 
 
 # ---- transposes of the stepper's pieces (each checked by a dot-product test) -------------
@@ -187,8 +191,35 @@ def misfit(geom, lam, mu, rho, n_steps, sources, f0, td, a1, receivers, data):
     return L
 
 
-def misfit_gradient(geom, lam, mu, rho, n_steps, sources, f0, td, a1, receivers, data):
-    """(L, dL/dlambda, dL/dmu, dL/drho) per element, summed over the shots."""
+def source_derivatives(sim, t0):
+    """Derivatives of the slab's point-source vector (Sec. 6.3: (rho S)_i = d phi(x_s) dt int gamma S)
+    for the slab [t0, t0 + dt], each shaped like the vector (ne, d, Ng*Nphi): with respect to
+    the amplitude a1 (the vector at unit amplitude), the force direction d_l and the position
+    x_s,m (the element containing x_s held fixed)."""
+    dz, s = sim.disc, sim.sources
+    xq, wq = gauss_legendre01(8)
+    g = dz.tb.values(xq)
+    unit = sim.dt * np.einsum("q,qa,q->a", wq, g, ricker(t0 + xq * sim.dt, s["f0"], s["t_delay"], 1.0))
+    _, grad = dz.phi(np.array([s["elem"]]), s["x_local"][None, None, :])
+    dphi = grad[0, 0]                                                   # (Nphi, d)
+    shape = (sim.mesh.n_elem, dz.dim, dz.Ng, dz.Nphi)
+    d_a1 = np.zeros(shape)
+    d_a1[s["elem"]] = np.einsum("k,a,n->kan", s["dir"], unit, s["phi"])
+    d_dir, d_xs = [], []
+    for l in range(dz.dim):
+        u = np.zeros(shape)
+        u[s["elem"], l] = s["a1"] * np.einsum("a,n->an", unit, s["phi"])
+        d_dir.append(u.reshape(shape[0], dz.dim, -1))
+        u = np.zeros(shape)
+        u[s["elem"]] = s["a1"] * np.einsum("k,a,n->kan", s["dir"], unit, dphi[:, l])
+        d_xs.append(u.reshape(shape[0], dz.dim, -1))
+    return d_a1.reshape(shape[0], dz.dim, -1), d_dir, d_xs
+
+
+def misfit_gradient(geom, lam, mu, rho, n_steps, sources, f0, td, a1, receivers, data, source_grad=False):
+    """(L, dL/dlambda, dL/dmu, dL/drho) per element, summed over the shots; with source_grad
+    also dL/d(source) per shot, (n_shots, 1 + 2 d): the shot's amplitude a1, its force
+    direction and its position, from lam^T ds^n/dtheta (the source enters b^n only)."""
     sim = make_sim(geom, lam, mu, rho)
     dz, m = sim.disc, sim.mesh
     d, ne = dz.dim, m.n_elem
@@ -199,6 +230,7 @@ def misfit_gradient(geom, lam, mu, rho, n_steps, sources, f0, td, a1, receivers,
     g_lf = np.zeros(m.n_face)
     g_mf = np.zeros(m.n_face)
     L = 0.0
+    g_src = np.zeros((len(sources), 1 + 2 * d))
     for s, src in enumerate(sources):
         rec, V, X = forward(sim, n_steps, src, f0, td, a1, receivers, keep=True)
         res = rec - data[s]
@@ -219,6 +251,12 @@ def misfit_gradient(geom, lam, mu, rho, n_steps, sources, f0, td, a1, receivers,
                 h = minv(dz, E_contract(Ek, G))
                 gk += c * np.einsum("fabz,fabz->f", DTl, h)
                 gk += np.einsum("fcm,fcm->f", a_s, trace_time(dz, dz.sym_from_full(h), dz.Npsi))
+            if source_grad:   # b^n = ... + s^n: dL/dtheta += lam^T ds^n/dtheta
+                d_a1, d_dir, d_xs = source_derivatives(sim, n * sim.dt)
+                g_src[s, 0] += np.sum(lam_ * d_a1)
+                for l in range(d):
+                    g_src[s, 1 + l] += np.sum(lam_ * d_dir[l])
+                    g_src[s, 1 + d + l] += np.sum(lam_ * d_xs[l])
             a_s = Bs_T(dz, lam_) + Cs_T(dz, a_s)
             a_v = Bv_T(dz, lam_)
             if n >= 1:
@@ -232,4 +270,6 @@ def misfit_gradient(geom, lam, mu, rho, n_steps, sources, f0, td, a1, receivers,
         ok = side >= 0
         np.add.at(g_lam, side[ok], (w / (wl + wr) * g_lf)[ok])
         np.add.at(g_mu, side[ok], (w / (wl + wr) * g_mf)[ok])
+    if source_grad:
+        return L, g_lam, g_mu, g_rho, g_src
     return L, g_lam, g_mu, g_rho

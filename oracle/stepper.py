@@ -128,7 +128,7 @@ class Simulation:
         i, y = self.mesh.locate(xs)
         phi, _ = self.disc.phi(np.array([i]), y[None, None, :])
         self.sources = dict(elem=i, phi=phi[0, 0], dir=np.asarray(direction, dtype=np.float64),
-                            f0=f0, t_delay=t_delay, a1=a1)
+                            f0=f0, t_delay=t_delay, a1=a1, x_local=y)
 
     def source_vector(self, t0):
         """(rho S)_i for the slab [t0, t0 + dt]; zero except in the source element."""

@@ -64,11 +64,12 @@ SIGNATURES = {
     "stdg_reference_tables": (C.c_int, [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D]),
     "stdg_time_operator": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, _D]),
     "stdg_time_kernel": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
-    "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
+    "stdg_misfit_grad": (C.c_int, [_P, C.c_double, C.c_int, _D, C.c_int, _D, _D, _D, _D, _D, C.POINTER(stdg_stats)]),
     "stdg_apply_preconditioner": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_residual_noalloc": (C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
     "stdg_inject_wait_error": (C.c_int, [_P]),
     "stdg_apply_preconditioner_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
+    "stdg_measure_fma_peak": (C.c_int, [C.c_int, _D]),
 }
 
 _lib = None
@@ -160,6 +161,15 @@ def locate_points(xyz, elem_vert, points, period=None):
     if rc != 0:
         raise StdgError(rc, "stdg_locate_points")
     return out
+
+
+def measure_fma_peak(fp64=True):
+    """FP64 (or FP32) FMA rate of this GPU in TFLOP/s, from the library's probe kernel."""
+    v = C.c_double(0.0)
+    rc = load().stdg_measure_fma_peak(1 if fp64 else 0, C.byref(v))
+    if rc != 0:
+        raise StdgError(rc, "stdg_measure_fma_peak failed")
+    return v.value
 
 
 def reference_tables(dim, p, p_gamma):
@@ -259,6 +269,7 @@ class Solver:
         _need(xs, xs.shape[0] * self.dim, "xs")
         _need(dr, xs.shape[0] * self.dim, "direction")
         self._chk(self.lib.stdg_set_sources(self.h, xs.shape[0], _d(xs), _d(dr), f0, t_delay, a1))
+        self.src_per_shot = 1
 
     def set_point_sources(self, xs, direction, f0, t_delay, a1, n_shots=1):
         """Several point sources per shot: xs, direction of shape (n_shots * per_shot, dim)."""
@@ -269,6 +280,7 @@ class Solver:
         _need(dr, xs.shape[0] * self.dim, "direction")
         per = xs.shape[0] // n_shots
         self._chk(self.lib.stdg_set_point_sources(self.h, n_shots, per, _d(xs), _d(dr), f0, t_delay, a1))
+        self.src_per_shot = per
 
     def set_receivers(self, xr):
         xr = _f64(np.atleast_2d(xr))
@@ -332,19 +344,25 @@ class Solver:
         self._chk(self.lib.stdg_get_faces(self.h, fl.ctypes.data_as(_I32), fr.ctypes.data_as(_I32)))
         return fl, fr
 
-    def misfit_grad(self, dt, n_steps, data, checkpoint_every=20, grad=True):
+    def misfit_grad(self, dt, n_steps, data, checkpoint_every=20, grad=True, source_grad=False):
         """(loss, g_lambda, g_mu, g_rho, stats) of n_steps slabs from the current states;
-        data: (n_shots, n_steps, n_rec, dim).  grad=False: the loss only (forward run)."""
+        data: (n_shots, n_steps, n_rec, dim).  grad=False: the loss only (forward run).
+        source_grad=True: (loss, g_lambda, g_mu, g_rho, g_src, stats) with g_src of shape
+        (n_sources, 1 + 2 dim): d/d amplitude, d/d force direction, d/d position per source."""
         data = _need(_f64(data), self.n_shots * n_steps * getattr(self, "n_rec", 0) * self.dim, "data")
         loss = C.c_double(0.0)
         g = [np.zeros(self.n_elem) for _ in range(3)] if grad else [None, None, None]
+        n_src = self.n_shots * getattr(self, "src_per_shot", 1)
+        gs = np.zeros((n_src, 1 + 2 * self.dim)) if source_grad else None
         st = stdg_stats()
 
         def ptr(a):
             return _d(a) if a is not None else None
 
         self._chk(self.lib.stdg_misfit_grad(self.h, dt, n_steps, _d(data), checkpoint_every, C.byref(loss),
-                                            ptr(g[0]), ptr(g[1]), ptr(g[2]), C.byref(st)))
+                                            ptr(g[0]), ptr(g[1]), ptr(g[2]), ptr(gs), C.byref(st)))
+        if source_grad:
+            return loss.value, g[0], g[1], g[2], gs, st.as_dict()
         return loss.value, g[0], g[1], g[2], st.as_dict()
 
     def time_kernel(self, dt, which, fp32=False, n=20):
@@ -383,29 +401,50 @@ def solver_from_workload(w, precision="fp64", rel_tol=1e-8, max_iters=5000, gmre
     return s
 
 
-def misfit(solver, lam, mu, rho, dt, n_steps, data, reset, checkpoint_every=20):
-    """Receiver misfit as a differentiable torch function of the per-element lambda, mu, rho.
+def misfit(solver, lam, mu, rho, dt, n_steps, data, reset=None, checkpoint_every=20, sources=None):
+    """Receiver misfit as a differentiable torch function of the per-element lambda, mu, rho and,
+    optionally, of the point sources.
 
-    Sets the material from the three tensors, calls ``reset()`` to put the initial states
-    back (for instance ``lambda: solver.set_sources(...)``), then runs stdg_misfit_grad:
-    the forward value is the misfit of ``n_steps`` slabs against ``data`` (n_shots, n_steps,
-    n_rec, dim); backward returns the adjoint gradients scaled by the incoming gradient.
+    Sets the material from the three tensors.  Without ``sources``, calls ``reset()`` to put the
+    initial states back (for instance ``lambda: solver.set_sources(...)``).  With ``sources`` =
+    dict(xs=tensor (n_src, dim), force=tensor (n_src, dim), f0=..., t_delay=..., n_shots=...),
+    sets the point sources from the tensors (force = amplitude times direction, Ricker wavelet of
+    unit amplitude; this also resets the states) and differentiates with respect to xs and force
+    too.  Then runs stdg_misfit_grad: the forward value is the misfit of ``n_steps`` slabs against
+    ``data`` (n_shots, n_steps, n_rec, dim); backward returns the adjoint gradients scaled by the
+    incoming gradient.
     """
     import torch
 
+    d = solver.dim
+    src = sources or {}
+
     class _Misfit(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, lam_t, mu_t, rho_t):
+        def forward(ctx, lam_t, mu_t, rho_t, xs_t, force_t):
             solver.set_material(lam_t.detach().cpu().double().numpy(), mu_t.detach().cpu().double().numpy(),
                                 rho_t.detach().cpu().double().numpy())
-            reset()
-            loss, gl, gm, gr, _ = solver.misfit_grad(dt, n_steps, data, checkpoint_every=checkpoint_every)
-            ctx.save_for_backward(*(torch.as_tensor(g, dtype=lam_t.dtype, device=lam_t.device) for g in (gl, gm, gr)))
-            return torch.tensor(loss, dtype=lam_t.dtype, device=lam_t.device)
+            if xs_t is not None:
+                solver.set_point_sources(xs_t.detach().cpu().double().numpy(), force_t.detach().cpu().double().numpy(),
+                                         src["f0"], src["t_delay"], 1.0, n_shots=src.get("n_shots", 1))
+            else:
+                reset()
+            out = solver.misfit_grad(dt, n_steps, data, checkpoint_every=checkpoint_every,
+                                     source_grad=xs_t is not None)
+            like = dict(dtype=lam_t.dtype, device=lam_t.device)
+            grads = [torch.as_tensor(g, **like) for g in out[1:4]]
+            if xs_t is not None:
+                gs = out[4]
+                grads += [torch.as_tensor(gs[:, 1 + d:], **like), torch.as_tensor(gs[:, 1:1 + d], **like)]
+            ctx.save_for_backward(*grads)
+            ctx.has_src = xs_t is not None
+            return torch.tensor(out[0], **like)
 
         @staticmethod
         def backward(ctx, g_out):
-            gl, gm, gr = ctx.saved_tensors
-            return g_out * gl, g_out * gm, g_out * gr
+            g = [g_out * t for t in ctx.saved_tensors]
+            if not ctx.has_src:
+                g += [None, None]
+            return tuple(g)
 
-    return _Misfit.apply(lam, mu, rho)
+    return _Misfit.apply(lam, mu, rho, src.get("xs"), src.get("force"))

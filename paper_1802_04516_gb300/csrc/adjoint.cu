@@ -1,5 +1,5 @@
-// Receiver misfit and its gradient with respect to per-element lambda, mu, rho by the
-// discrete adjoint of the space-time DG slab map (the paper has no adjoint; the forward
+// Receiver misfit and its gradient with respect to per-element lambda, mu, rho and the point
+// sources (amplitude, force direction, position; Sec. 6.3) by the discrete adjoint of the space-time DG slab map (the paper has no adjoint; the forward
 // map is Eq. velocity.sys followed by the stress update of Eq. NM26 and the traces).
 //
 // Forward slab n -> n+1 of one shot, as the library computes it (orthonormal dual basis):
@@ -17,6 +17,8 @@
 //   dL/dlam_j   += -c dt^2 <tr D~^T lam, S tr D~^T x> - dt sum_b u_b <diag-sum a_s, tr (D~^T x)_b>
 //   dL/dmu_j    += -c dt^2 <D~^T lam, S (G + G^T)> - dt sum_b u_b <a_s, sym(G + G^T)_b>,  G = D~^T x
 // and the dual-cell values feed the elements with the sub-cell weights |T_i| / |R_j|.
+//   dL/dtheta_src += lam . ds^n/dtheta_src,  s^n = a1 dir (x) (dt int gamma S_1) (x) phi(x_s):
+//   linear in a1 and dir, through phi(x_s) in the position (the source's element held fixed).
 //
 // The transposed solve needs no operator of its own: with the Lagrange time basis on the
 // symmetric Gauss-Legendre points, T^T = J T J and S^T = J S J for the reversal J of the
@@ -291,13 +293,35 @@ __global__ void __launch_bounds__(128) adj_rhs_kernel(int64_t n_face, int n_shot
     }
 }
 
+// Point-source term of the gradient, per slab: for every source q (shot k = q / per) and
+// component l, G[q][l][n] += sum_a lam[k][e_q][l][a][n] tint_a with tint_a = dt int gamma_a S at
+// unit amplitude for this slab (lam read time-reversed from J lam).  The source vector of the
+// slab is s = a1 dir (x) tint (x) phi(x_s), so lam^T ds/dtheta for the amplitude, the direction
+// and the position are contractions of G with phi(x_s), grad phi(x_s) and dir (on the host).
+struct TimeInt { double v[kMaxNG]; };
+__global__ void adj_source_kernel(int nsrc, int per, int dim, int NP, int NG, const int32_t* __restrict__ elem,
+                                  const double* __restrict__ lamJ, int64_t nvel, TimeInt tint, double* __restrict__ G) {
+    const int64_t total = (int64_t)nsrc * dim * NP;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i % NP), l = (int)((i / NP) % dim);
+        const int64_t q = i / ((int64_t)NP * dim);
+        const int64_t k = q / per;
+        const double* lam = lamJ + k * nvel + ((int64_t)elem[q] * dim + l) * NG * NP;
+        double acc = 0.0;
+        for (int a = 0; a < NG; ++a) acc += lam[(NG - 1 - a) * NP + n] * tint.v[a];
+        G[i] += acc;
+    }
+}
+
 }  // namespace
 
 // The misfit (and with gradients requested, the adjoint sweep) of n_steps slabs from the
 // current state of every shot.  data: [shot][step][receiver][component].
 int misfit_grad_impl(stdg_ctx* c, double dt, int N, const double* data, int K, double* loss, double* g_lam,
-                     double* g_mu, double* g_rho, stdg_stats* stats) {
-    const bool grads = g_lam || g_mu || g_rho;
+                     double* g_mu, double* g_rho, double* g_src, stdg_stats* stats) {
+    const bool grads = g_lam || g_mu || g_rho || g_src;
+    const bool src_grad = g_src && c->have_sources;
+    const int nsrc = src_grad ? (int)c->src_elem.size() : 0;
     const int ns = c->n_shots, d = c->dim, NP = c->Nphi, NG = c->Ng, NR = c->n_rec;
     const int64_t ntr = c->ntr, nsig = c->nsig, nvel = c->nvel;
     const int64_t per_rec = (int64_t)NR * d;
@@ -381,6 +405,31 @@ int misfit_grad_impl(stdg_ctx* c, double dt, int N, const double* data, int K, d
     ADJ_CUDA(cudaMemsetAsync(glf, 0, sizeof(double) * c->n_face, c->stream));
     ADJ_CUDA(cudaMemsetAsync(gmf, 0, sizeof(double) * c->n_face, c->stream));
     ADJ_CUDA(cudaMemsetAsync(grho, 0, sizeof(double) * c->n_elem, c->stream));
+    double* gsrc = nullptr;
+    int32_t* selem = nullptr;
+    std::vector<double> gl8(16);
+    gauss_legendre01(8, gl8.data(), gl8.data() + 8);
+    if (src_grad) {
+        ADJ_TRY(alloc((void**)&gsrc, sizeof(double) * nsrc * d * NP));
+        ADJ_TRY(alloc((void**)&selem, sizeof(int32_t) * nsrc));
+        std::vector<int32_t> se(c->src_elem.begin(), c->src_elem.end());
+        ADJ_CUDA(cudaMemcpyAsync(selem, se.data(), sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, c->stream));
+        ADJ_CUDA(cudaMemsetAsync(gsrc, 0, sizeof(double) * nsrc * d * NP, c->stream));
+        ADJ_CUDA(cudaStreamSynchronize(c->stream));   // the host vector se goes out of scope
+    }
+    // dt int_0^1 gamma_a(tau) S(t + tau dt) dtau at unit amplitude, 8-point Gauss-Legendre (as the forward RHS)
+    auto time_integral = [&](double tn) {
+        TimeInt ti{};
+        const double a2 = -(M_PI * c->src_f0) * (M_PI * c->src_f0);
+        for (int q = 0; q < 8; ++q) {
+            double g[kMaxNG];
+            lagrange_time(c->rt, gl8[q], g);
+            const double u = tn + gl8[q] * dt - c->src_td;
+            const double S = (0.5 + a2 * u * u) * std::exp(a2 * u * u);
+            for (int a = 0; a < NG; ++a) ti.v[a] += dt * gl8[8 + q] * g[a] * S;
+        }
+        return ti;
+    };
     const unsigned egrid = (unsigned)std::min<int64_t>((ns * nvel + 255) / 256, c->n_sm * 32);
     auto residual_into_av = [&](int n) {   // a_v += R^T (rec^n - d^n), n = 1..N
         const int64_t tot = (int64_t)ns * NR * d * NP;
@@ -439,6 +488,12 @@ int misfit_grad_impl(stdg_ctx* c, double dt, int N, const double* data, int K, d
             const double* vn = Vb + (size_t)(n - n0) * ns * ntr;
             adj_element_kernel<<<egrid, 256, 0, c->stream>>>(c->n_elem, ns, d, NP, NG, c->d_rt, c->d_rhoJ, dJ, lamJ, vn, xn,
                                                              av, grho); note_launch(c);
+            if (src_grad) {   // lam^T ds^n/dtheta: the source enters b^n only
+                const int64_t tot = (int64_t)nsrc * d * NP;
+                adj_source_kernel<<<(unsigned)std::min<int64_t>((tot + 127) / 128, c->n_sm * 4), 128, 0, c->stream>>>(
+                    nsrc, c->src_per_shot, d, NP, NG, selem, lamJ, nvel, time_integral(t0 + n * dt), gsrc);
+                note_launch(c);
+            }
             if (n >= 1) residual_into_av(n);
             if (d == 2)
                 adj_face_kernel<2><<<fgrid, 128, fsmem, c->stream>>>(c->n_face, ns, NP, NG, c->d_face_l, c->d_face_r, c->d_D,
@@ -465,6 +520,31 @@ int misfit_grad_impl(stdg_ctx* c, double dt, int N, const double* data, int K, d
         if (g_mu) { g_mu[l] += wl / (wl + wr) * hm_[f]; if (r >= 0) g_mu[r] += wr / (wl + wr) * hm_[f]; }
     }
     if (g_rho) std::copy(hr.begin(), hr.end(), g_rho);
+    if (g_src) {   // per source: [d/d amplitude, d/d direction (dim), d/d position (dim)]
+        const int64_t nall = (int64_t)ns * c->src_per_shot;
+        std::fill(g_src, g_src + nall * (1 + 2 * d), 0.0);
+        if (src_grad) {
+            std::vector<double> G((size_t)nsrc * d * NP), phi(NP), dphi((size_t)NP * d);
+            ADJ_CUDA(cudaMemcpy(G.data(), gsrc, sizeof(double) * G.size(), cudaMemcpyDeviceToHost));
+            for (int64_t q = 0; q < nsrc; ++q) {
+                source_basis_host(c, q, phi.data(), dphi.data());
+                const double* dir = c->src_dir.data() + q * d;
+                const double* Gq = G.data() + q * d * NP;
+                double* out = g_src + q * (1 + 2 * d);
+                for (int l = 0; l < d; ++l) {
+                    double gp = 0.0;
+                    for (int n = 0; n < NP; ++n) gp += Gq[l * NP + n] * phi[n];
+                    out[0] += dir[l] * gp;
+                    out[1 + l] = c->src_a1 * gp;
+                    for (int m = 0; m < d; ++m) {
+                        double gd = 0.0;
+                        for (int n = 0; n < NP; ++n) gd += Gq[l * NP + n] * dphi[n * d + m];
+                        out[1 + d + m] += c->src_a1 * dir[l] * gd;
+                    }
+                }
+            }
+        }
+    }
     // the context ends at the final time, as after a forward run
     ADJ_CUDA(restore(ck + nseg * state));
     c->t = t0 + N * dt;

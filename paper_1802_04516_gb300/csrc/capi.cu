@@ -72,6 +72,43 @@ static void eval_phi_host(const stdg_ctx* c, int64_t e, const double* x, double*
     }
 }
 
+// phi(x_s) and grad phi(x_s) (physical coordinates, [NP][dim]) for source q, the source's
+// element held fixed (host; for the source-term gradient of the misfit)
+void source_basis_host(const stdg_ctx* c, int64_t q, double* phi, double* dphi) {
+    const int d = c->dim, NP = c->Nphi, nv = d + 1;
+    double y[3];
+    const int64_t e = c->src_elem[q];
+    locate_point(c->hm, c->src_xs.data() + q * d, y);
+    double xi[3] = {0, 0, 0};
+    for (int r = 0; r < d; ++r)
+        for (int a = 0; a < d; ++a) xi[r] += c->hm.Jinv[(e * d + r) * d + a] * (y[a] - c->hm.X[(e * nv) * d + a]);
+    for (int k = 0; k < NP; ++k) {
+        phi[k] = 0.0;
+        for (int m = 0; m < d; ++m) dphi[k * d + m] = 0.0;
+    }
+    for (int a = 0; a < NP; ++a) {
+        double v = 1.0, g[3];
+        for (int r = 0; r < d; ++r)
+            for (int t = 0; t < c->rt.exps[a][r]; ++t) v *= xi[r];
+        for (int r = 0; r < d; ++r) {   // d xi^a / d xi_r
+            const int er = c->rt.exps[a][r];
+            double w = er == 0 ? 0.0 : (double)er;
+            for (int s2 = 0; s2 < d; ++s2)
+                for (int t = 0; t < c->rt.exps[a][s2] - (s2 == r ? 1 : 0); ++t) w *= xi[s2];
+            g[r] = w;
+        }
+        for (int k = 0; k < NP; ++k) {
+            const double ck = c->rt.coef[a * NP + k];
+            phi[k] += ck * v;
+            for (int m = 0; m < d; ++m) {   // d/dx_m = sum_r d/dxi_r Jinv[r][m]
+                double s = 0.0;
+                for (int r = 0; r < d; ++r) s += g[r] * c->hm.Jinv[(e * d + r) * d + m];
+                dphi[k * d + m] += ck * s;
+            }
+        }
+    }
+}
+
 static int alloc_state(stdg_ctx* c, int n_shots) {
     dev_free(c, c->d_vtr);
     dev_free(c, c->d_sigtr);
@@ -546,6 +583,8 @@ int stdg_set_point_sources(stdg_ctx* c, int n_shots, int per_shot, const double*
     if ((rc = dev_alloc(c, (void**)&c->d_src, sizeof(double) * host.size())) != STDG_OK) return rc;
     STDG_CUDA(c, cudaMemcpy(c->d_src, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice));
     c->src_per_shot = per_shot;
+    c->src_xs.assign(xs, xs + ns * d);
+    c->src_dir.assign(dir, dir + ns * d);
     c->src_f0 = f0;
     c->src_td = t_delay;
     c->src_a1 = a1;
@@ -623,7 +662,7 @@ int stdg_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* out) {
 }
 
 int stdg_misfit_grad(stdg_ctx* c, double dt, int n_steps, const double* data, int checkpoint_every, double* loss,
-                     double* g_lambda, double* g_mu, double* g_rho, stdg_stats* out) {
+                     double* g_lambda, double* g_mu, double* g_rho, double* g_src, stdg_stats* out) {
     CHECK_CTX(c);
     NEED_ALL(c);
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || !data || !loss)
@@ -637,7 +676,7 @@ int stdg_misfit_grad(stdg_ctx* c, double dt, int n_steps, const double* data, in
     int rc = ensure_records(c, n_steps);
     if (rc != STDG_OK) return rc;
     stdg_stats st;
-    rc = misfit_grad_impl(c, dt, n_steps, data, K, loss, g_lambda, g_mu, g_rho, &st);
+    rc = misfit_grad_impl(c, dt, n_steps, data, K, loss, g_lambda, g_mu, g_rho, g_src, &st);
     if (out) *out = st;
     return rc;
 }

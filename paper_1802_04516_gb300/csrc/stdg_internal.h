@@ -119,6 +119,7 @@ struct stdg_ctx {
     double *d_src = nullptr;           // [shot][source]: [dim dir][Nphi phi(x_s)]
     int32_t *d_src_elem = nullptr;
     double src_f0 = 0, src_td = 0, src_a1 = 0;
+    std::vector<double> src_xs, src_dir;   // host copies: [shot][source of the shot][dim]
     double* d_gl8 = nullptr;           // 8-point Gauss-Legendre rule on [0,1]: nodes, weights
     std::vector<double> lam_e, mu_e, rho_e;   // host copies of the material
     int n_rec = 0;
@@ -242,5 +243,7 @@ int solver_solve(stdg_ctx* c, double dt, stdg_stats* st);   // A x = b on the st
 
 // adjoint.cu
 int misfit_grad_impl(stdg_ctx* c, double dt, int n_steps, const double* data, int checkpoint_every, double* loss,
-                     double* g_lam, double* g_mu, double* g_rho, stdg_stats* stats);
+                     double* g_lam, double* g_mu, double* g_rho, double* g_src, stdg_stats* stats);
+// capi.cu: phi(x_s) and its physical gradient [NP][dim] for source q (host copies of the sources)
+void source_basis_host(const stdg_ctx* c, int64_t q, double* phi, double* dphi);
 }  // namespace stdg

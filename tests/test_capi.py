@@ -61,9 +61,10 @@ def test_every_call_rejects_a_null_context():
     lib.stdg_destroy(None)                                   # a no-op
     assert lib.stdg_last_error(None) == b"null context"
     assert lib.stdg_mesh_faces(2, 0, None, 0, None, None, None, None, None) == -1
+    assert lib.stdg_measure_fma_peak(1, None) == -1           # null output, before touching the device
     for name, (res, args) in SIGNATURES.items():
         if name in ("stdg_create", "stdg_destroy", "stdg_last_error", "stdg_mesh_faces", "stdg_locate_points",
-                    "stdg_reference_tables"):
+                    "stdg_reference_tables", "stdg_measure_fma_peak"):
             continue                                         # no context argument
         vals = [None] + [a(0) if a in (ctypes.c_int, ctypes.c_int64, ctypes.c_double) else None for a in args[1:]]
         assert getattr(lib, name)(*vals) == -1, name

@@ -501,15 +501,20 @@ def test_tensor_core_stencil_preconditioner_matches_oracle_per_shot(n_shots):
 
 
 def test_tensor_core_stencil_preconditioner_keeps_iteration_counts():
-    # the TF32 local step must not degrade the preconditioner: the stacked mixed-precision
-    # solve takes about as many iterations as the FP64 one (FP64 blocks, CUDA cores)
+    # the TF32 local step must not degrade the preconditioner: a stacked mixed-precision solve
+    # (tensor-core local step) takes about as many iterations as its slowest shot solved alone
+    # (one shot: the FP32 CUDA-core local step), as the per-shot recurrences make it do with
+    # exact arithmetic
+    import dataclasses
     need_gpu()
     w = synth.scaled("c4", ny=10, steps=3, n_shots=12)
-    its = {}
-    for precision in ("fp64", "mixed"):
-        s = gpu_solver(w, precision=precision, rel_tol=1e-10, max_iters=20000, preconditioner=2)
-        st = s.step(w.dt, 3)
-        assert st["status"] == 0
-        its[precision] = st["iters_max"]
-    print("stacked Pre2 iterations per slab (max): FP64 %d, mixed (tensor-core local step) %d" % (its["fp64"], its["mixed"]))
-    assert its["mixed"] <= 1.25 * its["fp64"] + 5
+    kw = dict(precision="mixed", rel_tol=1e-10, max_iters=20000, preconditioner=2)
+    st = gpu_solver(w, **kw).step(w.dt, 3)
+    assert st["status"] == 0
+    singles = []
+    for k in range(w.n_shots):
+        wk = dataclasses.replace(w, shots_xs=w.shots_xs[k:k + 1], shots_dir=w.shots_dir[k:k + 1])
+        singles.append(gpu_solver(wk, **kw).step(w.dt, 3)["iters_max"])
+    print("stacked Pre2 iterations per slab (max): tensor-core batch %d, shots alone (CUDA cores) max %d"
+          % (st["iters_max"], max(singles)))
+    assert st["iters_max"] <= 1.15 * max(singles) + 5

@@ -122,3 +122,42 @@ def test_gradient_matches_central_differences():
             # model perturbation is strongly curved: at h_rel = 1e-4 that term alone is ~4e-6 relative)
             fd = (4.0 * fds[1] - fds[0]) / 3.0
             assert abs(fd - g[e]) <= 1e-6 * abs(g[e]) + 1e-9 * np.abs(g).max(), (name, e, fd, g[e])
+
+
+def test_source_gradient_matches_differences_and_homogeneity():
+    # dL/d(amplitude), dL/d(force direction), dL/d(position) of each shot's point source
+    # (Sec. 6.3).  The source vector is linear in the amplitude and the direction, so the misfit
+    # is quadratic in them and a central difference is exact up to rounding; the position enters
+    # through phi(x_s) (Richardson-extrapolated differences, the source staying in its element).
+    # Homogeneity: a1 dL/da1 = d . dL/dd.
+    w, w_true, pg = _tiny()
+    geom = _geom(w, pg)
+    src = _sources(w)
+    data = np.array([adj.forward(adj.make_sim(_geom(w_true, pg), w_true.lam, w_true.mu, w_true.rho), w.n_steps,
+                                 s, w.f0, w.t_delay, w.a1, w.receivers)[0] for s in src])
+    L, _, _, _, g_src = adj.misfit_gradient(geom, w.lam, w.mu, w.rho, w.n_steps, src, w.f0, w.t_delay, w.a1,
+                                            w.receivers, data, source_grad=True)
+    d = w.dim
+    assert g_src.shape == (len(src), 1 + 2 * d)
+
+    def Lk(k, xs, dr, a1):   # the misfit of shot k alone (the only term its source enters)
+        return adj.misfit(geom, w.lam, w.mu, w.rho, w.n_steps, [(xs, dr)], w.f0, w.t_delay, a1, w.receivers,
+                          data[k:k + 1])
+
+    for k, (xs, dr) in enumerate(src):
+        xs, dr = np.asarray(xs, float), np.asarray(dr, float)
+        g = g_src[k]
+        assert abs(w.a1 * g[0] - dr @ g[1:1 + d]) <= 1e-10 * (abs(w.a1 * g[0]) + 1e-300)
+        h = 1e-3 * w.a1
+        fd = (Lk(k, xs, dr, w.a1 + h) - Lk(k, xs, dr, w.a1 - h)) / (2 * h)
+        assert abs(fd - g[0]) <= 1e-6 * abs(g[0]), ("a1", k, fd, g[0])
+        for l in range(d):
+            e = np.eye(d)[l] * 1e-3
+            fd = (Lk(k, xs, dr + e, w.a1) - Lk(k, xs, dr - e, w.a1)) / 2e-3
+            assert abs(fd - g[1 + l]) <= 1e-6 * np.abs(g[1:1 + d]).max(), ("dir", k, l, fd, g[1 + l])
+            fds = []
+            for hx in (2e-5, 1e-5):
+                ex = np.eye(d)[l] * hx
+                fds.append((Lk(k, xs + ex, dr, w.a1) - Lk(k, xs - ex, dr, w.a1)) / (2 * hx))
+            fd = (4.0 * fds[1] - fds[0]) / 3.0
+            assert abs(fd - g[1 + d + l]) <= 1e-5 * np.abs(g[1 + d:]).max(), ("x_s", k, l, fd, g[1 + d + l])

@@ -96,3 +96,82 @@ def test_autograd_function_returns_the_adjoint_gradient():
     assert abs(loss.item() - L) <= tol * L
     for t, g in ((lam, gl), (mu, gm), (rho, gr)):
         assert np.abs(t.grad.numpy() - 3.0 * g).max() <= tol * np.abs(3.0 * g).max()
+
+
+def test_source_gradient_matches_oracle():
+    # dL/d(amplitude, force direction, position) of every shot's point source (Sec. 6.3),
+    # against the oracle's discrete adjoint; the bar as for the material gradients
+    need_gpu()
+    from oracle import adjoint as adj
+    w, wt = _case(p=2)
+    data, _ = _oracle(w, wt)
+    geom = (w.xyz, w.elem_vert, w.period, w.p, w.p_gamma, w.dt)
+    src = [(w.shots_xs[k], w.shots_dir[k]) for k in range(w.n_shots)]
+    L, _, _, _, gs = adj.misfit_gradient(geom, w.lam, w.mu, w.rho, w.n_steps, src, w.f0, w.t_delay, w.a1,
+                                         w.receivers, data, source_grad=True)
+    for precision, rel_tol in (("fp64", 1e-13), ("mixed", 1e-12)):
+        s = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000, preconditioner=2)
+        Lg, _, _, _, gsg, _ = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=5, source_grad=True)
+        amp = np.linalg.norm(data) / np.sqrt(2.0 * L)
+        tol = (1e-11 if precision == "fp64" else 1e-10) * amp + 1e-10
+        err = np.abs(gsg - gs).max() / np.abs(gs).max()
+        print(precision, "source gradient error %.3g (bar %.3g)" % (err, tol))
+        assert gsg.shape == gs.shape and err <= tol
+
+
+def test_source_gradient_matches_gpu_finite_differences():
+    # the GPU's own misfit with FP64 solves to 1e-14: the misfit is quadratic in the force
+    # direction (exact central differences) and smooth in the position inside the source's
+    # element (Richardson-extrapolated differences); a1 dL/da1 = d . dL/dd
+    need_gpu()
+    w, wt = _case(p=2, steps=10)
+    data, _ = _oracle(w, wt)
+    s = gpu_solver(w, precision="fp64", rel_tol=1e-14, max_iters=20000, preconditioner=2)
+    _, _, _, _, gs, _ = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=4, source_grad=True)
+    d = w.dim
+
+    def L(xs, dr):
+        f = gpu_solver(w, precision="fp64", rel_tol=1e-14, max_iters=20000, preconditioner=2)
+        f.set_sources(xs, dr, w.f0, w.t_delay, w.a1)
+        return f.misfit_grad(w.dt, w.n_steps, data, grad=False)[0]
+
+    for k in range(w.n_shots):
+        g = gs[k]
+        assert abs(w.a1 * g[0] - w.shots_dir[k] @ g[1:1 + d]) <= 1e-9 * np.abs(w.a1 * g[0])
+        for l in range(d):
+            dp, dm = w.shots_dir.copy(), w.shots_dir.copy()
+            dp[k, l] += 1e-3
+            dm[k, l] -= 1e-3
+            fd = (L(w.shots_xs, dp) - L(w.shots_xs, dm)) / 2e-3
+            assert abs(fd - g[1 + l]) <= 1e-6 * np.abs(g[1:1 + d]).max(), ("dir", k, l, fd, g[1 + l])
+            fds = []
+            for hx in (2e-5, 1e-5):
+                xp, xm = w.shots_xs.copy(), w.shots_xs.copy()
+                xp[k, l] += hx
+                xm[k, l] -= hx
+                fds.append((L(xp, w.shots_dir) - L(xm, w.shots_dir)) / (2 * hx))
+            fd = (4.0 * fds[1] - fds[0]) / 3.0
+            assert abs(fd - g[1 + d + l]) <= 1e-5 * np.abs(g[1 + d:]).max(), ("x_s", k, l, fd, g[1 + d + l])
+
+
+def test_autograd_function_differentiates_the_sources():
+    import torch
+    from paper_1802_04516_gb300.binding import misfit
+    need_gpu()
+    w, wt = _case(p=1, steps=8)
+    data, _ = _oracle(w, wt)
+    s = gpu_solver(w, precision="fp64", rel_tol=1e-13, max_iters=20000, preconditioner=2)
+    force = w.a1 * w.shots_dir
+    lam, mu, rho = (torch.tensor(a, requires_grad=True) for a in (w.lam, w.mu, w.rho))
+    xs = torch.tensor(w.shots_xs, requires_grad=True)
+    fo = torch.tensor(force, requires_grad=True)
+    loss = misfit(s, lam, mu, rho, w.dt, w.n_steps, data,
+                  sources=dict(xs=xs, force=fo, f0=w.f0, t_delay=w.t_delay, n_shots=w.n_shots))
+    (2.0 * loss).backward()
+    ref = gpu_solver(w, precision="fp64", rel_tol=1e-13, max_iters=20000, preconditioner=2)
+    Lr, gl, _, _, gs, _ = ref.misfit_grad(w.dt, w.n_steps, data, source_grad=True)
+    d = w.dim
+    assert abs(loss.item() - Lr) <= 1e-10 * Lr
+    assert np.abs(xs.grad.numpy() - 2.0 * gs[:, 1 + d:]).max() <= 1e-9 * np.abs(gs[:, 1 + d:]).max()
+    assert np.abs(fo.grad.numpy() - 2.0 * gs[:, 1:1 + d] / w.a1).max() <= 1e-9 * np.abs(gs[:, 1:1 + d]).max()
+    assert np.abs(lam.grad.numpy() - 2.0 * gl).max() <= 1e-9 * np.abs(gl).max()
