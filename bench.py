@@ -273,6 +273,54 @@ def multishot_section(torch, args, stream, dist, world):
             "pre2_local_batch_roofline": local}
 
 
+def c3_solver(w, precision, stream, args, pre):
+    from paper_1802_04516_gb300.binding import Solver
+    s = Solver(w.dim, w.p, w.p_gamma, w.scheme, precision, rel_tol=1e-8, max_iters=20000, gmres_restart=args.restart,
+               inner_tol=args.inner_tol, use_graph=not args.host_loop, stream=stream, preconditioner=pre)
+    s.set_mesh(w.xyz, w.elem_vert, w.period)
+    s.set_material(w.lam, w.mu, w.rho)
+    s.set_shots(1)
+    pw = w.plane_wave
+    s.set_plane_wave(pw["kind"], pw["n"], pw["pol"], pw["amp"])
+    return s
+
+
+def c3_section(torch, args, stream, dist, world, pk, fp64_pk):
+    """The 3D configuration: [0,1]^3 periodic, 6 x 64^3 = 1,572,864 jittered Kuhn tetrahedra,
+    p = p_gamma = 2, homogeneous (vp = sqrt 3, vs = 1, rho = 1), plane S wave along x polarised
+    in y, dt = 0.02, mixed precision and FP64 at 1e-8 with the block-Jacobi Pre1 (the stencil
+    blocks would hold (3 N_phi N_gamma)^2 = 8,100 values per element: 51 GB in FP32 and 102 GB
+    in FP64 at this size).  Reports DOF-steps/s of both paths and the rooflines of the
+    operator's face kernel (3, 10, 3): FP32 against the measured HBM bandwidth, FP64 against the
+    measured FP64 FMA rate."""
+    import synth
+    w = synth.c3_cube_swave(n=args.c3_n, steps=args.c3_steps)
+    out = {"workload": "c3_cube_swave: %d tetrahedra (6 x %d^3, Kuhn, jitter 0.2h), p=p_gamma=2, plane S wave, dt=%.3g, "
+                       "block-Jacobi Pre1" % (w.n_elem, args.c3_n, w.dt)}
+    t0 = time.perf_counter()
+    s = c3_solver(w, "mixed", stream.cuda_stream, args, 1)
+    out["setup_s_mixed"] = time.perf_counter() - t0
+    n_face = s.n_face
+    dofs = dofs_per_slab(w, n_face)
+    ms, iters, launches, st = time_steps(torch, s, w, args.c3_steps, 1, stream, dist)
+    out["mixed"] = {"dof_steps_per_s": world * dofs * args.c3_steps / (ms * 1e-3), "ms_per_step": ms / args.c3_steps,
+                    "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"], "gpu_launches": launches}
+    out["face_fp32"] = face_kernel_roofline(s, w, True, n_face, pk)
+    out["face_fp64"] = face_kernel_roofline(s, w, False, n_face, pk, fp64_pk)
+    out["face_fp32"]["kernel"] = "face_apply_tma_kernel<3,10,3,float>"
+    out["face_fp64"]["kernel"] = "face_apply_kernel<3,10,double>"
+    s.close()
+    if args.c3_fp64_steps > 0:
+        s = c3_solver(w, "fp64", stream.cuda_stream, args, 1)
+        ms, iters, _, st = time_steps(torch, s, w, args.c3_fp64_steps, 0, stream, dist)
+        out["fp64"] = {"dof_steps_per_s": world * dofs * args.c3_fp64_steps / (ms * 1e-3),
+                       "ms_per_step": ms / args.c3_fp64_steps, "krylov_iters_per_step": iters,
+                       "final_rel_res": st["final_rel_res"], "note": "no warm-up slab: includes graph capture"}
+        s.close()
+    out["dofs_per_slab"] = dofs
+    return out
+
+
 def ragged_section(torch, args, stream, dist, world):
     """The ragged batch: 16 meshes of ~5k to ~80k triangles side by side as one disconnected
     mesh, one source per part, advanced by one mixed-precision solve per slab."""
@@ -310,7 +358,7 @@ def adjoint_section(torch, args, stream, dist, world):
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    loss, gl, gm, gr, st = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=20)
+    loss, gl, gm, gr, gs, st = s.misfit_grad(w.dt, w.n_steps, data, checkpoint_every=20, source_grad=True)
     torch.cuda.synchronize()
     sec = max_over_ranks(torch, dist, time.perf_counter() - t0)
     s.close()
@@ -319,7 +367,7 @@ def adjoint_section(torch, args, stream, dist, world):
                                                  "" if w.n_steps == 300 else " (of the workload's 300)", w.dt),
             "grads_per_s": world / sec, "seconds_per_gradient": sec, "loss": loss,
             "grad_norms": {"lambda": float(np.linalg.norm(gl)), "mu": float(np.linalg.norm(gm)),
-                           "rho": float(np.linalg.norm(gr))},
+                           "rho": float(np.linalg.norm(gr)), "sources": float(np.linalg.norm(gs))},
             "krylov_iters_total": st["iters_total"], "precision": "mixed FP32/FP64 (1e-8 rel residual)",
             "timing": "wall clock of one call, no warm-up (includes graph capture of the step and solve graphs)"}
 
@@ -461,6 +509,10 @@ def main():
     ap.add_argument("--no-multishot", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--c3-n", type=int, default=64, help="cubes per direction of the 3D configuration (64: 1.57M tets)")
+    ap.add_argument("--c3-steps", type=int, default=2, help="timed mixed-precision slabs of the 3D configuration")
+    ap.add_argument("--c3-fp64-steps", type=int, default=1, help="timed FP64 slabs of the 3D configuration (0: skip)")
     ap.add_argument("--adj-steps", type=int, default=300, help="slabs of the misfit-gradient run (the workload's 300)")
     ap.add_argument("--full-slabs", type=int, default=200,
                     help="slabs of the untimed-per-slab full run of the benchmark configuration (0: skip)")
@@ -523,6 +575,7 @@ def main():
         multishot = None if args.no_multishot else multishot_section(torch, args, stream, dist, world)
         ragged = None if args.no_ragged else ragged_section(torch, args, stream, dist, world)
         adjoint = None if args.no_adjoint else adjoint_section(torch, args, stream, dist, world)
+        c3 = None if args.no_c3 else c3_section(torch, args, stream, dist, world, pk, fp64_pk)
     if rank != 0:
         return
     cb = None if args.no_cpu_baseline else cpu_baseline()
@@ -550,6 +603,7 @@ def main():
         "multishot": multishot,
         "ragged": ragged,
         "adjoint": adjoint,
+        "c3": c3,
         "cpu_baseline": cb,
     }
     print(json.dumps(line))
