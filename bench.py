@@ -250,6 +250,7 @@ def multishot_section(torch, args, stream, dist, world):
     w = synth.c4_multishot(ny=args.ny, n_shots=args.shots, steps=args.ms_steps)
     s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
                      use_graph=not args.host_loop, pre=args.pre)
+    tuning = s.autotune(w.dt)
     n_face = s.n_face
     ms, iters, launches, st = time_steps(torch, s, w, args.ms_steps, 1, stream, dist)
     local = pre2_local_batch_roofline(s, w, peaks()) if args.pre == 2 else None
@@ -270,7 +271,7 @@ def multishot_section(torch, args, stream, dist, world):
             "fp64_single_shot": {"shot_steps_per_s": single, "dof_steps_per_s": single * dofs_shot,
                                  "ms_per_step": ms1 / args.ms_steps, "krylov_iters_per_step": it1},
             "speedup_shot_steps": multi / single, "dofs_per_slab_per_shot": dofs_shot, "steps": args.ms_steps,
-            "pre2_local_batch_roofline": local}
+            "pre2_local_batch_roofline": local, "tuning": tuning}
 
 
 def c3_solver(w, precision, stream, args, pre):
@@ -516,6 +517,8 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=300, help="slabs of the misfit-gradient run (the workload's 300)")
     ap.add_argument("--full-slabs", type=int, default=200,
                     help="slabs of the untimed-per-slab full run of the benchmark configuration (0: skip)")
+    ap.add_argument("--only", choices=["multishot", "ragged", "adjoint", "c3"],
+                    help="run this one section alone and print its object (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solver loops from the host instead of CUDA-graph while nodes (for kernel profilers)")
     args = ap.parse_args()
@@ -538,12 +541,22 @@ def main():
     if dist is not None:
         dist.barrier()
     import synth
-    w = synth.c2_layered_slivers(ny=args.ny, steps=args.steps)
     stream = torch.cuda.Stream()
     pk = peaks()
+    if args.only:
+        with torch.cuda.stream(stream):
+            sec = {"multishot": lambda: multishot_section(torch, args, stream, dist, world),
+                   "ragged": lambda: ragged_section(torch, args, stream, dist, world),
+                   "adjoint": lambda: adjoint_section(torch, args, stream, dist, world),
+                   "c3": lambda: c3_section(torch, args, stream, dist, world, pk, fp64_peak())}[args.only]()
+        if rank == 0:
+            print(json.dumps({"section": args.only, "result": sec}))
+        return
+    w = synth.c2_layered_slivers(ny=args.ny, steps=args.steps)
     with torch.cuda.stream(stream):
         s = build_solver(w, "mixed", stream.cuda_stream, shot_offset=rank_shot_offset(rank), restart=args.restart,
                          inner_tol=args.inner_tol, use_graph=not args.host_loop, pre=args.pre)
+        tuning = s.autotune(w.dt)   # launch shapes picked on this mesh before the step graph is captured
         n_face = s.n_face
         dofs = dofs_per_slab(w, n_face)
         sampler = ClockSampler(local)
@@ -591,7 +604,7 @@ def main():
                    "preconditioner": {0: "none", 1: "block Jacobi (Pre1)", 2: "stencil (Pre2)"}[args.pre],
                    "gmres_restart": args.restart, "inner_tol": args.inner_tol,
                    "control": "host loop" if args.host_loop else "CUDA graph per step (device while loops)", "l2": "working set (blocks, Krylov basis) > 129 MB L2; no flush",
-                   "parallelism": "independent shot per GPU"},
+                   "parallelism": "independent shot per GPU", "tuning": tuning},
         "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"], "refinements_last": st["refinements"],
         "gpu_launches": launches,
         "clocks": clocks,

@@ -287,6 +287,26 @@ int stdg_time_operator(stdg_ctx* ctx, double dt, int fp32, int n, double* ms_out
  * the paper. */
 int stdg_time_kernel(stdg_ctx* ctx, double dt, int which, int fp32, int n, double* ms_out);
 
+/* Launch shapes chosen by the library's autotuner (no counterpart in the paper). */
+typedef struct {
+    int face_warps_per_block;   /* face kernels of the operator: warps per block (1, 2, 4)            */
+    int face_blocks_per_sm;     /* single-shot bulk-copy face kernel: grid cap, blocks per SM         */
+    int pre2_warps_per_block;   /* CUDA-core element-local step of the stencil preconditioner         */
+    int mma_ctas_per_sm;        /* tensor-core element-local step (a batch of shots): CTAs per SM     */
+    double face_ms, pre2_ms;    /* best time per launch of the tuned face kernel / local step (0: not tuned) */
+    int candidates;             /* configurations timed                                               */
+} stdg_tuning;
+
+/* Autotuner: times every candidate launch shape of the hot kernels this context runs for slab
+ * size dt -- the FP32 face kernel (mixed precision; warps per block 1/2/4 and, for one shot, the
+ * grid cap 8/16/32/64 blocks per SM) and the element-local step of the stencil preconditioner
+ * (warps per block, or CTAs per SM of the tensor-core kernel) -- on the context's own mesh and
+ * shot count (zero vectors, 10 launches each, CUDA events) and keeps the fastest for every later
+ * launch; step graphs captured before are dropped and re-captured.  `out` (may be NULL) receives
+ * the choices.  Allocates three scratch vectors for the call.  Results do not depend on the
+ * choice beyond the order of floating-point atomics. */
+int stdg_autotune(stdg_ctx* ctx, double dt, stdg_tuning* out);
+
 /* Arithmetic peak of this GPU (no counterpart in the paper): the FP64 (fp64 != 0) or FP32 FMA
  * rate in TFLOP/s (2 flops per FMA) that the library's own probe kernel sustains -- 8 independent
  * FMA chains per thread, 8 blocks of 256 threads per SM, timed with CUDA events on a private

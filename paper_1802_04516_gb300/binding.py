@@ -32,6 +32,14 @@ class stdg_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class stdg_tuning(C.Structure):
+    _fields_ = [("face_warps_per_block", C.c_int), ("face_blocks_per_sm", C.c_int), ("pre2_warps_per_block", C.c_int),
+                ("mma_ctas_per_sm", C.c_int), ("face_ms", C.c_double), ("pre2_ms", C.c_double), ("candidates", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _I32 = C.POINTER(C.c_int32)
@@ -70,6 +78,7 @@ SIGNATURES = {
     "stdg_inject_wait_error": (C.c_int, [_P]),
     "stdg_apply_preconditioner_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
     "stdg_measure_fma_peak": (C.c_int, [C.c_int, _D]),
+    "stdg_autotune": (C.c_int, [_P, C.c_double, C.POINTER(stdg_tuning)]),
 }
 
 _lib = None
@@ -370,6 +379,12 @@ class Solver:
         ms = C.c_double(0.0)
         self._chk(self.lib.stdg_time_kernel(self.h, dt, int(which), 1 if fp32 else 0, n, C.byref(ms)))
         return ms.value
+
+    def autotune(self, dt):
+        """Time the candidate launch shapes of the hot kernels on this context and keep the fastest."""
+        t = stdg_tuning()
+        self._chk(self.lib.stdg_autotune(self.h, dt, C.byref(t)))
+        return t.as_dict()
 
     def inject_wait_error(self):
         """Set the device error word as a timed-out bulk-copy wait would (failure-path tests)."""

@@ -931,6 +931,93 @@ int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double*
     return take_device_error(c);
 }
 
+// Times each candidate launch shape of the kernels this context runs (zero vectors, n
+// back-to-back launches, CUDA events) and keeps the fastest; graphs captured before are dropped.
+int stdg_autotune(stdg_ctx* c, double dt, stdg_tuning* out) {
+    CHECK_CTX(c);
+    NEED_ALL(c);
+    if (!(dt > 0) || !std::isfinite(dt)) STDG_FAIL(c, STDG_EINVAL, "dt must be > 0");
+    int rc;
+    const bool mixed = c->opt.precision != STDG_FP64;
+    const int ns = c->n_shots;
+    if (mixed && (rc = ensure_fp32(c)) != STDG_OK) return rc;
+    if (mixed && (rc = upload_material32(c)) != STDG_OK) return rc;
+    if (c->opt.preconditioner && (rc = precond_for_dt(c, dt)) != STDG_OK) return rc;
+    const size_t w = mixed ? sizeof(float) : sizeof(double);
+    const size_t bytes = w * c->nvel * ns;
+    void *dx = nullptr, *dy = nullptr, *dw = nullptr;
+    if ((rc = dev_alloc(c, &dx, bytes)) != STDG_OK) return rc;
+    if ((rc = dev_alloc(c, &dy, bytes)) != STDG_OK) { dev_free(c, dx); return rc; }
+    if ((rc = dev_alloc(c, &dw, bytes)) != STDG_OK) { dev_free(c, dx); dev_free(c, dy); return rc; }
+    STDG_CUDA(c, cudaMemsetAsync(dx, 0, bytes, c->stream));
+    STDG_CUDA(c, cudaMemsetAsync(dy, 0, bytes, c->stream));
+    STDG_CUDA(c, cudaMemsetAsync(dw, 0, bytes, c->stream));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int tried = 0;
+    auto time = [&](auto launch) -> double {   // ms per launch, or a huge value if a launch fails
+        const int n = 10;
+        if (launch() != cudaSuccess) { cudaGetLastError(); return 1e30; }
+        cudaEventRecord(e0, c->stream);
+        for (int i = 0; i < n; ++i)
+            if (launch() != cudaSuccess) { cudaGetLastError(); return 1e30; }
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ++tried;
+        return ms / n;
+    };
+    stdg_tuning res{};
+    // the face kernel of the Krylov operator: FP32 in mixed precision (the bulk-copy kernel for one
+    // shot, the register kernel for a batch), FP64 otherwise (its generic kernel has fixed shapes)
+    if (mixed) {
+        double best = 1e30;
+        Tuning bt = c->tune;
+        for (int wpb : {1, 2, 4})
+            for (int bpsm : (ns == 1 ? std::vector<int>{8, 16, 32, 64} : std::vector<int>{16})) {
+                c->tune.face_wpb = wpb;
+                c->tune.face_bpsm = bpsm;
+                const double ms = time([&]() {
+                    return launch_apply32(c, dt, (const float*)dx, (float*)dy, 1.0, nullptr, 0, ns);
+                });
+                if (ms < best) { best = ms; bt = c->tune; }
+            }
+        c->tune = bt;
+        res.face_ms = best;
+    }
+    if (c->opt.preconditioner == 2) {
+        double best = 1e30;
+        Tuning bt = c->tune;
+        const bool mma = mixed && ns > 1 && c->d_pre2_mma;
+        for (int k : (mma ? std::vector<int>{1, 2} : std::vector<int>{1, 2, 4})) {
+            if (mma) c->tune.mma_cps = k; else c->tune.pre2_wpb = k;
+            const double ms = time([&]() -> cudaError_t {
+                if (mixed) return launch_pre2_local_batch(c, (const float*)dx, (const float*)dw, (float*)dy);
+                return launch_pre2_local(c, 0, dx, dw, dy);
+            });
+            if (ms < best) { best = ms; bt = c->tune; }
+        }
+        c->tune = bt;
+        res.pre2_ms = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(c, dx);
+    dev_free(c, dy);
+    dev_free(c, dw);
+    if ((rc = take_device_error(c)) != STDG_OK) return rc;
+    solver_invalidate_graph(c);   // graphs keep the launch shapes they were captured with
+    res.face_warps_per_block = c->tune.face_wpb;
+    res.face_blocks_per_sm = c->tune.face_bpsm;
+    res.pre2_warps_per_block = c->tune.pre2_wpb;
+    res.mma_ctas_per_sm = c->tune.mma_cps;
+    res.candidates = tried;
+    if (out) *out = res;
+    return STDG_OK;
+}
+
 int stdg_inject_wait_error(stdg_ctx* c) {
     CHECK_CTX(c);
     if (!c->d_err) STDG_FAIL(c, STDG_ESTATE, "no device error word");

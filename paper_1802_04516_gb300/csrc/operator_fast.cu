@@ -382,17 +382,17 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
     const bool aligned = (reinterpret_cast<uintptr_t>(D) % 16 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
                          ((ld * (int64_t)sizeof(R)) % 16 == 0);
     if (nshots == 1 && aligned && c->d_err) {
-        const int wpb = 4;
+        const int wpb = c->tune.face_wpb;   // <= 4: the kernel's launch bounds and its per-warp barriers
         const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
         cudaFuncSetAttribute(face_apply_tma_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, (int64_t)c->n_sm * 16);
+        const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
         face_apply_tma_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
             c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, c->d_err);
         note_launch(c);
         return cudaGetLastError();
     }
     using F = FaceReg<DIM, NP, NG, R>;
-    const int wpb = 4;
+    const int wpb = c->tune.face_wpb;
     const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, 1 << 30);
     if (F::HALVES == 2 && nshots >= 2) {
         constexpr int H = F::HALVES;

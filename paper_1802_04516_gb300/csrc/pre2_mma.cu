@@ -308,7 +308,7 @@ bool launch_pre2_local_mma(stdg_ctx* c, const float* r, const int* ridx, int64_t
     if (!aligned) return false;
     cudaFuncSetAttribute(pre2_local_mma_kernel<36>, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
     const int64_t npairs = (c->n_elem + 1) / 2;
-    const int64_t grid = std::min<int64_t>(npairs, (int64_t)c->n_sm * 2);
+    const int64_t grid = std::min<int64_t>(npairs, (int64_t)c->n_sm * c->tune.mma_cps);
     pre2_local_mma_kernel<36><<<(unsigned)grid, 128, Sh::SMEM, c->stream>>>(c->n_elem, c->d_pre2_mma, r, ridx, ld, w, z,
                                                                            nshots, c->nvel, c->d_err);
     note_launch(c);

@@ -281,7 +281,7 @@ static cudaError_t pre2_local_t(stdg_ctx* c, const S* Sinv, int64_t es, const R*
         cudaError_t e;
         if (nshots > 1 && launch_pre2_local_mma(c, r, ridx, ld, w, z, nshots, &e)) return e;
     }
-    const int wpb = 4;
+    const int wpb = c->tune.pre2_wpb;
     const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
     if (nshots == 1) {
         pre2_local_kernel<R, S, 1><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * N, c->stream>>>(

@@ -75,6 +75,16 @@ struct Scalars;   // device-side solver scalars (defined in solver.cu)
 
 }  // namespace stdg
 
+namespace stdg {
+// Launch shapes of the hot kernels, chosen by stdg_autotune (defaults until it runs)
+struct Tuning {
+    int face_wpb = 4;     // face kernels: warps per block (1, 2, 4)
+    int face_bpsm = 16;   // single-shot bulk-copy face kernel: grid cap, blocks per SM
+    int pre2_wpb = 4;     // CUDA-core stencil local step: warps per block (1, 2, 4)
+    int mma_cps = 2;      // tensor-core stencil local step: CTAs per SM (1, 2)
+};
+}  // namespace stdg
+
 struct stdg_ctx {
     int dim = 0;
     stdg_options opt{};
@@ -147,6 +157,7 @@ struct stdg_ctx {
     bool wait_gave_up = false;   // the last take_device_error found the word set
 
     int n_sm = 152;              // multiprocessors of the context's device (grid sizing)
+    stdg::Tuning tune;
 
     // ---- solver workspace (solver.cu)
     void* ws = nullptr;

@@ -518,3 +518,24 @@ def test_tensor_core_stencil_preconditioner_keeps_iteration_counts():
     print("stacked Pre2 iterations per slab (max): tensor-core batch %d, shots alone (CUDA cores) max %d"
           % (st["iters_max"], max(singles)))
     assert st["iters_max"] <= 1.15 * max(singles) + 5
+
+
+@pytest.mark.parametrize("shots", [1, 9])
+def test_autotuned_launch_shapes_keep_the_results(shots):
+    # the autotuner picks launch shapes on the context's own mesh and shot count; the states
+    # it then computes match an untuned context's and the oracle's
+    need_gpu()
+    w = synth.scaled("c4", ny=8, steps=2, n_shots=shots)
+    kw = dict(precision="mixed", rel_tol=1e-12, max_iters=20000, preconditioner=2)
+    plain = gpu_solver(w, **kw)
+    plain.step(w.dt, 2)
+    tuned = gpu_solver(w, **kw)
+    t = tuned.autotune(w.dt)
+    print("autotune", shots, "shots:", t)
+    assert t["face_warps_per_block"] in (1, 2, 4) and t["pre2_warps_per_block"] in (1, 2, 4)
+    assert t["mma_ctas_per_sm"] in (1, 2) and t["candidates"] >= 4 and t["face_ms"] > 0 and t["pre2_ms"] > 0
+    assert tuned.step(w.dt, 2)["status"] == 0
+    _, ref = _oracle_per_shot(w, 2)
+    for k in range(shots):
+        assert rel_l2(tuned.get_state(k)[0], plain.get_state(k)[0]) < 1e-9
+        assert rel_l2(tuned.get_state(k)[0], ref[k][0]) < 1e-8
