@@ -144,7 +144,9 @@ def build_solver(w, precision, stream, shot_offset=0.0, restart=20, inner_tol=1e
     return s
 
 
-def time_steps(torch, s, w, steps, warmup, stream, dist):
+def time_steps(torch, s, w, steps, warmup, stream, dist, start=0):
+    if start > 0:          # untimed spin-up into the run before the warm-up and the timed window
+        s.step(w.dt, start)
     for _ in range(warmup):
         s.step(w.dt, 1)
     torch.cuda.synchronize()
@@ -319,6 +321,25 @@ def c3_section(torch, args, stream, dist, world, pk, fp64_pk):
                        "final_rel_res": st["final_rel_res"], "note": "no warm-up slab: includes graph capture"}
         s.close()
     out["dofs_per_slab"] = dofs
+    return out
+
+
+def order_section(torch, args, stream, dist, world):
+    """Element order: the benchmark mesh as generated (raster order) and the same mesh with its
+    elements and vertices renumbered by a random permutation, mixed precision, same slabs;
+    ms per slab of both (the face kernels gather and scatter whole element rows, and the
+    129 MB L2 holds the FP32 velocity vectors of this mesh)."""
+    import synth
+    out = {}
+    for name, w in (("raster", synth.c2_layered_slivers(ny=args.ny, steps=args.steps)),
+                    ("permuted", synth.permuted(synth.c2_layered_slivers(ny=args.ny, steps=args.steps), seed=5))):
+        s = build_solver(w, "mixed", stream.cuda_stream, restart=args.restart, inner_tol=args.inner_tol,
+                         use_graph=not args.host_loop, pre=args.pre)
+        ms, iters, _, st = time_steps(torch, s, w, args.steps, args.warmup, stream, dist)
+        face_ms = s.time_operator(w.dt, fp32=True, n=20)
+        s.close()
+        out[name] = {"ms_per_step": ms / args.steps, "krylov_iters_per_step": iters, "face_fp32_ms": face_ms}
+    out["slowdown"] = out["permuted"]["ms_per_step"] / out["raster"]["ms_per_step"]
     return out
 
 
@@ -498,6 +519,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--start-slab", type=int, default=100,
+                    help="untimed slabs before the warm-up and the timed window (the benchmark run has 200: the "
+                         "window then lies mid-run, where the Krylov counts are typical of the whole run)")
     ap.add_argument("--ny", type=int, default=224, help="cells in y (224 = the 200,704-triangle mesh)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -517,7 +541,7 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=300, help="slabs of the misfit-gradient run (the workload's 300)")
     ap.add_argument("--full-slabs", type=int, default=200,
                     help="slabs of the untimed-per-slab full run of the benchmark configuration (0: skip)")
-    ap.add_argument("--only", choices=["multishot", "ragged", "adjoint", "c3"],
+    ap.add_argument("--only", choices=["multishot", "ragged", "adjoint", "c3", "order"],
                     help="run this one section alone and print its object (profiling runs)")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solver loops from the host instead of CUDA-graph while nodes (for kernel profilers)")
@@ -548,7 +572,8 @@ def main():
             sec = {"multishot": lambda: multishot_section(torch, args, stream, dist, world),
                    "ragged": lambda: ragged_section(torch, args, stream, dist, world),
                    "adjoint": lambda: adjoint_section(torch, args, stream, dist, world),
-                   "c3": lambda: c3_section(torch, args, stream, dist, world, pk, fp64_peak())}[args.only]()
+                   "c3": lambda: c3_section(torch, args, stream, dist, world, pk, fp64_peak()),
+                   "order": lambda: order_section(torch, args, stream, dist, world)}[args.only]()
         if rank == 0:
             print(json.dumps({"section": args.only, "result": sec}))
         return
@@ -561,7 +586,7 @@ def main():
         dofs = dofs_per_slab(w, n_face)
         sampler = ClockSampler(local)
         sampler.start()
-        ms, iters, launches, st = time_steps(torch, s, w, args.steps, args.warmup, stream, dist)
+        ms, iters, launches, st = time_steps(torch, s, w, args.steps, args.warmup, stream, dist, start=args.start_slab)
         clocks = sampler.stop()
         value = world * dofs * args.steps / (ms * 1e-3)
         cands = {"face": face_kernel_roofline(s, w, True, n_face, pk)}
@@ -604,7 +629,10 @@ def main():
                    "preconditioner": {0: "none", 1: "block Jacobi (Pre1)", 2: "stencil (Pre2)"}[args.pre],
                    "gmres_restart": args.restart, "inner_tol": args.inner_tol,
                    "control": "host loop" if args.host_loop else "CUDA graph per step (device while loops)", "l2": "working set (blocks, Krylov basis) > 129 MB L2; no flush",
-                   "parallelism": "independent shot per GPU", "tuning": tuning},
+                   "parallelism": "independent shot per GPU", "tuning": tuning,
+                   "window": "slabs %d..%d of the %d-slab run (after %d untimed and %d warm-up slabs)"
+                             % (args.start_slab + args.warmup + 1, args.start_slab + args.warmup + args.steps,
+                                200, args.start_slab, args.warmup)},
         "krylov_iters_per_step": iters, "final_rel_res": st["final_rel_res"], "refinements_last": st["refinements"],
         "gpu_launches": launches,
         "clocks": clocks,

@@ -9,5 +9,5 @@ from .meshes import tri_grid, tet_kuhn, add_slivers, unwrap_elements  # noqa: F4
 from .media import layered_2d, homogeneous, gaussian_random_field, lame_from_speeds  # noqa: F401
 from .workloads import (  # noqa: F401
     Workload, c1_periodic_pwave, c2_layered_slivers, c3_cube_swave,
-    c4_multishot, c4_ragged, c5_adjoint, scaled, ragged_union,
+    c4_multishot, c4_ragged, c5_adjoint, scaled, ragged_union, permuted,
 )

@@ -199,3 +199,16 @@ def ragged_union(ks=range(16), p=2, steps=200, scale=1.0, seed=1300, gap=0.5):
                  shots_xs=None, shots_dir=None, receivers=np.concatenate(rec),
                  extra={"part_sources": np.array(xs), "spans": spans})
     return u, spans
+
+
+def permuted(w, seed=0):
+    """The same workload with its elements and vertices renumbered by a seeded random
+    permutation (the same mesh, media, sources and receivers in an unfavourable order)."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    pe = rng.permutation(w.n_elem)
+    pv = rng.permutation(w.xyz.shape[0])            # new id of old vertex v: inv[v]
+    inv = np.empty_like(pv)
+    inv[pv] = np.arange(pv.size)
+    return dataclasses.replace(w, name=w.name + "_permuted", xyz=w.xyz[pv], elem_vert=inv[w.elem_vert[pe]].astype(np.int32),
+                               lam=w.lam[pe], mu=w.mu[pe], rho=w.rho[pe])
