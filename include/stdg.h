@@ -58,7 +58,7 @@ typedef struct stdg_ctx stdg_ctx;
 
 typedef struct {
     int p;              /* spatial degree, 1..4 in 2D, 1..3 in 3D                      */
-    int p_gamma;        /* time degree, 0..3; must be 0 for Crank-Nicolson             */
+    int p_gamma;        /* time degree, 0..4; must be 0 for Crank-Nicolson             */
     int scheme;         /* stdg_scheme                                                   */
     int precision;      /* stdg_precision                                                */
     double rel_tol;     /* Krylov stop: ||b - A x||_2 <= rel_tol ||b||_2                 */
@@ -72,7 +72,9 @@ typedef struct {
                            block row of the inverse of the system restricted to the element and its
                            face neighbours.  Pre2 is not symmetric, so Crank-Nicolson then runs
                            GMRES instead of CG.  Needs d N_phi N_gamma <= 128 (else STDG_EINVAL at
-                           stdg_set_material); costs (d N_phi N_gamma)^2 values per element.    */
+                           stdg_set_material); costs (d N_phi N_gamma)^2 values per element, FP64
+                           in FP64 contexts and FP32 in mixed-precision ones (which keep no FP64
+                           copy: the FP64 stencil apply calls are then STDG_ESTATE).            */
 } stdg_options;
 
 typedef struct {
@@ -212,7 +214,7 @@ int stdg_locate_points(int dim, int64_t n_vert, const double* xyz, int64_t n_ele
  * of the Schur term), kappa = gamma(1)^T T^{-1} gamma(0) and u = gamma(1)^T T^{-1} W
  * (N_gamma; the stress-trace update sigma <- kappa sigma - dt sum_b u_b (E:g)_b).  Any
  * output may be NULL.  Returns STDG_OK or STDG_EINVAL (dim not 2 or 3, p outside 1..4 in
- * 2D or 1..3 in 3D, p_gamma outside 0..3). */
+ * 2D or 1..3 in 3D, p_gamma outside 0..4). */
 int stdg_reference_tables(int dim, int p, int p_gamma, double* Mref, double* W, double* T, double* S, double* kappa,
                           double* u);
 
@@ -292,7 +294,7 @@ typedef struct {
     int face_warps_per_block;   /* face kernels of the operator: warps per block (1, 2, 4)            */
     int face_blocks_per_sm;     /* single-shot bulk-copy face kernel: grid cap, blocks per SM         */
     int pre2_warps_per_block;   /* CUDA-core element-local step of the stencil preconditioner         */
-    int mma_ctas_per_sm;        /* tensor-core element-local step (a batch of shots): CTAs per SM     */
+    int mma_ctas_per_sm;        /* tensor-core element-local step (a batch of shots): CTAs per SM (1-3) */
     double face_ms, pre2_ms;    /* best time per launch of the tuned face kernel / local step (0: not tuned) */
     int candidates;             /* configurations timed                                               */
 } stdg_tuning;

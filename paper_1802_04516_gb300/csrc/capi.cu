@@ -199,8 +199,11 @@ static int setup_pre1(stdg_ctx* c) {
         if (!pre2_supported(c)) STDG_FAIL(c, STDG_EINVAL, "stencil preconditioner: element block too large for this shape");
         const int N = c->dim * c->Nphi * c->Ng;
         const int64_t nS = ne * (int64_t)N * N;
-        if (!c->d_pre2) {
-            if ((rc = dev_alloc(c, (void**)&c->d_pre2, sizeof(double) * nS)) != STDG_OK) return rc;
+        if (!c->d_pre2 && !c->d_pre2_32) {
+            // the FP64 solver keeps FP64 blocks; the mixed path keeps only the FP32 ones its inner
+            // solve applies (its FP64 refinement residual needs no preconditioner)
+            if (c->opt.precision == STDG_FP64 &&
+                (rc = dev_alloc(c, (void**)&c->d_pre2, sizeof(double) * nS)) != STDG_OK) return rc;
             if (c->opt.precision != STDG_FP64 &&
                 (rc = dev_alloc(c, (void**)&c->d_pre2_32, sizeof(float) * ne * pre2_stride32(c))) != STDG_OK) return rc;
             // tensor-core image of the FP32 blocks for batches of shots
@@ -265,7 +268,7 @@ int stdg_create(stdg_ctx** out, int dim, const stdg_options* opt, void* cuda_str
     *out = nullptr;
     if (dim != 2 && dim != 3) return STDG_EINVAL;
     if (opt->p < 1 || opt->p > (dim == 2 ? 4 : 3)) return STDG_EINVAL;
-    if (opt->p_gamma < 0 || opt->p_gamma > 3) return STDG_EINVAL;
+    if (opt->p_gamma < 0 || opt->p_gamma > 4) return STDG_EINVAL;
     if (opt->scheme != STDG_SCHEME_CN && opt->scheme != STDG_SCHEME_STDG) return STDG_EINVAL;
     if (opt->scheme == STDG_SCHEME_CN && opt->p_gamma != 0) return STDG_EINVAL;
     if (opt->precision != STDG_FP64 && opt->precision != STDG_MIXED_FP32) return STDG_EINVAL;
@@ -822,7 +825,7 @@ int stdg_locate_points(int dim, int64_t n_vert, const double* xyz, int64_t n_ele
 int stdg_reference_tables(int dim, int p, int p_gamma, double* Mref, double* W, double* T, double* S, double* kappa,
                           double* u) {
     if (dim != 2 && dim != 3) return STDG_EINVAL;
-    if (p < 1 || p > (dim == 2 ? 4 : 3) || p_gamma < 0 || p_gamma > 3) return STDG_EINVAL;
+    if (p < 1 || p > (dim == 2 ? 4 : 3) || p_gamma < 0 || p_gamma > 4) return STDG_EINVAL;
     RefTables rt;
     build_ref_tables(dim, p, p_gamma, &rt);
     const int n = rt.Nphi, g = rt.Ng;
@@ -843,6 +846,8 @@ int stdg_apply_preconditioner(stdg_ctx* c, double dt, const double* r, double* z
     int rc = precond_for_dt(c, dt);
     if (rc != STDG_OK) return rc;
     if (c->opt.preconditioner == 2 && !c->d_p2y) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_shots (or set a state) first");
+    if (c->opt.preconditioner == 2 && !c->d_pre2)
+        STDG_FAIL(c, STDG_ESTATE, "FP64 stencil blocks exist only in FP64 contexts (mixed precision keeps FP32 blocks)");
     double *dr = nullptr, *dz = nullptr;
     if ((rc = dev_alloc(c, (void**)&dr, sizeof(double) * c->nvel)) != STDG_OK) return rc;
     if ((rc = dev_alloc(c, (void**)&dz, sizeof(double) * c->nvel)) != STDG_OK) { dev_free(c, dr); return rc; }
@@ -865,6 +870,8 @@ int stdg_apply_preconditioner_device(stdg_ctx* c, double dt, const void* r_dev, 
     int rc = precond_for_dt(c, dt);
     if (rc != STDG_OK) return rc;
     if (c->opt.preconditioner == 2 && !c->d_p2y) STDG_FAIL(c, STDG_ESTATE, "call stdg_set_shots (or set a state) first");
+    if (!fp32 && c->opt.preconditioner == 2 && !c->d_pre2)
+        STDG_FAIL(c, STDG_ESTATE, "FP64 stencil blocks exist only in FP64 contexts (mixed precision keeps FP32 blocks)");
     if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
     if (fp32 && (rc = upload_material32(c)) != STDG_OK) return rc;
     const int ns = c->n_shots;
@@ -886,6 +893,7 @@ int stdg_time_kernel(stdg_ctx* c, double dt, int which, int fp32, int n, double*
     if (which == 1 && !c->opt.preconditioner) STDG_FAIL(c, STDG_ESTATE, "context created without a preconditioner");
     if (which == 2 && c->opt.preconditioner != 2) STDG_FAIL(c, STDG_ESTATE, "context created without the stencil preconditioner");
     if (which == 2 && fp32 && !c->d_pre2_32) STDG_FAIL(c, STDG_ESTATE, "FP32 stencil blocks exist only in mixed precision");
+    if (which == 2 && !fp32 && !c->d_pre2) STDG_FAIL(c, STDG_ESTATE, "FP64 stencil blocks exist only in FP64 contexts");
     if (which == 1 && fp32 && !c->d_preV32) STDG_FAIL(c, STDG_ESTATE, "FP32 block-Jacobi blocks exist only in mixed precision");
     int rc;
     if (fp32 && (rc = ensure_fp32(c)) != STDG_OK) return rc;
@@ -991,7 +999,7 @@ int stdg_autotune(stdg_ctx* c, double dt, stdg_tuning* out) {
         double best = 1e30;
         Tuning bt = c->tune;
         const bool mma = mixed && ns > 1 && c->d_pre2_mma;
-        for (int k : (mma ? std::vector<int>{1, 2} : std::vector<int>{1, 2, 4})) {
+        for (int k : (mma ? std::vector<int>{1, 2, 3} : std::vector<int>{1, 2, 4})) {
             if (mma) c->tune.mma_cps = k; else c->tune.pre2_wpb = k;
             const double ms = time([&]() -> cudaError_t {
                 if (mixed) return launch_pre2_local_batch(c, (const float*)dx, (const float*)dw, (float*)dy);

@@ -8,12 +8,13 @@
 //   A = T^T  (rows: shots, K: the N entries of t_e,s -- the shot-major vectors as they lie),
 //   B = S_e^{-T} (K: columns c of S_e^{-1}, N_mma: its rows r),
 //   D = Z^T  (TMEM lane = shot, column = r), written back to the shot-major z.
-// One MMA instruction has M = 128 rows: two elements e0, e0 + 1 with up to 64 shots each.
-// Their products are independent, so A is block-diagonal in (element, K) -- rows of e0
-// carry e0's t in K-cores 0..KC-1 and zeros in e1's K-cores, and vice versa -- and B stacks
-// the two S^{-T} blocks along K.  The zero half costs tensor-core time only; the kernel is
-// bound by HBM (the vectors of all shots plus one S^{-1} block per element), which is read
-// once for all shots instead of once per small group of shots.
+// Each element's product is its own MMA chain with M = 64 (up to 64 shots per group), N = the
+// rows of S^{-1} rounded up to 8, K = N (in steps of 8): for M = 64 the accumulator row r lies in
+// TMEM lane 32 (r / 16) + r % 16 (lanes 16..31 of each 32-lane sub-partition stay unused, as
+// measured on the GPU).  A CTA handles two consecutive elements per iteration (their S^{-1}
+// images are adjacent, one bulk copy), their accumulators in TMEM columns 0.. and 64..; the
+// kernel is bound by HBM (the vectors of all shots plus one S^{-1} block per element), which is
+// read once for all shots instead of once per small group of shots.
 //
 // Precision (kind::tf32, FP32 accumulation): S^{-1} is stored rounded to TF32 (a fixed,
 // linear perturbation of the preconditioner of relative size 2^-11, like any change of
@@ -44,16 +45,18 @@ struct MmaShape {
     static_assert(N % 4 == 0, "element block order must be a multiple of 4");
     static constexpr int NI = (N + 7) / 8;              // row cores of S^{-T} (MMA N side)
     static constexpr int KC = N / 4;                    // K cores per element
+    static constexpr int KCP = (KC + 1) / 2 * 2;        // ... rounded up to whole K steps (8 = 2 cores)
     static constexpr int IMG = KC * NI * 32;            // floats per element image
-    static constexpr int NMMA = (NI * 8 + 15) / 16 * 16;   // MMA N (multiple of 16 for M = 128)
-    static constexpr int M = 128, MI = 16;              // MMA rows: 2 elements x 64 shots
-    static constexpr int KI = 2 * KC;                   // K cores of one MMA group (two elements)
-    static constexpr int A_BYTES = KI * MI * 128;       // one A operand (K-core major)
-    static constexpr int B_BYTES = 2 * IMG * 4 + 128 * (NMMA / 8 - NI + 1);   // two images + slack
-    static constexpr int TMEM_COLS = NMMA <= 32 ? 32 : NMMA <= 64 ? 64 : NMMA <= 128 ? 128 : 256;
-    static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES;
-    static_assert(NMMA <= 256, "MMA N too large");
-    static_assert(((long)KI * MI * 128 / 16) < (1 << 14) && (NI * 128 / 16) < (1 << 14), "descriptor offsets");
+    static constexpr int NMMA = NI * 8;                 // MMA N (multiple of 8 for M = 64)
+    static constexpr int M = 64, MI = 8;                // MMA rows: up to 64 shots of one element
+    static constexpr int A_BYTES = KCP * MI * 128;      // one A operand of one element (K-core major)
+    // two images; an element's last K step may read one K-core column past the pair's images
+    static constexpr int B_BYTES = 2 * IMG * 4 + NI * 128 * (KCP - KC) + 16;
+    static constexpr int DCOL = 64;                     // TMEM column offset of the second element
+    static constexpr int TMEM_COLS = 128;
+    static constexpr int SMEM = 4 * A_BYTES + 2 * B_BYTES;   // A_hi, A_lo of two elements; two B stages
+    static_assert(NMMA <= 64 && NMMA % 8 == 0, "MMA N");
+    static_assert(((long)MI * 128 / 16) < (1 << 14) && (NI * 128 / 16) < (1 << 14), "descriptor offsets");
 };
 
 // shared-memory matrix descriptor: K-major, no swizzle (sm_100 descriptor version 1)
@@ -135,24 +138,24 @@ __global__ void pre2_mma_image_kernel(int64_t n_elem, const float* __restrict__ 
 }
 
 template <int N>
-__global__ void __launch_bounds__(128, 1) pre2_local_mma_kernel(int64_t n_elem, const float* __restrict__ img,
+__global__ void __launch_bounds__(128, 3) pre2_local_mma_kernel(int64_t n_elem, const float* __restrict__ img,
                                                                 const float* __restrict__ r, const int* __restrict__ ridx,
                                                                 int64_t ld, const float* __restrict__ w,
                                                                 float* __restrict__ z, int nshots, int64_t nvec,
                                                                 int* __restrict__ err) {
     using Sh = MmaShape<N>;
-    constexpr int NI = Sh::NI, KC = Sh::KC, IMG = Sh::IMG, MI = Sh::MI;
+    constexpr int NI = Sh::NI, KC = Sh::KC, KCP = Sh::KCP, IMG = Sh::IMG, MI = Sh::MI;
     constexpr uint32_t LBO_A = MI * 128, SBO_A = 128, LBO_B = NI * 128, SBO_B = 128;
     constexpr uint32_t IDESC = idesc_tf32(Sh::M, Sh::NMMA);
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[3];      // B stage 0, B stage 1, MMA done
     __shared__ uint32_t tmem_slot;
     if (ridx) r += (int64_t)(*ridx) * ld;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    unsigned char* A_hi = smraw;
-    unsigned char* A_lo = smraw + Sh::A_BYTES;
-    unsigned char* B0 = smraw + 2 * Sh::A_BYTES;   // stage 0; stage 1 follows at + B_BYTES
-    // zero both A operands (the other element's K-cores stay zero) and both B stages (slack)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // A operands: [element 0 hi, element 0 lo, element 1 hi, element 1 lo]
+    auto A_of = [&](int ek, int lo) { return smraw + (2 * ek + lo) * Sh::A_BYTES; };
+    unsigned char* B0 = smraw + 4 * Sh::A_BYTES;   // stage 0; stage 1 follows at + B_BYTES
+    // zero the A operands (their padding K-core stays zero) and both B stages (slack)
     for (int i = tid; i < Sh::SMEM / 16; i += blockDim.x) reinterpret_cast<float4*>(smraw)[i] = make_float4(0, 0, 0, 0);
     const uint32_t bar_b0 = smem_u32(&bars[0]), bar_b1 = smem_u32(&bars[1]), bar_m = smem_u32(&bars[2]);
     if (warp == 0) {
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(128, 1) pre2_local_mma_kernel(int64_t n_elem, 
         mbar_expect_tx(bar, bytes);
         bulk_g2s(smem_u32(B0 + st * Sh::B_BYTES), img + e0 * IMG, bytes, bar);
     };
-    // rows of this thread in A (loads) and in D (TMEM lane = tid): element ek, shot slot sl
+    // the row of A this thread fills: element ek of the pair, shot slot sl of the group
     const int ek = tid >> 6, sl = tid & 63;
     // per stage: phase bit (bit 0 / bit 1 of ph_b) and whether a copy is in flight (pend_b)
     uint32_t ph_b = 0, pend_b = 0, ph_m = 0;
@@ -193,6 +196,26 @@ __global__ void __launch_bounds__(128, 1) pre2_local_mma_kernel(int64_t n_elem, 
         if (tid == 0) issue_b(pair, 0);
         pend_b = 1u;
     }
+    // t = 2 r - w of the next (pair, shot group) is loaded into registers one item ahead, so
+    // that its memory latency overlaps the MMA and the epilogue of the current item
+    float4 tn[KC];
+    auto prefetch = [&](int64_t pp, int g) {
+        const int64_t e = 2 * pp + ek;
+        const int s = g * 64 + sl;
+        const bool valid = pp < npairs && e < n_elem && s < nshots;
+        const float4* r4 = reinterpret_cast<const float4*>(r + (int64_t)s * nvec + e * N);
+        const float4* w4 = reinterpret_cast<const float4*>(w + (int64_t)s * nvec + e * N);
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            float4 t = make_float4(0, 0, 0, 0);
+            if (valid) {
+                const float4 a = __ldg(r4 + k), b = __ldg(w4 + k);
+                t = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
+            }
+            tn[k] = t;
+        }
+    };
+    prefetch(pair, 0);
     for (; pair < npairs && ok; pair += gridDim.x) {
         const int64_t nxt = pair + gridDim.x;
         if (nxt < npairs) {
@@ -203,39 +226,40 @@ __global__ void __launch_bounds__(128, 1) pre2_local_mma_kernel(int64_t n_elem, 
         if (__syncthreads_and(got) == 0) { ok = false; break; }
         ph_b ^= 1u << st;
         pend_b &= ~(1u << st);
-        const int64_t e = 2 * pair + ek;
         for (int g = 0; g < ngroups; ++g) {
-            const int s = g * 64 + sl;
-            const bool valid = e < n_elem && s < nshots;
-            // ---- A: t = 2 r - w of (element e, shot s), split hi / lo, into this row of A
-            const float4* r4 = reinterpret_cast<const float4*>(r + (int64_t)s * nvec + e * N);
-            const float4* w4 = reinterpret_cast<const float4*>(w + (int64_t)s * nvec + e * N);
-            const uint32_t row_off = (uint32_t)((ek * 8 + (sl >> 3)) * 128 + (sl & 7) * 16);
+            float4 tc[KC];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) tc[k] = tn[k];
+            if (g + 1 < ngroups) prefetch(pair, g + 1);
+            else prefetch(pair + gridDim.x, 0);
+            // ---- A: t of (element e, shot s), split hi / lo, into row sl of element ek's operands
+            const uint32_t row_off = (uint32_t)((sl >> 3) * 128 + (sl & 7) * 16);
 #pragma unroll
             for (int k = 0; k < KC; ++k) {
-                float4 t = make_float4(0, 0, 0, 0);
-                if (valid) {
-                    const float4 a = __ldg(r4 + k), b = __ldg(w4 + k);
-                    t = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
-                }
+                const float4 t = tc[k];
                 const float4 hi = make_float4(tf32_round(t.x), tf32_round(t.y), tf32_round(t.z), tf32_round(t.w));
                 const float4 lo = make_float4(t.x - hi.x, t.y - hi.y, t.z - hi.z, t.w - hi.w);
-                const uint32_t off = (uint32_t)(ek * KC + k) * LBO_A + row_off;
-                *reinterpret_cast<float4*>(A_hi + off) = hi;
-                *reinterpret_cast<float4*>(A_lo + off) = lo;
+                const uint32_t off = (uint32_t)k * LBO_A + row_off;
+                *reinterpret_cast<float4*>(A_of(ek, 0) + off) = hi;
+                *reinterpret_cast<float4*>(A_of(ek, 1) + off) = lo;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fence_before();
             __syncthreads();
-            // ---- MMA: D = A_hi B + A_lo B over the KC K-steps of 2 cores
+            // ---- MMA per element: D_k = A_hi B_k + A_lo B_k over KCP / 2 K-steps of 2 cores
             if (tid == 0) {
                 fence_after();
-                const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bb = smem_u32(B0 + st * Sh::B_BYTES);
+                const uint32_t bb = smem_u32(B0 + st * Sh::B_BYTES);
 #pragma unroll 1
-                for (int k = 0; k < KC; ++k) {
-                    const uint64_t db = smem_desc(bb + 2 * k * LBO_B, LBO_B, SBO_B);
-                    mma_tf32(tmem, smem_desc(ah + 2 * k * LBO_A, LBO_A, SBO_A), db, IDESC, k > 0);
-                    mma_tf32(tmem, smem_desc(al + 2 * k * LBO_A, LBO_A, SBO_A), db, IDESC, 1);
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const uint32_t ah = smem_u32(A_of(k2, 0)), al = smem_u32(A_of(k2, 1));
+                    const uint32_t dt = tmem + (uint32_t)(k2 * Sh::DCOL);
+#pragma unroll 1
+                    for (int k = 0; k < KCP / 2; ++k) {
+                        const uint64_t db = smem_desc(bb + (k2 * KC + 2 * k) * LBO_B, LBO_B, SBO_B);
+                        mma_tf32(dt, smem_desc(ah + 2 * k * LBO_A, LBO_A, SBO_A), db, IDESC, k > 0);
+                        mma_tf32(dt, smem_desc(al + 2 * k * LBO_A, LBO_A, SBO_A), db, IDESC, 1);
+                    }
                 }
                 mma_commit(bar_m);
             }
@@ -243,24 +267,33 @@ __global__ void __launch_bounds__(128, 1) pre2_local_mma_kernel(int64_t n_elem, 
             if (__syncthreads_and(done) == 0) { ok = false; mma_pending = true; break; }
             ph_m ^= 1u;
             fence_after();
-            // ---- epilogue: this warp's 32 TMEM lanes, columns 0..N-1 -> z of (element, shot)
-            const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-            float4* z4 = reinterpret_cast<float4*>(z + (int64_t)s * nvec + e * N);
+            // ---- epilogue: lane 32 w + t (t < 16) of the accumulators holds shot 16 w + t of this
+            // group; both elements' rows (columns 0.. and 64..) go to z
+            {
+                const int so = g * 64 + warp * 16 + lane;
+                const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-            for (int c0 = 0; c0 + 8 <= N; c0 += 8) {
-                float v[8];
-                tmem_ld8(tl + c0, v);
-                tmem_wait_ld();
-                if (valid) {
-                    z4[c0 / 4] = make_float4(v[0], v[1], v[2], v[3]);
-                    z4[c0 / 4 + 1] = make_float4(v[4], v[5], v[6], v[7]);
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int64_t ee = 2 * pair + k2;
+                    const bool ok2 = lane < 16 && ee < n_elem && so < nshots;
+                    float4* z4 = reinterpret_cast<float4*>(z + (int64_t)so * nvec + ee * N);
+#pragma unroll
+                    for (int c0 = 0; c0 + 8 <= N; c0 += 8) {
+                        float v[8];
+                        tmem_ld8(tl + k2 * Sh::DCOL + c0, v);
+                        tmem_wait_ld();
+                        if (ok2) {
+                            z4[c0 / 4] = make_float4(v[0], v[1], v[2], v[3]);
+                            z4[c0 / 4 + 1] = make_float4(v[4], v[5], v[6], v[7]);
+                        }
+                    }
+                    if constexpr (N % 8 != 0) {
+                        float v[4];
+                        tmem_ld4(tl + k2 * Sh::DCOL + (N / 8) * 8, v);
+                        tmem_wait_ld();
+                        if (ok2) z4[N / 4 - 1] = make_float4(v[0], v[1], v[2], v[3]);
+                    }
                 }
-            }
-            if constexpr (N % 8 != 0) {
-                float v[4];
-                tmem_ld4(tl + (N / 8) * 8, v);
-                tmem_wait_ld();
-                if (valid) z4[N / 4 - 1] = make_float4(v[0], v[1], v[2], v[3]);
             }
             fence_before();
             __syncthreads();   // TMEM and both A operands are free for the next group

@@ -12,7 +12,7 @@
 namespace stdg {
 
 constexpr int kMaxNP = 20;   // N_phi = N_psi <= 20 (3D p=3, 2D p=4: 15)
-constexpr int kMaxNG = 4;    // N_gamma <= 4
+constexpr int kMaxNG = 5;    // N_gamma <= 5
 
 // Reference-element and time-basis tables, built on the host (host_setup.cpp) and
 // copied to the device once per context.
@@ -81,7 +81,7 @@ struct Tuning {
     int face_wpb = 4;     // face kernels: warps per block (1, 2, 4)
     int face_bpsm = 16;   // single-shot bulk-copy face kernel: grid cap, blocks per SM
     int pre2_wpb = 4;     // CUDA-core stencil local step: warps per block (1, 2, 4)
-    int mma_cps = 2;      // tensor-core stencil local step: CTAs per SM (1, 2)
+    int mma_cps = 3;      // tensor-core stencil local step: CTAs per SM (1, 2, 3)
 };
 }  // namespace stdg
 

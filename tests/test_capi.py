@@ -40,7 +40,7 @@ def _opts(**kw):
 def test_create_rejects_bad_options_before_touching_the_device():
     # every rejection happens on the host, before a stream or device buffer exists
     lib = _lib()
-    bad = [dict(p=0), dict(p=5), dict(p_gamma=-1), dict(p_gamma=4), dict(scheme=2), dict(scheme=0, p_gamma=1),
+    bad = [dict(p=0), dict(p=5), dict(p_gamma=-1), dict(p_gamma=5), dict(scheme=2), dict(scheme=0, p_gamma=1),
            dict(precision=2), dict(preconditioner=3), dict(preconditioner=-1), dict(rel_tol=0.0),
            dict(rel_tol=float("nan")), dict(max_iters=0)]
     for kw in bad:

@@ -64,7 +64,7 @@ def _run(p, n):
     s.close()
     # L2 error of each velocity component with the element mass matrices |J_i| M_ref
     Mref = reference_tables(2, p, p)["Mref"]
-    X = xyz[ev]
+    X = synth.unwrap_elements(xyz, ev, per)          # elements across the periodic seam unwrapped
     detJ = np.abs((X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1]) - (X[:, 1, 1] - X[:, 0, 1]) * (X[:, 2, 0] - X[:, 0, 0]))
     e = v - vT
     err = np.sqrt(np.einsum("i,ikn,nm,ikm->k", detJ, e, Mref, e))
