@@ -293,6 +293,7 @@ int stdg_time_kernel(stdg_ctx* ctx, double dt, int which, int fp32, int n, doubl
 typedef struct {
     int face_warps_per_block;   /* face kernels of the operator: warps per block (1, 2, 4)            */
     int face_blocks_per_sm;     /* single-shot bulk-copy face kernel: grid cap, blocks per SM         */
+    int face_register_cap;      /* single-shot bulk-copy face kernel: 1 register cap for occupancy, 0 none */
     int pre2_warps_per_block;   /* CUDA-core element-local step of the stencil preconditioner         */
     int mma_ctas_per_sm;        /* tensor-core element-local step (a batch of shots): CTAs per SM (1-3) */
     double face_ms, pre2_ms;    /* best time per launch of the tuned face kernel / local step (0: not tuned) */
@@ -301,7 +302,7 @@ typedef struct {
 
 /* Autotuner: times every candidate launch shape of the hot kernels this context runs for slab
  * size dt -- the FP32 face kernel (mixed precision; warps per block 1/2/4 and, for one shot, the
- * grid cap 8/16/32/64 blocks per SM) and the element-local step of the stencil preconditioner
+ * grid cap 8/16/32/64 blocks per SM and the kernel compiled with or without a register cap) and the element-local step of the stencil preconditioner
  * (warps per block, or CTAs per SM of the tensor-core kernel) -- on the context's own mesh and
  * shot count (zero vectors, 10 launches each, CUDA events) and keeps the fastest for every later
  * launch; step graphs captured before are dropped and re-captured.  `out` (may be NULL) receives

@@ -33,7 +33,8 @@ class stdg_stats(C.Structure):
 
 
 class stdg_tuning(C.Structure):
-    _fields_ = [("face_warps_per_block", C.c_int), ("face_blocks_per_sm", C.c_int), ("pre2_warps_per_block", C.c_int),
+    _fields_ = [("face_warps_per_block", C.c_int), ("face_blocks_per_sm", C.c_int), ("face_register_cap", C.c_int),
+                ("pre2_warps_per_block", C.c_int),
                 ("mma_ctas_per_sm", C.c_int), ("face_ms", C.c_double), ("pre2_ms", C.c_double), ("candidates", C.c_int)]
 
     def as_dict(self):

@@ -983,15 +983,17 @@ int stdg_autotune(stdg_ctx* c, double dt, stdg_tuning* out) {
     if (mixed) {
         double best = 1e30;
         Tuning bt = c->tune;
-        for (int wpb : {1, 2, 4})
-            for (int bpsm : (ns == 1 ? std::vector<int>{8, 16, 32, 64} : std::vector<int>{16})) {
-                c->tune.face_wpb = wpb;
-                c->tune.face_bpsm = bpsm;
-                const double ms = time([&]() {
-                    return launch_apply32(c, dt, (const float*)dx, (float*)dy, 1.0, nullptr, 0, ns);
-                });
-                if (ms < best) { best = ms; bt = c->tune; }
-            }
+        for (int cap : (ns == 1 ? std::vector<int>{1, 0} : std::vector<int>{1}))
+            for (int wpb : {1, 2, 4})
+                for (int bpsm : (ns == 1 ? std::vector<int>{8, 16, 32, 64} : std::vector<int>{16})) {
+                    c->tune.face_cap = cap;
+                    c->tune.face_wpb = wpb;
+                    c->tune.face_bpsm = bpsm;
+                    const double ms = time([&]() {
+                        return launch_apply32(c, dt, (const float*)dx, (float*)dy, 1.0, nullptr, 0, ns);
+                    });
+                    if (ms < best) { best = ms; bt = c->tune; }
+                }
         c->tune = bt;
         res.face_ms = best;
     }
@@ -1019,6 +1021,7 @@ int stdg_autotune(stdg_ctx* c, double dt, stdg_tuning* out) {
     solver_invalidate_graph(c);   // graphs keep the launch shapes they were captured with
     res.face_warps_per_block = c->tune.face_wpb;
     res.face_blocks_per_sm = c->tune.face_bpsm;
+    res.face_register_cap = c->tune.face_cap;
     res.pre2_warps_per_block = c->tune.pre2_wpb;
     res.mma_ctas_per_sm = c->tune.mma_cps;
     res.candidates = tried;

@@ -218,12 +218,13 @@ struct FaceTma {
     static constexpr int SZ_T = round_up(NS * NG * NP, 4);
     static constexpr int SZ_H = round_up(NS * NG * NP, 4);
     static constexpr int PER_WARP = round_up(2 * STAGE + SZ_G + SZ_T + SZ_H, 16 / (int)sizeof(R));
-    // resident blocks of 4 warps requested per SM: a register cap where it costs no spills
-    static constexpr int MIN_BLOCKS = (DIM == 2 && NP == 6) ? 6 : (DIM == 2 && NP == 10) ? 6 : 1;
+    // resident blocks of 4 warps requested per SM when the register cap is on (the autotuner
+    // times the kernel with and without it)
+    static constexpr int MIN_BLOCKS = (DIM == 2 && NP == 6) ? 6 : (DIM == 2 && NP == 10) ? 6 : (DIM == 3 && NP == 10) ? 4 : 2;
 };
 
-template <int DIM, int NP, int NG, typename R>
-__global__ void __launch_bounds__(128, (FaceTma<DIM, NP, NG, R>::MIN_BLOCKS)) face_apply_tma_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+template <int DIM, int NP, int NG, typename R, int MINB>
+__global__ void __launch_bounds__(128, MINB) face_apply_tma_kernel(int64_t n_face, const int32_t* __restrict__ fl,
                                                              const int32_t* __restrict__ fr, const R* __restrict__ D,
                                                              const R* __restrict__ lamf, const R* __restrict__ muf,
                                                              const RefTables* __restrict__ rtp, const R* __restrict__ x,
@@ -384,10 +385,14 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
     if (nshots == 1 && aligned && c->d_err) {
         const int wpb = c->tune.face_wpb;   // <= 4: the kernel's launch bounds and its per-warp barriers
         const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
-        cudaFuncSetAttribute(face_apply_tma_kernel<DIM, NP, NG, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
-        face_apply_tma_kernel<DIM, NP, NG, R><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
-            c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, c->d_err);
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf,
+                                                                 c->d_rt, x, xidx, ld, y, (R)scale, c->d_err);
+        };
+        if (c->tune.face_cap) go(face_apply_tma_kernel<DIM, NP, NG, R, T::MIN_BLOCKS>);
+        else go(face_apply_tma_kernel<DIM, NP, NG, R, 1>);
         note_launch(c);
         return cudaGetLastError();
     }
