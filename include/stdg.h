@@ -295,7 +295,7 @@ typedef struct {
     int face_blocks_per_sm;     /* single-shot bulk-copy face kernel: grid cap, blocks per SM         */
     int face_register_cap;      /* single-shot bulk-copy face kernel: 1 register cap for occupancy, 0 none */
     int pre2_warps_per_block;   /* CUDA-core element-local step of the stencil preconditioner         */
-    int mma_ctas_per_sm;        /* tensor-core element-local step (a batch of shots): CTAs per SM (1-3) */
+    int mma_ctas_per_sm;        /* tensor-core element-local step (a batch of shots): CTAs per SM (1, 2) */
     double face_ms, pre2_ms;    /* best time per launch of the tuned face kernel / local step (0: not tuned) */
     int candidates;             /* configurations timed                                               */
 } stdg_tuning;

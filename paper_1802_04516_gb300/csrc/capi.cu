@@ -1001,7 +1001,7 @@ int stdg_autotune(stdg_ctx* c, double dt, stdg_tuning* out) {
         double best = 1e30;
         Tuning bt = c->tune;
         const bool mma = mixed && ns > 1 && c->d_pre2_mma;
-        for (int k : (mma ? std::vector<int>{1, 2, 3} : std::vector<int>{1, 2, 4})) {
+        for (int k : (mma ? std::vector<int>{1, 2} : std::vector<int>{1, 2, 4})) {
             if (mma) c->tune.mma_cps = k; else c->tune.pre2_wpb = k;
             const double ms = time([&]() -> cudaError_t {
                 if (mixed) return launch_pre2_local_batch(c, (const float*)dx, (const float*)dw, (float*)dy);

@@ -12,9 +12,11 @@
 // rows of S^{-1} rounded up to 8, K = N (in steps of 8): for M = 64 the accumulator row r lies in
 // TMEM lane 32 (r / 16) + r % 16 (lanes 16..31 of each 32-lane sub-partition stay unused, as
 // measured on the GPU).  A CTA handles two consecutive elements per iteration (their S^{-1}
-// images are adjacent, one bulk copy), their accumulators in TMEM columns 0.. and 64..; the
-// kernel is bound by HBM (the vectors of all shots plus one S^{-1} block per element), which is
-// read once for all shots instead of once per small group of shots.
+// images are adjacent, one bulk copy), their accumulators in TMEM columns 0.. and 64..; each
+// thread stages the r and w rows of its (element, shot) for the next iteration with cp.async
+// while the current iteration's MMAs and epilogue run.  The kernel is bound by HBM (the
+// vectors of all shots plus one S^{-1} block per element), which is read once for all shots
+// instead of once per small group of shots.
 //
 // Precision (kind::tf32, FP32 accumulation): S^{-1} is stored rounded to TF32 (a fixed,
 // linear perturbation of the preconditioner of relative size 2^-11, like any change of
@@ -54,8 +56,11 @@ struct MmaShape {
     static constexpr int B_BYTES = 2 * IMG * 4 + NI * 128 * (KCP - KC) + 16;
     static constexpr int DCOL = 64;                     // TMEM column offset of the second element
     static constexpr int TMEM_COLS = 128;
-    static constexpr int SMEM = 4 * A_BYTES + 2 * B_BYTES;   // A_hi, A_lo of two elements; two B stages
+    static constexpr int ROW = 2 * N + 4;               // staged floats per thread: r and w of its row, padded
+    static constexpr int STAGE = 128 * ROW * 4;         // per-thread staging rows of the next item
+    static constexpr int SMEM = 4 * A_BYTES + 2 * B_BYTES + STAGE;   // A_hi, A_lo of two elements; two B stages
     static_assert(NMMA <= 64 && NMMA % 8 == 0, "MMA N");
+    static_assert((ROW * 4) % 16 == 0, "staging rows of whole 16-byte chunks");
     static_assert(((long)MI * 128 / 16) < (1 << 14) && (NI * 128 / 16) < (1 << 14), "descriptor offsets");
 };
 
@@ -94,15 +99,20 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
-// 8 consecutive TMEM columns of this warp's 32 lanes (one lane per thread)
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-    uint32_t u[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
-                 : "r"(taddr)
-                 : "memory");
+// 32 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t u[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+          "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
+          "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
+          "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(u[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
 }
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
     uint32_t u[4];
@@ -116,6 +126,13 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 constexpr long kPoll = 1L << 24;
+
+// 16-byte asynchronous global -> shared copy (L2 only), zero-filled when `bytes` is 0
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 }  // namespace
 
@@ -138,7 +155,7 @@ __global__ void pre2_mma_image_kernel(int64_t n_elem, const float* __restrict__ 
 }
 
 template <int N>
-__global__ void __launch_bounds__(128, 3) pre2_local_mma_kernel(int64_t n_elem, const float* __restrict__ img,
+__global__ void __launch_bounds__(128, 2) pre2_local_mma_kernel(int64_t n_elem, const float* __restrict__ img,
                                                                 const float* __restrict__ r, const int* __restrict__ ridx,
                                                                 int64_t ld, const float* __restrict__ w,
                                                                 float* __restrict__ z, int nshots, int64_t nvec,
@@ -196,24 +213,23 @@ __global__ void __launch_bounds__(128, 3) pre2_local_mma_kernel(int64_t n_elem, 
         if (tid == 0) issue_b(pair, 0);
         pend_b = 1u;
     }
-    // t = 2 r - w of the next (pair, shot group) is loaded into registers one item ahead, so
-    // that its memory latency overlaps the MMA and the epilogue of the current item
-    float4 tn[KC];
+    // r and w of the next (pair, shot group) are copied asynchronously (cp.async) into this
+    // thread's own staging row while the current item's MMA and epilogue run; each thread
+    // reads back only what it copied, so completion needs no barrier
+    float* my_row = reinterpret_cast<float*>(B0 + 2 * Sh::B_BYTES) + tid * Sh::ROW;
     auto prefetch = [&](int64_t pp, int g) {
         const int64_t e = 2 * pp + ek;
         const int s = g * 64 + sl;
         const bool valid = pp < npairs && e < n_elem && s < nshots;
-        const float4* r4 = reinterpret_cast<const float4*>(r + (int64_t)s * nvec + e * N);
-        const float4* w4 = reinterpret_cast<const float4*>(w + (int64_t)s * nvec + e * N);
+        const float* rs = valid ? r + (int64_t)s * nvec + e * N : r;
+        const float* ws = valid ? w + (int64_t)s * nvec + e * N : w;
+        const uint32_t d0 = smem_u32(my_row), nb = valid ? 16u : 0u;
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-            float4 t = make_float4(0, 0, 0, 0);
-            if (valid) {
-                const float4 a = __ldg(r4 + k), b = __ldg(w4 + k);
-                t = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
-            }
-            tn[k] = t;
+            cp_async16(d0 + 16 * k, rs + 4 * k, nb);
+            cp_async16(d0 + 16 * (KC + k), ws + 4 * k, nb);
         }
+        cp_async_commit();
     };
     prefetch(pair, 0);
     for (; pair < npairs && ok; pair += gridDim.x) {
@@ -228,8 +244,13 @@ __global__ void __launch_bounds__(128, 3) pre2_local_mma_kernel(int64_t n_elem, 
         pend_b &= ~(1u << st);
         for (int g = 0; g < ngroups; ++g) {
             float4 tc[KC];
+            cp_async_wait_all();
 #pragma unroll
-            for (int k = 0; k < KC; ++k) tc[k] = tn[k];
+            for (int k = 0; k < KC; ++k) {
+                const float4 a = reinterpret_cast<const float4*>(my_row)[k];
+                const float4 b = reinterpret_cast<const float4*>(my_row)[KC + k];
+                tc[k] = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
+            }
             if (g + 1 < ngroups) prefetch(pair, g + 1);
             else prefetch(pair + gridDim.x, 0);
             // ---- A: t of (element e, shot s), split hi / lo, into row sl of element ek's operands
@@ -277,21 +298,22 @@ __global__ void __launch_bounds__(128, 3) pre2_local_mma_kernel(int64_t n_elem, 
                     const int64_t ee = 2 * pair + k2;
                     const bool ok2 = lane < 16 && ee < n_elem && so < nshots;
                     float4* z4 = reinterpret_cast<float4*>(z + (int64_t)so * nvec + ee * N);
+                    // all N columns of this element in one or two loads, one wait
+                    static_assert(N <= 36, "epilogue loads 32 + 4 columns");
+                    float v[36];
+                    tmem_ld32(tl + k2 * Sh::DCOL, v);
+                    if constexpr (N > 32) {
+                        float v4[4];
+                        tmem_ld4(tl + k2 * Sh::DCOL + 32, v4);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int c0 = 0; c0 + 8 <= N; c0 += 8) {
-                        float v[8];
-                        tmem_ld8(tl + k2 * Sh::DCOL + c0, v);
+                        for (int i = 0; i < 4; ++i) v[32 + i] = v4[i];
+                    } else {
                         tmem_wait_ld();
-                        if (ok2) {
-                            z4[c0 / 4] = make_float4(v[0], v[1], v[2], v[3]);
-                            z4[c0 / 4 + 1] = make_float4(v[4], v[5], v[6], v[7]);
-                        }
                     }
-                    if constexpr (N % 8 != 0) {
-                        float v[4];
-                        tmem_ld4(tl + k2 * Sh::DCOL + (N / 8) * 8, v);
-                        tmem_wait_ld();
-                        if (ok2) z4[N / 4 - 1] = make_float4(v[0], v[1], v[2], v[3]);
+                    if (ok2) {
+#pragma unroll
+                        for (int q = 0; q < N / 4; ++q) z4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     }
                 }
             }
@@ -311,6 +333,7 @@ __global__ void __launch_bounds__(128, 3) pre2_local_mma_kernel(int64_t n_elem, 
             if (!drained) atomicExch(err, 2);
         }
     }
+    cp_async_wait_all();   // no copy into shared memory outlives the CTA
     fence_before();
     __syncthreads();
     if (warp == 0) {

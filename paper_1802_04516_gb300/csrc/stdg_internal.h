@@ -82,7 +82,7 @@ struct Tuning {
     int face_bpsm = 16;   // single-shot bulk-copy face kernel: grid cap, blocks per SM
     int face_cap = 1;     // single-shot bulk-copy face kernel: register cap for occupancy (1) or none (0)
     int pre2_wpb = 4;     // CUDA-core stencil local step: warps per block (1, 2, 4)
-    int mma_cps = 3;      // tensor-core stencil local step: CTAs per SM (1, 2, 3)
+    int mma_cps = 2;      // tensor-core stencil local step: CTAs per SM (1, 2)
 };
 }  // namespace stdg
 

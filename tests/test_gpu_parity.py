@@ -533,7 +533,7 @@ def test_autotuned_launch_shapes_keep_the_results(shots):
     t = tuned.autotune(w.dt)
     print("autotune", shots, "shots:", t)
     assert t["face_warps_per_block"] in (1, 2, 4) and t["pre2_warps_per_block"] in (1, 2, 4)
-    assert t["mma_ctas_per_sm"] in (1, 2, 3) and t["candidates"] >= 4 and t["face_ms"] > 0 and t["pre2_ms"] > 0
+    assert t["mma_ctas_per_sm"] in (1, 2) and t["candidates"] >= 4 and t["face_ms"] > 0 and t["pre2_ms"] > 0
     assert tuned.step(w.dt, 2)["status"] == 0
     _, ref = _oracle_per_shot(w, 2)
     for k in range(shots):
