@@ -56,11 +56,15 @@ struct MmaShape {
     static constexpr int B_BYTES = 2 * IMG * 4 + NI * 128 * (KCP - KC) + 16;
     static constexpr int DCOL = 64;                     // TMEM column offset of the second element
     static constexpr int TMEM_COLS = 128;
-    static constexpr int ROW = 2 * N + 4;               // staged floats per thread: r and w of its row, padded
-    static constexpr int STAGE = 128 * ROW * 4;         // per-thread staging rows of the next item
+    // staging of one item's vectors, per shot row: r of both elements, then w of both (4N floats
+    // + 4 of padding: rows 16-byte aligned and spread over the banks)
+    static constexpr int ROW = 4 * N + 4;
+    static constexpr int STAGE = 64 * ROW * 4;
+    static constexpr int ZROW = 2 * N + 4;              // z staging row (both elements), in the A area
     static constexpr int SMEM = 4 * A_BYTES + 2 * B_BYTES + STAGE;   // A_hi, A_lo of two elements; two B stages
+    static_assert(64 * ZROW * 4 <= 4 * A_BYTES, "z staging fits in the A operands");
     static_assert(NMMA <= 64 && NMMA % 8 == 0, "MMA N");
-    static_assert((ROW * 4) % 16 == 0, "staging rows of whole 16-byte chunks");
+    static_assert((ROW * 4) % 16 == 0 && (ZROW * 4) % 16 == 0, "staging rows of whole 16-byte chunks");
     static_assert(((long)MI * 128 / 16) < (1 << 14) && (NI * 128 / 16) < (1 << 14), "descriptor offsets");
 };
 
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(128, 2) pre2_local_mma_kernel(int64_t n_elem, 
     // A operands: [element 0 hi, element 0 lo, element 1 hi, element 1 lo]
     auto A_of = [&](int ek, int lo) { return smraw + (2 * ek + lo) * Sh::A_BYTES; };
     unsigned char* B0 = smraw + 4 * Sh::A_BYTES;   // stage 0; stage 1 follows at + B_BYTES
-    // zero the A operands (their padding K-core stays zero) and both B stages (slack)
+    // zero the A operands and both B stages (the slack past the images stays zero)
     for (int i = tid; i < Sh::SMEM / 16; i += blockDim.x) reinterpret_cast<float4*>(smraw)[i] = make_float4(0, 0, 0, 0);
     const uint32_t bar_b0 = smem_u32(&bars[0]), bar_b1 = smem_u32(&bars[1]), bar_m = smem_u32(&bars[2]);
     if (warp == 0) {
@@ -213,24 +217,25 @@ __global__ void __launch_bounds__(128, 2) pre2_local_mma_kernel(int64_t n_elem, 
         if (tid == 0) issue_b(pair, 0);
         pend_b = 1u;
     }
-    // r and w of the next (pair, shot group) are copied asynchronously (cp.async) into this
-    // thread's own staging row while the current item's MMA and epilogue run; each thread
-    // reads back only what it copied, so completion needs no barrier
-    float* my_row = reinterpret_cast<float*>(B0 + 2 * Sh::B_BYTES) + tid * Sh::ROW;
+    // The vectors of an item -- for each of up to 64 shots, the 2 x N contiguous values of the
+    // pair's two elements in r and in w -- are copied with cp.async into the staging rows,
+    // warp-coalesced (consecutive threads take consecutive 16-byte chunks of a row), one item
+    // ahead: the copies of the next item overlap the MMA and the epilogue of the current one.
+    float* stage = reinterpret_cast<float*>(B0 + 2 * Sh::B_BYTES);
+    constexpr int CH = 2 * N / 4;                       // 16-byte chunks per row and vector
     auto prefetch = [&](int64_t pp, int g) {
-        const int64_t e = 2 * pp + ek;
-        const int s = g * 64 + sl;
-        const bool valid = pp < npairs && e < n_elem && s < nshots;
-        const float* rs = valid ? r + (int64_t)s * nvec + e * N : r;
-        const float* ws = valid ? w + (int64_t)s * nvec + e * N : w;
-        const uint32_t d0 = smem_u32(my_row), nb = valid ? 16u : 0u;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            cp_async16(d0 + 16 * k, rs + 4 * k, nb);
-            cp_async16(d0 + 16 * (KC + k), ws + 4 * k, nb);
+        const int64_t e0 = 2 * pp;
+        const int nch = pp < npairs ? (e0 + 1 < n_elem ? CH : CH / 2) : 0;   // valid chunks of a row
+        for (int c = tid; c < 64 * 2 * CH; c += blockDim.x) {
+            const int row = c / (2 * CH), q = c % (2 * CH), vec = q / CH, part = q % CH;
+            const int s = g * 64 + row;
+            const bool valid = part < nch && s < nshots;
+            const float* src = valid ? (vec ? w : r) + (int64_t)s * nvec + e0 * N + 4 * part : r;
+            cp_async16(smem_u32(stage + row * Sh::ROW + vec * 2 * N + 4 * part), src, valid ? 16u : 0u);
         }
         cp_async_commit();
     };
+    float* zst = reinterpret_cast<float*>(smraw);       // z staging, aliasing the A operands after the MMA
     prefetch(pair, 0);
     for (; pair < npairs && ok; pair += gridDim.x) {
         const int64_t nxt = pair + gridDim.x;
@@ -243,30 +248,35 @@ __global__ void __launch_bounds__(128, 2) pre2_local_mma_kernel(int64_t n_elem, 
         ph_b ^= 1u << st;
         pend_b &= ~(1u << st);
         for (int g = 0; g < ngroups; ++g) {
-            float4 tc[KC];
             cp_async_wait_all();
+            __syncthreads();   // every thread's copies of this item have landed
+            // ---- A: t = 2 r - w of (element ek, shot sl), split hi / lo, into row sl of its operands
+            {
+                const float4* rr = reinterpret_cast<const float4*>(stage + sl * Sh::ROW + ek * N);
+                const float4* wr = reinterpret_cast<const float4*>(stage + sl * Sh::ROW + 2 * N + ek * N);
+                const uint32_t row_off = (uint32_t)((sl >> 3) * 128 + (sl & 7) * 16);
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const float4 a = reinterpret_cast<const float4*>(my_row)[k];
-                const float4 b = reinterpret_cast<const float4*>(my_row)[KC + k];
-                tc[k] = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
-            }
-            if (g + 1 < ngroups) prefetch(pair, g + 1);
-            else prefetch(pair + gridDim.x, 0);
-            // ---- A: t of (element e, shot s), split hi / lo, into row sl of element ek's operands
-            const uint32_t row_off = (uint32_t)((sl >> 3) * 128 + (sl & 7) * 16);
+                for (int k = 0; k < KC; ++k) {
+                    const float4 a = rr[k], b = wr[k];
+                    const float4 t = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
+                    const float4 hi = make_float4(tf32_round(t.x), tf32_round(t.y), tf32_round(t.z), tf32_round(t.w));
+                    const float4 lo = make_float4(t.x - hi.x, t.y - hi.y, t.z - hi.z, t.w - hi.w);
+                    const uint32_t off = (uint32_t)k * LBO_A + row_off;
+                    *reinterpret_cast<float4*>(A_of(ek, 0) + off) = hi;
+                    *reinterpret_cast<float4*>(A_of(ek, 1) + off) = lo;
+                }
 #pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const float4 t = tc[k];
-                const float4 hi = make_float4(tf32_round(t.x), tf32_round(t.y), tf32_round(t.z), tf32_round(t.w));
-                const float4 lo = make_float4(t.x - hi.x, t.y - hi.y, t.z - hi.z, t.w - hi.w);
-                const uint32_t off = (uint32_t)k * LBO_A + row_off;
-                *reinterpret_cast<float4*>(A_of(ek, 0) + off) = hi;
-                *reinterpret_cast<float4*>(A_of(ek, 1) + off) = lo;
+                for (int k = KC; k < KCP; ++k) {   // the padding K-core (the z staging used this area)
+                    const uint32_t off = (uint32_t)k * LBO_A + row_off;
+                    *reinterpret_cast<float4*>(A_of(ek, 0) + off) = make_float4(0, 0, 0, 0);
+                    *reinterpret_cast<float4*>(A_of(ek, 1) + off) = make_float4(0, 0, 0, 0);
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fence_before();
-            __syncthreads();
+            __syncthreads();   // A complete; the staging rows are free for the next item
+            if (g + 1 < ngroups) prefetch(pair, g + 1);
+            else prefetch(pair + gridDim.x, 0);
             // ---- MMA per element: D_k = A_hi B_k + A_lo B_k over KCP / 2 K-steps of 2 cores
             if (tid == 0) {
                 fence_after();
@@ -288,17 +298,13 @@ __global__ void __launch_bounds__(128, 2) pre2_local_mma_kernel(int64_t n_elem, 
             if (__syncthreads_and(done) == 0) { ok = false; mma_pending = true; break; }
             ph_m ^= 1u;
             fence_after();
-            // ---- epilogue: lane 32 w + t (t < 16) of the accumulators holds shot 16 w + t of this
-            // group; both elements' rows (columns 0.. and 64..) go to z
+            // ---- epilogue: lane 32 w + t (t < 16) of the accumulators holds shot 16 w + t of the
+            // group; both elements' rows (TMEM columns 0.. and 64..) go to the z staging rows ...
             {
-                const int so = g * 64 + warp * 16 + lane;
                 const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+                float* zr = zst + (warp * 16 + (lane & 15)) * Sh::ZROW;
 #pragma unroll
                 for (int k2 = 0; k2 < 2; ++k2) {
-                    const int64_t ee = 2 * pair + k2;
-                    const bool ok2 = lane < 16 && ee < n_elem && so < nshots;
-                    float4* z4 = reinterpret_cast<float4*>(z + (int64_t)so * nvec + ee * N);
-                    // all N columns of this element in one or two loads, one wait
                     static_assert(N <= 36, "epilogue loads 32 + 4 columns");
                     float v[36];
                     tmem_ld32(tl + k2 * Sh::DCOL, v);
@@ -311,14 +317,28 @@ __global__ void __launch_bounds__(128, 2) pre2_local_mma_kernel(int64_t n_elem, 
                     } else {
                         tmem_wait_ld();
                     }
-                    if (ok2) {
+                    if (lane < 16) {
 #pragma unroll
-                        for (int q = 0; q < N / 4; ++q) z4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        for (int q = 0; q < N / 4; ++q)
+                            reinterpret_cast<float4*>(zr + k2 * N)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     }
                 }
             }
+            __syncthreads();
+            // ... and from there to z, warp-coalesced (2 N contiguous values per shot row)
+            {
+                const int64_t e0 = 2 * pair;
+                const int nch = e0 + 1 < n_elem ? CH : CH / 2;
+                for (int c = tid; c < 64 * CH; c += blockDim.x) {
+                    const int row = c / CH, part = c % CH;
+                    const int s = g * 64 + row;
+                    if (part < nch && s < nshots)
+                        *reinterpret_cast<float4*>(z + (int64_t)s * nvec + e0 * N + 4 * part) =
+                            *reinterpret_cast<const float4*>(zst + row * Sh::ZROW + 4 * part);
+                }
+            }
             fence_before();
-            __syncthreads();   // TMEM and both A operands are free for the next group
+            __syncthreads();   // TMEM and the A area are free for the next group
         }
         st ^= 1;
     }
