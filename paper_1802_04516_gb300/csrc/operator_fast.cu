@@ -44,10 +44,20 @@ struct FaceReg {
     static constexpr int SZ_G = round_up(DIM * DIM * NG * NP, W);   // g[k][l][b][m]
     static constexpr int SZ_T = round_up(NS * NG * NP, W);          // t[c][b][m]
     static constexpr int SZ_H = NS * NG * NPP;           // rows (c,b) of h
-    static constexpr int PER_WARP = SZ_V + SZ_G + SZ_T + SZ_H;   // per shot in flight
+    static constexpr int PER_WARP = 2 * SZ_V + SZ_G + SZ_T + SZ_H;   // per shot in flight (two value buffers)
     // several shots: two per warp (one per half-warp) when a column and a row of D~ fit in 16 lanes
     static constexpr int HALVES = (DIM * NP <= 16 && 2 * NP <= 16) ? 2 : 1;
 };
+
+// element-sized asynchronous global -> shared copy (zero-filled when `bytes` is 0)
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* dst, const R* src, bool on) {
+    const uint32_t d = smem_u32(dst);
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(on ? 4u : 0u) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(on ? 8u : 0u) : "memory");
+}
 
 // acc + sum_{n<NP} a[n] row[n] for a broadcast shared-memory row.  FP32 with NP even: the
 // row starts on an 8-byte boundary, so pairs (n, n+1) come in one 8-byte load and go through
@@ -93,11 +103,11 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
     for (int t = threadIdx.x; t < NG * NG; t += blockDim.x) sS[t] = (R)rtp->S[t];
     // with HALVES = 2 each half-warp works on its own shot (same D~ registers, own buffers)
     const int hv = lane / LANES, li = lane % LANES;
-    R* sV = sm + (warp * HALVES + hv) * F::PER_WARP;   // [s][k][b][n] rows padded
-    R* sG = sV + F::SZ_V;              // [k][l][b][m]
+    R* sV0 = sm + (warp * HALVES + hv) * F::PER_WARP;   // [s][k][b][n] rows padded, two buffers
+    R* sG = sV0 + 2 * F::SZ_V;         // [k][l][b][m]
     R* sT = sG + F::SZ_G;              // [c][b][m]
     R* sH = sT + F::SZ_T;              // [c][b][m] rows padded
-    for (int t = li; t < F::PER_WARP; t += LANES) sV[t] = (R)0;   // padding stays zero
+    for (int t = li; t < F::PER_WARP; t += LANES) sV0[t] = (R)0;   // padding stays zero
     __syncthreads();
     const bool gl = li < DIM * NP;            // gather lane: column (gl_l, gl_m)
     const int gl_l = gl ? li / NP : 0, gl_m = gl ? li % NP : 0;
@@ -118,22 +128,36 @@ __global__ void __launch_bounds__(128) face_apply_fast_kernel(int64_t n_face, co
 #pragma unroll
             for (int m = 0; m < NP; ++m) Ds[l][m] = sc ? Df[((sc_s * DIM + l) * NP + sc_n) * NP + m] : (R)0;
         const R lam = lamf[f], mu = muf[f];
+        // the neighbours' values of a shot, rows (s,k,b) padded, copied asynchronously one shot
+        // (pair) ahead into the other buffer, so that the loads overlap the current shot's work
+        auto issue = [&](int s0n, R* buf) {
+            const bool vld = s0n + hv < nshots;
+            const int64_t base = (int64_t)(vld ? s0n + hv : 0) * nvec;
+            const R* xl = x + base + (int64_t)el * NVS;
+            const R* xr = x + base + (int64_t)(er >= 0 ? er : el) * NVS;
+#pragma unroll
+            for (int e0 = 0; e0 < NVS; e0 += LANES) {
+                const int e = e0 + li;
+                if (e < NVS) {
+                    const int row = e / NP, n = e % NP;
+                    cp_async_elem(buf + row * NPP + n, vld ? xl + e : x, vld);
+                    cp_async_elem(buf + (DIM * NG + row) * NPP + n, vld && er >= 0 ? xr + e : x, vld && er >= 0);
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        issue(0, sV0);
         // D~ stays in registers for every shot of the batch
-        for (int s0 = 0; s0 < nshots; s0 += HALVES) {
+        for (int s0 = 0, it = 0; s0 < nshots; s0 += HALVES, ++it) {
         const bool valid = s0 + hv < nshots;
         const int shot = valid ? s0 + hv : s0;
         R* y = y0 + (int64_t)shot * nvec;
-        // ---- neighbours' values, rows (s,k,b) padded
-        const R* xl = x + (int64_t)shot * nvec + (int64_t)el * NVS;
-        const R* xr = x + (int64_t)shot * nvec + (int64_t)(er >= 0 ? er : el) * NVS;
-#pragma unroll
-        for (int e0 = 0; e0 < NVS; e0 += LANES) {
-            const int e = e0 + li;
-            if (e < NVS) {
-                const int row = e / NP, n = e % NP;
-                sV[row * NPP + n] = valid ? xl[e] : (R)0;
-                sV[(DIM * NG + row) * NPP + n] = valid && er >= 0 ? xr[e] : (R)0;
-            }
+        R* sV = sV0 + (it & 1) * F::SZ_V;
+        if (s0 + HALVES < nshots) {
+            issue(s0 + HALVES, sV0 + ((it + 1) & 1) * F::SZ_V);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncwarp();
         // ---- gather: g[k][l][b][m] = sum_s sum_n D~_s[l][n][m] v_s[k][b][n]
