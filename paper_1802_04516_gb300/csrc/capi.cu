@@ -143,6 +143,10 @@ static int ensure_fp32(stdg_ctx* c) {
     const int64_t nD = c->n_face * 2 * c->dim * c->Nphi * c->Nphi;
     if ((rc = dev_alloc(c, (void**)&c->d_D32, sizeof(float) * nD)) != STDG_OK) return rc;
     STDG_CUDA(c, launch_to_fp32(c));
+    if (face_tiled_shape(c)) {   // the single-shot face kernel of this shape reads D~ in tiles
+        if ((rc = dev_alloc(c, (void**)&c->d_Dt32, sizeof(float) * face_tiled_floats(c))) != STDG_OK) return rc;
+        STDG_CUDA(c, launch_tile_d32(c));
+    }
     return STDG_OK;
 }
 
@@ -375,7 +379,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     c->d_X = c->d_Jinv = c->d_detJ = c->d_faceX = c->d_shift = c->d_normal = c->d_xc = c->d_hj = nullptr;
     c->d_frame = nullptr;
     c->d_D = c->d_L = c->d_Mdual = nullptr;
-    c->d_D32 = nullptr;
+    c->d_D32 = c->d_Dt32 = nullptr;
     c->d_lamf = c->d_muf = c->d_rhoJ = nullptr;
     c->d_lamf32 = c->d_muf32 = c->d_rhoJ32 = nullptr;
     c->d_vtr = c->d_sigtr = c->d_b = c->d_x = c->d_energy = c->d_sigtmp = nullptr;

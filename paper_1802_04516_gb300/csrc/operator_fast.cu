@@ -400,12 +400,287 @@ __global__ void __launch_bounds__(128, MINB) face_apply_tma_kernel(int64_t n_fac
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Tiled single-shot FP32 kernel for 2D, p = 3 (d = 2, N_phi = 10, N_gamma = 4).  Per face the
+// gather g[(k,b)][(l,m)] = sum_(s,n) v_s[k][b][n] D~_s[l][n][m] and the scatter
+// y_s[k][b][n] += sum_(l,m) D~_s[l][n][m] h[(k,l)][b][m] are 8 x 20 x 20 products.  Two faces
+// per warp, 16 lanes each; lane (k, bp, q) owns the rows (k, 2bp) and (k, 2bp+1):
+//   gather:  columns (l, m) in group q (l = q/2, m in 5(q%2) .. +4), full contraction;
+//   E : g :  partner lane (1-k, bp, q^2) holds g[1-k][1-l] (one shuffle);
+//   S t   :  partner lane (k, 1-bp, q) holds the other two time nodes (one shuffle);
+//   scatter: rows (s, n) in group q (s = q/2, n in 5(q%2) .. +4), full contraction over (l, m).
+// D~ is stored per face as 16 tiles of 5 x 5 (row group Rg of (s,n) x column group C of (l,m)),
+// 28 floats each, at swizzled positions 4Rg + (C+Rg)%4 so that the four tiles a warp reads at
+// once fall in distinct shared-memory banks for both access orders.  Inside a tile the values
+// are ordered in pairs of adjacent rows (the pairs of the row group that meet adjacent value
+// pairs of v in an 8-byte load), so both products run on the packed FP32 FMA: the gather with
+// pairs (v_n, v_n+1) against (D~ row n, row n+1), the scatter with h stored twice in shared
+// memory ((h, h) pairs) against the same tile pairs.  Each lane loads 8 tiles (7 x 16 bytes
+// each) per face; the face's D~ block and element rows arrive by cp.async.bulk one face pair
+// ahead, as in the kernel above.
+// ---------------------------------------------------------------------------------
+struct FaceTile {
+    static constexpr int NP = 10, NG = 4, NVS = 2 * NG * NP;   // 80 values per element
+    static constexpr int TS = 28;                    // floats per 5 x 5 tile (3 of padding)
+    static constexpr int DT = 16 * TS;               // 448 floats per face
+    static constexpr int XOFF = DT, XR = NVS;        // element rows after the tiles
+    static constexpr int FACE_SEG = 624;             // 156 x 16 bytes: the second face 4 bank groups over
+    static constexpr int STAGE = 2 * FACE_SEG;
+    static constexpr int HROW = 52, HFACE = 420;     // h rows (k, b): 4 groups x (5 pairs + 2 pad) + 4
+    static constexpr int PER_WARP = 2 * STAGE + 2 * HFACE;
+    static_assert(XOFF + 2 * XR <= FACE_SEG && PER_WARP % 4 == 0, "tile kernel layout");
+};
+
+__host__ __device__ constexpr int tile_pos(int Rg, int C) { return 4 * Rg + ((C + Rg) & 3); }
+
+// tile slot -> (r, c) of the 5 x 5 tile of row group Rg (rows paired (0,1),(2,3) | 4 for even
+// Rg, (1,2),(3,4) | 0 for odd Rg); false for padding
+__host__ __device__ inline bool tile_slot_rc(int slot, int odd, int* r, int* c) {
+    if (slot < 10) { *c = slot >> 1; *r = (slot & 1) + (odd ? 1 : 0); return true; }
+    if (slot < 20) { *c = (slot - 10) >> 1; *r = (slot & 1) + (odd ? 3 : 2); return true; }
+    if (slot < 25) { *c = slot - 20; *r = odd ? 0 : 4; return true; }
+    return false;
+}
+
+// FP64 D~ [face][s][l][n][m] -> FP32 tiles
+__global__ void tile_d32_kernel(int64_t n_face, const double* __restrict__ D, float* __restrict__ Dt) {
+    using F = FaceTile;
+    const int64_t n = n_face * F::DT;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = i / F::DT;
+        const int w = (int)(i % F::DT), pos = w / F::TS, slot = w % F::TS;
+        const int Rg = pos >> 2, C = ((pos & 3) - Rg) & 3;
+        int r, c;
+        float v = 0.f;
+        if (tile_slot_rc(slot, Rg & 1, &r, &c)) {
+            const int s = Rg >> 1, nn = 5 * (Rg & 1) + r, l = C >> 1, m = 5 * (C & 1) + c;
+            v = (float)D[f * (2 * 2 * F::NP * F::NP) + ((s * 2 + l) * F::NP + nn) * F::NP + m];
+        }
+        Dt[i] = v;
+    }
+}
+
+__device__ __forceinline__ void load_tile(const float* p, float (&t)[FaceTile::TS]) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int j = 0; j < FaceTile::TS / 4; ++j) {
+        const float4 v = p4[j];
+        t[4 * j] = v.x; t[4 * j + 1] = v.y; t[4 * j + 2] = v.z; t[4 * j + 3] = v.w;
+    }
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) face_apply_tile_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+                                                              const int32_t* __restrict__ fr, const float* __restrict__ Dt,
+                                                              const float* __restrict__ lamf, const float* __restrict__ muf,
+                                                              const RefTables* __restrict__ rtp, const float* __restrict__ x,
+                                                              const int* __restrict__ xidx, int64_t ld, float* __restrict__ y,
+                                                              float scale, int* __restrict__ err) {
+    using F = FaceTile;
+    constexpr int TS = F::TS, NVS = F::NVS;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[4][2];
+    if (xidx) x += (int64_t)(*xidx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    float* base = reinterpret_cast<float*>(smraw) + warp * F::PER_WARP;
+    for (int t = lane; t < F::PER_WARP; t += 32) base[t] = 0.f;   // rows of absent r sides stay finite
+    const uint32_t bar0 = smem_u32(&bars[warp][0]), bar1 = smem_u32(&bars[warp][1]);
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int fs = lane >> 4, k = (lane >> 3) & 1, bp = (lane >> 2) & 1, q = lane & 3;
+    // scale * S, the lane's two rows: columns of its own time-node pair and of the partner's
+    float Sown[2][2], Soth[2][2];
+#pragma unroll
+    for (int bi = 0; bi < 2; ++bi)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            Sown[bi][j] = scale * (float)rtp->S[(2 * bp + bi) * F::NG + 2 * bp + j];
+            Soth[bi][j] = scale * (float)rtp->S[(2 * bp + bi) * F::NG + 2 * (1 - bp) + j];
+        }
+    float* sH = base + 2 * F::STAGE + fs * F::HFACE;
+    const int64_t n_pair = (n_face + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    constexpr long kPollLimit = 1L << 24;
+
+    auto issue = [&](int64_t p, int st) {   // lane 0 only: both faces of pair p into stage st
+        const uint32_t bar = st ? bar1 : bar0;
+        float* sg = base + st * F::STAGE;
+        uint32_t bytes = 0;
+        int el[2], er[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int64_t f = 2 * p + i;
+            el[i] = f < n_face ? fl[f] : -1;
+            er[i] = f < n_face ? fr[f] : -1;
+            if (el[i] >= 0) bytes += (F::DT + (er[i] >= 0 ? 2 : 1) * NVS) * sizeof(float);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bytes);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (el[i] < 0) continue;
+            float* seg = sg + i * F::FACE_SEG;
+            bulk_g2s(smem_u32(seg), Dt + (2 * p + i) * (int64_t)F::DT, F::DT * sizeof(float), bar);
+            bulk_g2s(smem_u32(seg + F::XOFF), x + (int64_t)el[i] * NVS, NVS * sizeof(float), bar);
+            if (er[i] >= 0) bulk_g2s(smem_u32(seg + F::XOFF + F::XR), x + (int64_t)er[i] * NVS, NVS * sizeof(float), bar);
+        }
+    };
+
+    int64_t p = blockIdx.x * (int64_t)wpb + warp;
+    if (p < n_pair && lane == 0) issue(p, 0);
+    uint32_t ph0 = 0, ph1 = 0;
+    int st = 0;
+    for (; p < n_pair; p += stride) {
+        const int64_t pn = p + stride;
+        if (pn < n_pair && lane == 0) issue(pn, st ^ 1);
+        // the lanes leave together (the shuffles below take the whole warp)
+        if (!__all_sync(FULL, mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit))) {
+            if (lane == 0) atomicExch(err, 1);
+            bool drained = mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit);
+            if (pn < n_pair) drained = mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit) && drained;
+            if (!drained && lane == 0) atomicExch(err, 2);
+            break;
+        }
+        if (st) ph1 ^= 1u; else ph0 ^= 1u;
+        const float* seg = base + st * F::STAGE + fs * F::FACE_SEG;
+        const int64_t f = 2 * p + fs;
+        const bool fok = f < n_face;
+        const int el = fok ? fl[f] : -1, er = fok ? fr[f] : -1;
+        const float lam = fok ? lamf[f] : 0.f, mu = fok ? muf[f] : 0.f;
+        // ---- gather: rows (k, 2bp + bi), columns of group q; the r side's tiles are zero on
+        // boundary faces
+        float2 acc[2][5];
+#pragma unroll
+        for (int bi = 0; bi < 2; ++bi)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc[bi][c] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float2 V[2][5];
+#pragma unroll
+            for (int bi = 0; bi < 2; ++bi) {
+                const float2* vr = reinterpret_cast<const float2*>(seg + F::XOFF + s * F::XR + (4 * k + 2 * bp + bi) * F::NP);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) V[bi][i] = vr[i];
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float T[TS];
+                load_tile(seg + TS * tile_pos(2 * s + h, q), T);
+#pragma unroll
+                for (int bi = 0; bi < 2; ++bi) {
+                    const float2 pa = h ? V[bi][3] : V[bi][0];   // n = (6,7) | (0,1)
+                    const float2 pb = h ? V[bi][4] : V[bi][1];   // n = (8,9) | (2,3)
+                    const float sg = h ? V[bi][2].y : V[bi][2].x;   // n = 5 | 4
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) {
+                        acc[bi][c] = ffma2(make_float2(T[2 * c], T[2 * c + 1]), pa, acc[bi][c]);
+                        acc[bi][c] = ffma2(make_float2(T[10 + 2 * c], T[11 + 2 * c]), pb, acc[bi][c]);
+                        acc[bi][c].x = fmaf(T[20 + c], sg, acc[bi][c].x);
+                    }
+                }
+            }
+        }
+        // ---- t = E_j : g with the partner lane (1-k, bp, q^2), then h = scale S t with (k, 1-bp, q)
+        const bool diag = k == (q >> 1);
+        const float al = diag ? 2.f * mu + lam : mu, be = diag ? lam : mu;
+        float tv[2][5], hv[2][5];
+#pragma unroll
+        for (int bi = 0; bi < 2; ++bi)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const float gv = acc[bi][c].x + acc[bi][c].y;
+                const float gp = __shfl_xor_sync(FULL, gv, 10);
+                tv[bi][c] = al * gv + be * gp;
+            }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float tq0 = __shfl_xor_sync(FULL, tv[0][c], 4), tq1 = __shfl_xor_sync(FULL, tv[1][c], 4);
+#pragma unroll
+            for (int bi = 0; bi < 2; ++bi)
+                hv[bi][c] = Sown[bi][0] * tv[0][c] + Sown[bi][1] * tv[1][c] + Soth[bi][0] * tq0 + Soth[bi][1] * tq1;
+        }
+        // h of rows (k, 2bp + bi), columns of group q, each value twice
+#pragma unroll
+        for (int bi = 0; bi < 2; ++bi) {
+            float* hr = sH + (4 * k + 2 * bp + bi) * F::HROW + 12 * q;
+            reinterpret_cast<float4*>(hr)[0] = make_float4(hv[bi][0], hv[bi][0], hv[bi][1], hv[bi][1]);
+            reinterpret_cast<float4*>(hr)[1] = make_float4(hv[bi][2], hv[bi][2], hv[bi][3], hv[bi][3]);
+            reinterpret_cast<float2*>(hr)[4] = make_float2(hv[bi][4], hv[bi][4]);
+        }
+        __syncwarp();
+        // ---- scatter: rows (k, 2bp + bi), (s, n) of group q, contraction over all (l, m)
+        float2 oA[2], oB[2];
+        float oS[2];
+#pragma unroll
+        for (int bi = 0; bi < 2; ++bi) { oA[bi] = make_float2(0.f, 0.f); oB[bi] = oA[bi]; oS[bi] = 0.f; }
+#pragma unroll
+        for (int C = 0; C < 4; ++C) {
+            float T[TS];
+            load_tile(seg + TS * tile_pos(q, C), T);
+#pragma unroll
+            for (int bi = 0; bi < 2; ++bi) {
+                const float* hr = sH + (4 * k + 2 * bp + bi) * F::HROW + 12 * C;
+                const float4 h01 = reinterpret_cast<const float4*>(hr)[0];
+                const float4 h23 = reinterpret_cast<const float4*>(hr)[1];
+                const float2 h4 = reinterpret_cast<const float2*>(hr)[4];
+                const float2 H[5] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
+                                     make_float2(h23.z, h23.w), h4};
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    oA[bi] = ffma2(make_float2(T[2 * c], T[2 * c + 1]), H[c], oA[bi]);
+                    oB[bi] = ffma2(make_float2(T[10 + 2 * c], T[11 + 2 * c]), H[c], oB[bi]);
+                    oS[bi] = fmaf(T[20 + c], H[c].x, oS[bi]);
+                }
+            }
+        }
+        const int es = (q >> 1) == 0 ? el : er, odd = q & 1;
+        if (es >= 0) {
+#pragma unroll
+            for (int bi = 0; bi < 2; ++bi) {
+                float* yr = y + (int64_t)es * NVS + (4 * k + 2 * bp + bi) * F::NP + 5 * odd;
+                // row pairs (1,2),(3,4) | 0 for odd groups, (0,1),(2,3) | 4 for even: 8-byte aligned
+                atomicAdd(reinterpret_cast<float2*>(yr + odd), oA[bi]);
+                atomicAdd(reinterpret_cast<float2*>(yr + 2 + odd), oB[bi]);
+                atomicAdd(yr + (odd ? 0 : 4), oS[bi]);
+            }
+        }
+        __syncwarp();   // stage st and the h rows are free for the next pair
+        st ^= 1;
+    }
+}
+
 template <int DIM, int NP, int NG, typename R>
 static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx,
                                int64_t ld, R* y, double scale, int nshots) {
     using T = FaceTma<DIM, NP, NG, R>;
     const bool aligned = (reinterpret_cast<uintptr_t>(D) % 16 == 0) && (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
                          ((ld * (int64_t)sizeof(R)) % 16 == 0);
+    if constexpr (DIM == 2 && NP == 10 && NG == 4 && std::is_same<R, float>::value) {
+        // the tiled kernel, on the tiled copy of D~ made with the FP32 copy
+        if (nshots == 1 && aligned && c->d_err && c->d_Dt32 && D == c->d_D32 &&
+            reinterpret_cast<uintptr_t>(y) % 8 == 0) {
+            using TF = FaceTile;
+            const int wpb = c->tune.face_wpb;   // <= 4: the kernel's launch bounds and its per-warp barriers
+            const size_t smem = sizeof(float) * (size_t)wpb * TF::PER_WARP;
+            const int64_t n_pair = (c->n_face + 1) / 2;
+            const int64_t blocks = std::min<int64_t>((n_pair + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
+            auto go = [&](auto kern) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kern<<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_face, c->d_face_l, c->d_face_r, c->d_Dt32, lamf,
+                                                                     muf, c->d_rt, x, xidx, ld, y, (float)scale, c->d_err);
+            };
+            if (c->tune.face_cap) go(face_apply_tile_kernel<4>);
+            else go(face_apply_tile_kernel<1>);
+            note_launch(c);
+            return cudaGetLastError();
+        }
+    }
     if (nshots == 1 && aligned && c->d_err) {
         const int wpb = c->tune.face_wpb;   // <= 4: the kernel's launch bounds and its per-warp barriers
         const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
@@ -437,6 +712,15 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
         face_apply_fast_kernel<DIM, NP, NG, R, 1><<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
             c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (R)scale, nshots, c->nvel);
     }
+    note_launch(c);
+    return cudaGetLastError();
+}
+
+// FP32 tiles of D~ for the tiled (2,10,4) kernel; false for other shapes
+bool face_tiled_shape(const stdg_ctx* c) { return c->dim == 2 && c->Nphi == 10 && c->Ng == 4; }
+int64_t face_tiled_floats(const stdg_ctx* c) { return face_tiled_shape(c) ? c->n_face * FaceTile::DT : 0; }
+cudaError_t launch_tile_d32(stdg_ctx* c) {
+    tile_d32_kernel<<<(unsigned)(c->n_sm * 8), 256, 0, c->stream>>>(c->n_face, c->d_D, c->d_Dt32);
     note_launch(c);
     return cudaGetLastError();
 }

@@ -114,6 +114,7 @@ struct stdg_ctx {
     double *d_L = nullptr;      // Cholesky factors of the dual mass matrices (lower, [face][m][m'])
     double *d_Mdual = nullptr;  // dual mass matrices (set-up workspace)
     float *d_D32 = nullptr;     // FP32 copy of D~
+    float *d_Dt32 = nullptr;    // FP32 D~ in 5 x 5 tiles (2D, p = 3 only: the tiled face kernel)
     double *d_lamf = nullptr, *d_muf = nullptr, *d_rhoJ = nullptr;    // per face / element
     float *d_lamf32 = nullptr, *d_muf32 = nullptr, *d_rhoJ32 = nullptr;
 
@@ -198,6 +199,9 @@ cudaError_t launch_precompute(stdg_ctx* c, const double* d_rule_v, const double*
 cudaError_t launch_orthonormalize(stdg_ctx* c);
 cudaError_t launch_sig_convert(stdg_ctx* c, const double* in, double* out, int dir);
 cudaError_t launch_to_fp32(stdg_ctx* c);
+bool face_tiled_shape(const stdg_ctx* c);
+int64_t face_tiled_floats(const stdg_ctx* c);
+cudaError_t launch_tile_d32(stdg_ctx* c);
 // y = A x (cfac scales the Schur part; 1 for the operator).  With xidx != null the input is
 // x + (*xidx) * ld, the index read on the device (Krylov basis column j).
 // nshots > 1: x and y hold nshots consecutive (shot-major) velocity vectors of c->nvel values.
