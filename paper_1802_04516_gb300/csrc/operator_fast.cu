@@ -403,31 +403,32 @@ __global__ void __launch_bounds__(128, MINB) face_apply_tma_kernel(int64_t n_fac
 // ---------------------------------------------------------------------------------
 // Tiled single-shot FP32 kernel for 2D, p = 3 (d = 2, N_phi = 10, N_gamma = 4).  Per face the
 // gather g[(k,b)][(l,m)] = sum_(s,n) v_s[k][b][n] D~_s[l][n][m] and the scatter
-// y_s[k][b][n] += sum_(l,m) D~_s[l][n][m] h[(k,l)][b][m] are 8 x 20 x 20 products.  Two faces
-// per warp, 16 lanes each; lane (k, bp, q) owns the rows (k, 2bp) and (k, 2bp+1):
-//   gather:  columns (l, m) in group q (l = q/2, m in 5(q%2) .. +4), full contraction;
-//   E : g :  partner lane (1-k, bp, q^2) holds g[1-k][1-l] (one shuffle);
-//   S t   :  partner lane (k, 1-bp, q) holds the other two time nodes (one shuffle);
-//   scatter: rows (s, n) in group q (s = q/2, n in 5(q%2) .. +4), full contraction over (l, m).
-// D~ is stored per face as 16 tiles of 5 x 5 (row group Rg of (s,n) x column group C of (l,m)),
-// 28 floats each, at swizzled positions 4Rg + (C+Rg)%4 so that the four tiles a warp reads at
-// once fall in distinct shared-memory banks for both access orders.  Inside a tile the values
-// are ordered in pairs of adjacent rows (the pairs of the row group that meet adjacent value
-// pairs of v in an 8-byte load), so both products run on the packed FP32 FMA: the gather with
-// pairs (v_n, v_n+1) against (D~ row n, row n+1), the scatter with h stored twice in shared
-// memory ((h, h) pairs) against the same tile pairs.  Each lane loads 8 tiles (7 x 16 bytes
-// each) per face; the face's D~ block and element rows arrive by cp.async.bulk one face pair
-// ahead, as in the kernel above.
+// y_s[k][b][n] += sum_(l,m) D~_s[l][n][m] h[(k,l)][b][m] are 8 x 20 x 20 products.  Four faces
+// per warp, eight lanes each; lane (k, q) owns the four time-node rows (k, b) and column group
+// q of (l, m) (l = q/2, m in 5(q%2) .. +4):
+//   gather:  g[(k,b)][group q] over the full (s, n) contraction, tiles (Rg, q), Rg = 0..3;
+//   E : g :  partner lane (1-k, q^2) holds g[1-k][1-l] (one shuffle per value);
+//   S t   :  in registers (the lane holds every time node);
+//   scatter: partial sums over the lane's own columns with the same tiles (Rg, q), then a
+//            reduce-scatter over the four column lanes (shuffles): each lane ends with one
+//            time-node row of each row group Rg, 5 values, added to y with packed atomics.
+// Shared memory delivers one 4-byte value per lane and clock however many lanes share an
+// address, so the work per value loaded decides the rate: every tile value loaded feeds four
+// rows.  D~ is stored per face as 16 tiles of 5 x 5 (row group Rg of (s,n) x column group C of
+// (l,m)), 28 floats each, at swizzled positions 4Rg + (C+Rg)%4, so the four tiles a quarter-warp
+// reads fall in distinct banks.  Inside a tile the values are paired by adjacent rows (the pairs
+// that meet adjacent pairs of v in one 8-byte load), so both products run on the packed FP32
+// FMA.  The face's D~ block and element rows arrive by cp.async.bulk one group of faces ahead.
 // ---------------------------------------------------------------------------------
 struct FaceTile {
     static constexpr int NP = 10, NG = 4, NVS = 2 * NG * NP;   // 80 values per element
     static constexpr int TS = 28;                    // floats per 5 x 5 tile (3 of padding)
     static constexpr int DT = 16 * TS;               // 448 floats per face
     static constexpr int XOFF = DT, XR = NVS;        // element rows after the tiles
-    static constexpr int FACE_SEG = 624;             // 156 x 16 bytes: the second face 4 bank groups over
-    static constexpr int STAGE = 2 * FACE_SEG;
-    static constexpr int HROW = 52, HFACE = 420;     // h rows (k, b): 4 groups x (5 pairs + 2 pad) + 4
-    static constexpr int PER_WARP = 2 * STAGE + 2 * HFACE;
+    static constexpr int FPW = 4;                    // faces per warp
+    static constexpr int FACE_SEG = 624;             // 156 x 16 bytes: a half-warp's two faces 4 bank groups apart
+    static constexpr int STAGE = FPW * FACE_SEG;
+    static constexpr int PER_WARP = 2 * STAGE;
     static_assert(XOFF + 2 * XR <= FACE_SEG && PER_WARP % 4 == 0, "tile kernel layout");
 };
 
@@ -460,6 +461,14 @@ __global__ void tile_d32_kernel(int64_t n_face, const double* __restrict__ D, fl
     }
 }
 
+// y[0] += a (and y[1] += b): reductions without a returned value (y 8-byte aligned for two)
+__device__ __forceinline__ void red_add2(float* y, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(y), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_add1(float* y, float a) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(y), "f"(a) : "memory");
+}
+
 __device__ __forceinline__ void load_tile(const float* p, float (&t)[FaceTile::TS]) {
     const float4* p4 = reinterpret_cast<const float4*>(p);
 #pragma unroll
@@ -469,15 +478,15 @@ __device__ __forceinline__ void load_tile(const float* p, float (&t)[FaceTile::T
     }
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(128, MINB) face_apply_tile_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+template <int MAXREG>
+__global__ void __maxnreg__(MAXREG) face_apply_tile_kernel(int64_t n_face, const int32_t* __restrict__ fl,
                                                               const int32_t* __restrict__ fr, const float* __restrict__ Dt,
                                                               const float* __restrict__ lamf, const float* __restrict__ muf,
                                                               const RefTables* __restrict__ rtp, const float* __restrict__ x,
                                                               const int* __restrict__ xidx, int64_t ld, float* __restrict__ y,
                                                               float scale, int* __restrict__ err) {
     using F = FaceTile;
-    constexpr int TS = F::TS, NVS = F::NVS;
+    constexpr int TS = F::TS, NVS = F::NVS, NG = F::NG, FPW = F::FPW;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bars[4][2];
@@ -492,166 +501,183 @@ __global__ void __launch_bounds__(128, MINB) face_apply_tile_kernel(int64_t n_fa
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int fs = lane >> 4, k = (lane >> 3) & 1, bp = (lane >> 2) & 1, q = lane & 3;
-    // scale * S, the lane's two rows: columns of its own time-node pair and of the partner's
-    float Sown[2][2], Soth[2][2];
+    const int fq = lane >> 3, k = (lane >> 2) & 1, q = lane & 3;
+    // qs = q with its two bits swapped.  scale * S with the rows in this lane's order (slot i =
+    // time node i ^ qs): the scatter's partial sums then come out in the order in which the
+    // reduce-scatter over the column lanes sends and keeps them (first step with lane q^1: slots
+    // 0,1 kept, 2,3 sent; second step with lane q^2: slot 0 kept, 1 sent), and the lane ends
+    // with time node qs
+    const int qs = ((q & 1) << 1) | (q >> 1);
+    float Sm[NG][NG];
 #pragma unroll
-    for (int bi = 0; bi < 2; ++bi)
+    for (int i = 0; i < NG; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            Sown[bi][j] = scale * (float)rtp->S[(2 * bp + bi) * F::NG + 2 * bp + j];
-            Soth[bi][j] = scale * (float)rtp->S[(2 * bp + bi) * F::NG + 2 * (1 - bp) + j];
-        }
-    float* sH = base + 2 * F::STAGE + fs * F::HFACE;
-    const int64_t n_pair = (n_face + 1) / 2;
+        for (int b = 0; b < NG; ++b) Sm[i][b] = scale * (float)rtp->S[(i ^ qs) * NG + b];
+    const int64_t n_grp = (n_face + FPW - 1) / FPW;
     const int64_t stride = (int64_t)gridDim.x * wpb;
     constexpr long kPollLimit = 1L << 24;
 
-    auto issue = [&](int64_t p, int st) {   // lane 0 only: both faces of pair p into stage st
+    // element ids of the faces of group pp (every lane loads them, one group before the copies
+    // that need them are issued, so that lane 0 does not stall the warp on the loads)
+    auto load_ids = [&](int64_t pp, int (&el)[FPW], int (&er)[FPW]) {
+#pragma unroll
+        for (int i = 0; i < FPW; ++i) {
+            const int64_t f = FPW * pp + i;
+            const bool ok = pp < n_grp && f < n_face;
+            el[i] = ok ? fl[f] : -1;
+            er[i] = ok ? fr[f] : -1;
+        }
+    };
+    auto issue = [&](int64_t p, int st, const int (&el)[FPW], const int (&er)[FPW]) {   // lane 0 only
         const uint32_t bar = st ? bar1 : bar0;
         float* sg = base + st * F::STAGE;
         uint32_t bytes = 0;
-        int el[2], er[2];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int64_t f = 2 * p + i;
-            el[i] = f < n_face ? fl[f] : -1;
-            er[i] = f < n_face ? fr[f] : -1;
+        for (int i = 0; i < FPW; ++i)
             if (el[i] >= 0) bytes += (F::DT + (er[i] >= 0 ? 2 : 1) * NVS) * sizeof(float);
-        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, bytes);
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < FPW; ++i) {
             if (el[i] < 0) continue;
             float* seg = sg + i * F::FACE_SEG;
-            bulk_g2s(smem_u32(seg), Dt + (2 * p + i) * (int64_t)F::DT, F::DT * sizeof(float), bar);
+            bulk_g2s(smem_u32(seg), Dt + (FPW * p + i) * (int64_t)F::DT, F::DT * sizeof(float), bar);
             bulk_g2s(smem_u32(seg + F::XOFF), x + (int64_t)el[i] * NVS, NVS * sizeof(float), bar);
             if (er[i] >= 0) bulk_g2s(smem_u32(seg + F::XOFF + F::XR), x + (int64_t)er[i] * NVS, NVS * sizeof(float), bar);
         }
     };
 
+    // the lane's face of group pp: element ids and Lame parameters, loaded one group ahead
+    auto fetch = [&](int64_t pp, int& a, int& b, float& l, float& m) {
+        const int64_t ff = FPW * pp + fq;
+        const bool ok = pp < n_grp && ff < n_face;
+        a = ok ? fl[ff] : -1;
+        b = ok ? fr[ff] : -1;
+        l = ok ? lamf[ff] : 0.f;
+        m = ok ? muf[ff] : 0.f;
+    };
     int64_t p = blockIdx.x * (int64_t)wpb + warp;
-    if (p < n_pair && lane == 0) issue(p, 0);
+    int idl[FPW], idr[FPW];   // ids of the group whose copies are issued next
+    load_ids(p, idl, idr);
+    if (p < n_grp && lane == 0) issue(p, 0, idl, idr);
+    load_ids(p + stride, idl, idr);
+    int el, er;
+    float lam, mu;
+    fetch(p, el, er, lam, mu);
     uint32_t ph0 = 0, ph1 = 0;
     int st = 0;
-    for (; p < n_pair; p += stride) {
+    for (; p < n_grp; p += stride) {
         const int64_t pn = p + stride;
-        if (pn < n_pair && lane == 0) issue(pn, st ^ 1);
+        if (pn < n_grp && lane == 0) issue(pn, st ^ 1, idl, idr);
+        int nidl[FPW], nidr[FPW];
+        load_ids(pn + stride, nidl, nidr);
+        int el_n, er_n;
+        float lam_n, mu_n;
+        fetch(pn, el_n, er_n, lam_n, mu_n);
         // the lanes leave together (the shuffles below take the whole warp)
         if (!__all_sync(FULL, mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit))) {
             if (lane == 0) atomicExch(err, 1);
             bool drained = mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit);
-            if (pn < n_pair) drained = mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit) && drained;
+            if (pn < n_grp) drained = mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit) && drained;
             if (!drained && lane == 0) atomicExch(err, 2);
             break;
         }
         if (st) ph1 ^= 1u; else ph0 ^= 1u;
-        const float* seg = base + st * F::STAGE + fs * F::FACE_SEG;
-        const int64_t f = 2 * p + fs;
-        const bool fok = f < n_face;
-        const int el = fok ? fl[f] : -1, er = fok ? fr[f] : -1;
-        const float lam = fok ? lamf[f] : 0.f, mu = fok ? muf[f] : 0.f;
-        // ---- gather: rows (k, 2bp + bi), columns of group q; the r side's tiles are zero on
+        const float* seg = base + st * F::STAGE + fq * F::FACE_SEG;
+        // ---- gather: rows (k, b), b = 0..3, columns of group q; the r side's tiles are zero on
         // boundary faces
-        float2 acc[2][5];
+        float2 acc[NG][5];
 #pragma unroll
-        for (int bi = 0; bi < 2; ++bi)
+        for (int b = 0; b < NG; ++b)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) acc[bi][c] = make_float2(0.f, 0.f);
+            for (int c = 0; c < 5; ++c) acc[b][c] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            float2 V[2][5];
-#pragma unroll
-            for (int bi = 0; bi < 2; ++bi) {
-                const float2* vr = reinterpret_cast<const float2*>(seg + F::XOFF + s * F::XR + (4 * k + 2 * bp + bi) * F::NP);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) V[bi][i] = vr[i];
-            }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 float T[TS];
                 load_tile(seg + TS * tile_pos(2 * s + h, q), T);
 #pragma unroll
-                for (int bi = 0; bi < 2; ++bi) {
-                    const float2 pa = h ? V[bi][3] : V[bi][0];   // n = (6,7) | (0,1)
-                    const float2 pb = h ? V[bi][4] : V[bi][1];   // n = (8,9) | (2,3)
-                    const float sg = h ? V[bi][2].y : V[bi][2].x;   // n = 5 | 4
+                for (int b = 0; b < NG; ++b) {
+                    const float2* vr = reinterpret_cast<const float2*>(seg + F::XOFF + s * F::XR + (4 * k + b) * F::NP);
+                    const float2 pa = vr[h ? 3 : 0];           // n = (6,7) | (0,1)
+                    const float2 pb = vr[h ? 4 : 1];           // n = (8,9) | (2,3)
+                    const float2 m2 = vr[2];                   // n = (4,5)
+                    const float sg = h ? m2.y : m2.x;
 #pragma unroll
                     for (int c = 0; c < 5; ++c) {
-                        acc[bi][c] = ffma2(make_float2(T[2 * c], T[2 * c + 1]), pa, acc[bi][c]);
-                        acc[bi][c] = ffma2(make_float2(T[10 + 2 * c], T[11 + 2 * c]), pb, acc[bi][c]);
-                        acc[bi][c].x = fmaf(T[20 + c], sg, acc[bi][c].x);
+                        acc[b][c] = ffma2(make_float2(T[2 * c], T[2 * c + 1]), pa, acc[b][c]);
+                        acc[b][c] = ffma2(make_float2(T[10 + 2 * c], T[11 + 2 * c]), pb, acc[b][c]);
+                        acc[b][c].x = fmaf(T[20 + c], sg, acc[b][c].x);
                     }
                 }
             }
         }
-        // ---- t = E_j : g with the partner lane (1-k, bp, q^2), then h = scale S t with (k, 1-bp, q)
+        // ---- t = E_j : g with the partner lane (1-k, q^2); h = scale S t in registers
         const bool diag = k == (q >> 1);
         const float al = diag ? 2.f * mu + lam : mu, be = diag ? lam : mu;
-        float tv[2][5], hv[2][5];
+        float tv[NG][5];
 #pragma unroll
-        for (int bi = 0; bi < 2; ++bi)
+        for (int b = 0; b < NG; ++b)
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
-                const float gv = acc[bi][c].x + acc[bi][c].y;
-                const float gp = __shfl_xor_sync(FULL, gv, 10);
-                tv[bi][c] = al * gv + be * gp;
+                const float gv = acc[b][c].x + acc[b][c].y;
+                const float gp = __shfl_xor_sync(FULL, gv, 6);
+                tv[b][c] = al * gv + be * gp;
             }
+        float2 hp[NG][5];   // (h, h) pairs for the packed scatter products, slot i = time node i ^ qs
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            const float tq0 = __shfl_xor_sync(FULL, tv[0][c], 4), tq1 = __shfl_xor_sync(FULL, tv[1][c], 4);
+        for (int i = 0; i < NG; ++i)
 #pragma unroll
-            for (int bi = 0; bi < 2; ++bi)
-                hv[bi][c] = Sown[bi][0] * tv[0][c] + Sown[bi][1] * tv[1][c] + Soth[bi][0] * tq0 + Soth[bi][1] * tq1;
-        }
-        // h of rows (k, 2bp + bi), columns of group q, each value twice
+            for (int c = 0; c < 5; ++c) {
+                float hv = 0.f;
 #pragma unroll
-        for (int bi = 0; bi < 2; ++bi) {
-            float* hr = sH + (4 * k + 2 * bp + bi) * F::HROW + 12 * q;
-            reinterpret_cast<float4*>(hr)[0] = make_float4(hv[bi][0], hv[bi][0], hv[bi][1], hv[bi][1]);
-            reinterpret_cast<float4*>(hr)[1] = make_float4(hv[bi][2], hv[bi][2], hv[bi][3], hv[bi][3]);
-            reinterpret_cast<float2*>(hr)[4] = make_float2(hv[bi][4], hv[bi][4]);
-        }
-        __syncwarp();
-        // ---- scatter: rows (k, 2bp + bi), (s, n) of group q, contraction over all (l, m)
-        float2 oA[2], oB[2];
-        float oS[2];
+                for (int b2 = 0; b2 < NG; ++b2) hv = fmaf(Sm[i][b2], tv[b2][c], hv);
+                hp[i][c] = make_float2(hv, hv);
+            }
+        // ---- scatter: partial sums over this lane's columns for each row group Rg, reduced
+        // over the four column lanes of the face
 #pragma unroll
-        for (int bi = 0; bi < 2; ++bi) { oA[bi] = make_float2(0.f, 0.f); oB[bi] = oA[bi]; oS[bi] = 0.f; }
-#pragma unroll
-        for (int C = 0; C < 4; ++C) {
+        for (int Rg = 0; Rg < 4; ++Rg) {
             float T[TS];
-            load_tile(seg + TS * tile_pos(q, C), T);
+            load_tile(seg + TS * tile_pos(Rg, q), T);
+            float R[NG][5];   // per slot (time node i ^ qs): row pair A, row pair B, single row
 #pragma unroll
-            for (int bi = 0; bi < 2; ++bi) {
-                const float* hr = sH + (4 * k + 2 * bp + bi) * F::HROW + 12 * C;
-                const float4 h01 = reinterpret_cast<const float4*>(hr)[0];
-                const float4 h23 = reinterpret_cast<const float4*>(hr)[1];
-                const float2 h4 = reinterpret_cast<const float2*>(hr)[4];
-                const float2 H[5] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
-                                     make_float2(h23.z, h23.w), h4};
+            for (int b = 0; b < NG; ++b) {
+                float2 oA = make_float2(0.f, 0.f), oB = oA;
+                float oS = 0.f;
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    oA[bi] = ffma2(make_float2(T[2 * c], T[2 * c + 1]), H[c], oA[bi]);
-                    oB[bi] = ffma2(make_float2(T[10 + 2 * c], T[11 + 2 * c]), H[c], oB[bi]);
-                    oS[bi] = fmaf(T[20 + c], H[c].x, oS[bi]);
+                    oA = ffma2(make_float2(T[2 * c], T[2 * c + 1]), hp[b][c], oA);
+                    oB = ffma2(make_float2(T[10 + 2 * c], T[11 + 2 * c]), hp[b][c], oB);
+                    oS = fmaf(T[20 + c], hp[b][c].x, oS);
                 }
+                R[b][0] = oA.x; R[b][1] = oA.y; R[b][2] = oB.x; R[b][3] = oB.y; R[b][4] = oS;
             }
-        }
-        const int es = (q >> 1) == 0 ? el : er, odd = q & 1;
-        if (es >= 0) {
+            // step 1 (lane q^1): its slots 2,3 hold this lane's slots 0,1 (time nodes qs, qs^1);
+            // step 2 (lane q^2): its slot 1 holds this lane's slot 0 (time node qs)
+            float K[2][5];
 #pragma unroll
-            for (int bi = 0; bi < 2; ++bi) {
-                float* yr = y + (int64_t)es * NVS + (4 * k + 2 * bp + bi) * F::NP + 5 * odd;
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int v = 0; v < 5; ++v) K[j][v] = R[j][v] + __shfl_xor_sync(FULL, R[2 + j][v], 1);
+            float Y[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Y[v] = K[0][v] + __shfl_xor_sync(FULL, K[1][v], 2);
+            const int es = (Rg >> 1) == 0 ? el : er, odd = Rg & 1, b = qs;
+            if (es >= 0) {
+                float* yr = y + (int64_t)es * NVS + (4 * k + b) * F::NP + 5 * odd;
                 // row pairs (1,2),(3,4) | 0 for odd groups, (0,1),(2,3) | 4 for even: 8-byte aligned
-                atomicAdd(reinterpret_cast<float2*>(yr + odd), oA[bi]);
-                atomicAdd(reinterpret_cast<float2*>(yr + 2 + odd), oB[bi]);
-                atomicAdd(yr + (odd ? 0 : 4), oS[bi]);
+                red_add2(yr + odd, Y[0], Y[1]);
+                red_add2(yr + 2 + odd, Y[2], Y[3]);
+                red_add1(yr + (odd ? 0 : 4), Y[4]);
             }
         }
-        __syncwarp();   // stage st and the h rows are free for the next pair
+        __syncwarp();   // stage st is free for the next group
         st ^= 1;
+        el = el_n; er = er_n; lam = lam_n; mu = mu_n;
+#pragma unroll
+        for (int i = 0; i < FPW; ++i) { idl[i] = nidl[i]; idr[i] = nidr[i]; }
     }
 }
 
@@ -668,15 +694,17 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
             using TF = FaceTile;
             const int wpb = c->tune.face_wpb;   // <= 4: the kernel's launch bounds and its per-warp barriers
             const size_t smem = sizeof(float) * (size_t)wpb * TF::PER_WARP;
-            const int64_t n_pair = (c->n_face + 1) / 2;
-            const int64_t blocks = std::min<int64_t>((n_pair + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
+            const int64_t n_grp = (c->n_face + TF::FPW - 1) / TF::FPW;
+            const int64_t blocks = std::min<int64_t>((n_grp + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
             auto go = [&](auto kern) {
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 kern<<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_face, c->d_face_l, c->d_face_r, c->d_Dt32, lamf,
                                                                      muf, c->d_rt, x, xidx, ld, y, (float)scale, c->d_err);
             };
-            if (c->tune.face_cap) go(face_apply_tile_kernel<4>);
-            else go(face_apply_tile_kernel<1>);
+            // capped: the registers of 11 resident warps per SM, the most that the shared memory of
+            // the bulk-copy stages admits
+            if (c->tune.face_cap) go(face_apply_tile_kernel<184>);
+            else go(face_apply_tile_kernel<255>);
             note_launch(c);
             return cudaGetLastError();
         }
