@@ -681,6 +681,209 @@ __global__ void __maxnreg__(MAXREG) face_apply_tile_kernel(int64_t n_face, const
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Multi-shot FP32 kernel for 2D, p = 2 (d = 2, N_phi = 6, N_gamma = 3): one lane per shot.
+// A warp takes a face and 32 shots of a stacked vector at a time.  Each lane keeps its shot's
+// two element rows (72 values) and its 72 outputs in registers; the face's D~ block is read
+// from shared memory by all lanes at once, one column m at a time (24 values, each used in 12
+// products).  S acts on the time nodes only and commutes with D~ and E, so it is applied to v
+// first: per column m the gather g[k][l][b] = sum_(s,n) D~_s[l][n][m] v'_s[k][b][n], the stress
+// map h = E_j : g and the scatter y_s[k][b][n] += sum_l D~_s[l][n][m] h[(k,l)][b] need no other
+// column.  The rows of the next (face, 32 shots) item are copied by cp.async while the current
+// one is computed; the outputs go back through the same shared rows so that the atomic
+// additions are 16-byte vectors along one shot's element row.
+// ---------------------------------------------------------------------------------
+struct FaceShots {
+    static constexpr int NP = 6, NG = 3, NVS = 2 * NG * NP;   // 36 values per element
+    static constexpr int DFACE = 2 * 2 * NP * NP;             // 144
+    static constexpr int ROW = 76;                             // 72 values + 4: 19 x 16 bytes (odd)
+    static constexpr int VBUF = 32 * ROW;
+    static constexpr int PER_WARP = 2 * VBUF + 2 * DFACE;
+    static_assert(2 * NVS <= ROW && (ROW / 4) % 2 == 1 && (NVS * 4) % 16 == 0 && (DFACE * 4) % 16 == 0, "layout");
+};
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool on) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(on ? 16u : 0u)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add4(float* y, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(128) face_apply_shots_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+                                                               const int32_t* __restrict__ fr, const float* __restrict__ D,
+                                                               const float* __restrict__ lamf, const float* __restrict__ muf,
+                                                               const RefTables* __restrict__ rtp, const float* __restrict__ x,
+                                                               const int* __restrict__ xidx, int64_t ld,
+                                                               float* __restrict__ y0, float scale, int nshots, int64_t nvec) {
+    using F = FaceShots;
+    constexpr int NP = F::NP, NG = F::NG, NVS = F::NVS;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (xidx) x += (int64_t)(*xidx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    float* vbuf = reinterpret_cast<float*>(smraw) + warp * F::PER_WARP;   // two buffers of 32 rows
+    float* dbuf = vbuf + 2 * F::VBUF;                                      // two D~ blocks
+    float Sm[NG][NG];   // scale * S
+#pragma unroll
+    for (int a = 0; a < NG; ++a)
+#pragma unroll
+        for (int b = 0; b < NG; ++b) Sm[a][b] = scale * (float)rtp->S[a * NG + b];
+    const int nc = (nshots + 31) >> 5;            // 32-shot chunks
+    const int64_t gw = blockIdx.x * (int64_t)wpb + warp, W = (int64_t)gridDim.x * wpb;
+    const int64_t n_mine = gw < n_face ? (n_face - 1 - gw) / W + 1 : 0;
+    const int64_t n_items = n_mine * nc;         // item t: face gw + (t / nc) W, chunk t % nc
+    struct Info { int el, er; float lam, mu; };
+    auto info = [&](int64_t t) {
+        Info r{-1, -1, 0.f, 0.f};
+        if (t < n_items) {
+            const int64_t f = gw + (t / nc) * W;
+            r.el = fl[f]; r.er = fr[f]; r.lam = lamf[f]; r.mu = muf[f];
+        }
+        return r;
+    };
+    // the 32 shots' rows of an item are 32 x 18 chunks of 16 bytes, copied in order by the warp
+    // (one instruction covers 2-3 shot rows: the shots lie a whole vector apart in memory, and 32
+    // of them per instruction would fall on the same memory partitions)
+    constexpr int CPR = 2 * NVS / 4;   // chunks per shot row
+    auto issue = [&](int64_t t, const Info& I) {   // every lane: a share of the rows, and of the D~ block
+        if (t < n_items) {
+            const int64_t f = gw + (t / nc) * W;
+            const int c0 = (int)(t % nc) * 32;
+            float* buf = vbuf + (t & 1) * F::VBUF;
+#pragma unroll
+            for (int u = 0; u < CPR; ++u) {
+                const int ci = lane + 32 * u, sl = ci / CPR, part = ci % CPR;
+                const int side = part >= NVS / 4, j = side ? part - NVS / 4 : part;
+                const bool ok = c0 + sl < nshots && (side == 0 || I.er >= 0);
+                const int e = side ? I.er : I.el;
+                const float* src = x + (ok ? (int64_t)(c0 + sl) * nvec + (int64_t)e * NVS + 4 * j : 0);
+                cp_async16(buf + sl * F::ROW + side * NVS + 4 * j, src, ok);
+            }
+            float* db = dbuf + (t & 1) * F::DFACE;
+            const float* src = D + f * (int64_t)F::DFACE;
+            for (int j = lane; j < F::DFACE / 4; j += 32) cp_async16(db + 4 * j, src + 4 * j, true);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    Info I0 = info(0), I1 = info(1);
+    issue(0, I0);
+    for (int64_t t = 0; t < n_items; ++t) {
+        issue(t + 1, I1);
+        const Info I2 = info(t + 2);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncwarp();
+        float* row = vbuf + (t & 1) * F::VBUF + lane * F::ROW;
+        const float* sD = dbuf + (t & 1) * F::DFACE;
+        // ---- v' = scale S v over the time nodes, rows (s, k, b), N_phi values each
+        float v[2][2][NG][NP];
+#pragma unroll
+        for (int j = 0; j < 2 * NVS / 4; ++j) {
+            const float4 q = reinterpret_cast<const float4*>(row)[j];
+            const float e4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * j + u, s = e / NVS, r = e % NVS;
+                v[s][r / (NG * NP)][(r / NP) % NG][r % NP] = e4[u];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int n = 0; n < NP; ++n) {
+                    float w[NG];
+#pragma unroll
+                    for (int b = 0; b < NG; ++b) {
+                        float a = 0.f;
+#pragma unroll
+                        for (int b2 = 0; b2 < NG; ++b2) a = fmaf(Sm[b][b2], v[s][k][b2][n], a);
+                        w[b] = a;
+                    }
+#pragma unroll
+                    for (int b = 0; b < NG; ++b) v[s][k][b][n] = w[b];
+                }
+        const float lam = I0.lam, mu = I0.mu, dg = 2.f * mu + lam;
+        float yv[2][2][NG][NP];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int b = 0; b < NG; ++b)
+#pragma unroll
+                    for (int n = 0; n < NP; ++n) yv[s][k][b][n] = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            float Dc[2][2][NP];   // D~_s[l][n][m]
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int l = 0; l < 2; ++l)
+#pragma unroll
+                    for (int n = 0; n < NP; ++n) Dc[s][l][n] = sD[((s * 2 + l) * NP + n) * NP + m];
+            float h[3][NG];
+#pragma unroll
+            for (int b = 0; b < NG; ++b) {
+                float g[2][2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        float a = 0.f;
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int n = 0; n < NP; ++n) a = fmaf(Dc[s][l][n], v[s][k][b][n], a);
+                        g[k][l] = a;
+                    }
+                h[0][b] = dg * g[0][0] + lam * g[1][1];
+                h[1][b] = lam * g[0][0] + dg * g[1][1];
+                h[2][b] = mu * (g[0][1] + g[1][0]);
+            }
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int b = 0; b < NG; ++b)
+#pragma unroll
+                    for (int n = 0; n < NP; ++n) {
+                        // k = 0: components (xx, xy) with l = 0, 1; k = 1: (xy, yy)
+                        yv[s][0][b][n] = fmaf(Dc[s][0][n], h[0][b], fmaf(Dc[s][1][n], h[2][b], yv[s][0][b][n]));
+                        yv[s][1][b][n] = fmaf(Dc[s][0][n], h[2][b], fmaf(Dc[s][1][n], h[1][b], yv[s][1][b][n]));
+                    }
+        }
+        // ---- outputs back through the lane's row, then vector additions along each shot's rows
+#pragma unroll
+        for (int j = 0; j < 2 * NVS / 4; ++j) {
+            float e4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * j + u, s = e / NVS, r = e % NVS;
+                e4[u] = yv[s][r / (NG * NP)][(r / NP) % NG][r % NP];
+            }
+            reinterpret_cast<float4*>(row)[j] = make_float4(e4[0], e4[1], e4[2], e4[3]);
+        }
+        __syncwarp();
+        const int c0 = (int)(t % nc) * 32;
+        const float* rows = vbuf + (t & 1) * F::VBUF;
+        if (lane < 2 * NVS / 4) {
+            const bool right = lane >= NVS / 4;
+            const int es = right ? I0.er : I0.el, q = right ? lane - NVS / 4 : lane;
+            if (es >= 0) {
+                for (int j = 0; j < 32 && c0 + j < nshots; ++j) {
+                    const float4 val = reinterpret_cast<const float4*>(rows + j * F::ROW)[lane];
+                    red_add4(y0 + (int64_t)(c0 + j) * nvec + (int64_t)es * NVS + 4 * q, val);
+                }
+            }
+        }
+        __syncwarp();   // the rows and the D~ block are free for the item after next
+        I0 = I1;
+        I1 = I2;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <int DIM, int NP, int NG, typename R>
 static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* muf, const R* x, const int* xidx,
                                int64_t ld, R* y, double scale, int nshots) {
@@ -722,6 +925,22 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
         else go(face_apply_tma_kernel<DIM, NP, NG, R, 1>);
         note_launch(c);
         return cudaGetLastError();
+    }
+    if constexpr (DIM == 2 && NP == 6 && NG == 3 && std::is_same<R, float>::value) {
+        // batches of 16 shots or more: one lane per shot
+        if (nshots >= 16 && (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(D) % 16 == 0) &&
+            (reinterpret_cast<uintptr_t>(y) % 16 == 0) && (ld * (int64_t)sizeof(R)) % 16 == 0 &&
+            (c->nvel * (int64_t)sizeof(R)) % 16 == 0) {
+            using SF = FaceShots;
+            const int wpb = c->tune.face_wpb;
+            const size_t smem = sizeof(float) * (size_t)wpb * SF::PER_WARP;
+            const int64_t blocks = std::min<int64_t>((c->n_face + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
+            cudaFuncSetAttribute(face_apply_shots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            face_apply_shots_kernel<<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(
+                c->n_face, c->d_face_l, c->d_face_r, D, lamf, muf, c->d_rt, x, xidx, ld, y, (float)scale, nshots, c->nvel);
+            note_launch(c);
+            return cudaGetLastError();
+        }
     }
     using F = FaceReg<DIM, NP, NG, R>;
     const int wpb = c->tune.face_wpb;
