@@ -444,7 +444,7 @@ __global__ void gm_scale0_kernel(int64_t nvec, const DevScalars* __restrict__ sc
 
 // slot k, shot s: sum_i V_k[i] w[i] over the shot's segment, k = 0..j (basis columns at stride ldv)
 template <typename R>
-__global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
+__global__ void __launch_bounds__(256, 4) gm_mdot_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
                                                       const R* __restrict__ V, const R* __restrict__ w,
                                                       double* __restrict__ part) {
     constexpr int VW = VL<R>::W;
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(256) gm_mdot_kernel(int64_t nvec, int64_t ldv,
 // Second Gram-Schmidt pass fused with the first subtraction:
 // w_s <- w_s - sum_k h1_s[k] V_k, then partials of V_k . w_s for the re-orthogonalisation.
 template <typename R>
-__global__ void __launch_bounds__(256) gm_orth_fused_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
+__global__ void __launch_bounds__(256, 3) gm_orth_fused_kernel(int64_t nvec, int64_t ldv, const DevScalars* __restrict__ sc,
                                                             const ShotScalars* __restrict__ ss, const R* __restrict__ V,
                                                             R* __restrict__ w, double* __restrict__ part) {
     constexpr int VW = VL<R>::W;
