@@ -382,11 +382,165 @@ __global__ void __launch_bounds__(128) pre1_apply_reg_kernel(int64_t n_elem, con
     }
 }
 
+// Multi-shot FP32 variant for 2D, p = 2 (d N_phi = 12, N_gamma = 3), batches of 16 shots or
+// more: one lane per shot.  A warp takes an element and 32 shots at a time; the element's V
+// (12 x 12) and B (12 blocks of 3 x 3) are copied to shared memory once and read by all lanes
+// at once, and each lane computes u = V^T r, w = B u, z = V w for its shot in registers.  The
+// rows of r of the next (element, 32 shots) item are copied by the warp in order (cp.async)
+// while the current one is computed, and z goes back through the same shared rows to
+// 16-byte stores along each shot's element row.
+struct Pre1Shots {
+    static constexpr int NP = 6, NG = 3, N = 2 * NP, NV = N * NG;   // 36 values per element
+    static constexpr int ROW = 44;                                  // 11 x 16 bytes (odd)
+    static constexpr int RBUF = 32 * ROW;
+    static constexpr int VB = N * N + N * NG * NG;                  // V then B: 144 + 108
+    static constexpr int PER_WARP = 2 * RBUF + 2 * VB;
+    static_assert(NV <= ROW && (ROW / 4) % 2 == 1 && (VB * 4) % 16 == 0 && (N * N * 4) % 16 == 0, "layout");
+};
+
+__device__ __forceinline__ void pre_cp16(float* dst, const float* src, bool on) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(on ? 16u : 0u)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(128) pre1_apply_shots_kernel(int64_t n_elem, const float* __restrict__ V,
+                                                               const float* __restrict__ B, const float* __restrict__ r,
+                                                               const int* __restrict__ ridx, int64_t ld_vec,
+                                                               float* __restrict__ z0, int nshots, int64_t nvec) {
+    using P = Pre1Shots;
+    constexpr int NP = P::NP, NG = P::NG, N = P::N, NV = P::NV;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    if (ridx) r += (int64_t)(*ridx) * ld_vec;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    float* rbuf = reinterpret_cast<float*>(smraw) + warp * P::PER_WARP;
+    float* vbb = rbuf + 2 * P::RBUF;
+    const int nc = (nshots + 31) >> 5;
+    const int64_t gw = blockIdx.x * (int64_t)wpb + warp, W = (int64_t)gridDim.x * wpb;
+    const int64_t n_mine = gw < n_elem ? (n_elem - 1 - gw) / W + 1 : 0;
+    const int64_t n_items = n_mine * nc;
+    constexpr int CPR = NV / 4;   // 16-byte chunks per shot row
+    auto issue = [&](int64_t t) {
+        if (t < n_items) {
+            const int64_t e = gw + (t / nc) * W;
+            const int c0 = (int)(t % nc) * 32;
+            float* buf = rbuf + (t & 1) * P::RBUF;
+#pragma unroll
+            for (int u = 0; u < CPR; ++u) {
+                const int ci = lane + 32 * u, sl = ci / CPR, j = ci % CPR;
+                const bool ok = c0 + sl < nshots;
+                pre_cp16(buf + sl * P::ROW + 4 * j, r + (ok ? (int64_t)(c0 + sl) * nvec + e * NV + 4 * j : 0), ok);
+            }
+            float* vb = vbb + (t & 1) * P::VB;
+            for (int j = lane; j < N * N / 4; j += 32) pre_cp16(vb + 4 * j, V + e * (N * N) + 4 * j, true);
+            for (int j = lane; j < N * NG * NG / 4; j += 32)
+                pre_cp16(vb + N * N + 4 * j, B + e * (N * NG * NG) + 4 * j, true);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    issue(0);
+    for (int64_t t = 0; t < n_items; ++t) {
+        issue(t + 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncwarp();
+        float* row = rbuf + (t & 1) * P::RBUF + lane * P::ROW;
+        const float* sV = vbb + (t & 1) * P::VB;
+        const float* sB = sV + N * N;
+        // r[row][a], row = (k, n), from the element layout [k][a][n]
+        float rv[N][NG];
+#pragma unroll
+        for (int j = 0; j < CPR; ++j) {
+            const float4 q = reinterpret_cast<const float4*>(row)[j];
+            const float e4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = 4 * j + u, k = i / (NG * NP), a = (i / NP) % NG, n = i % NP;
+                rv[k * NP + n][a] = e4[u];
+            }
+        }
+        // w[q] = B_q (V^T r)[q]
+        float w[N][NG];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            float u[NG];
+#pragma unroll
+            for (int a = 0; a < NG; ++a) u[a] = 0.f;
+#pragma unroll
+            for (int rr = 0; rr < N; ++rr) {
+                const float vq = sV[rr * N + q];
+#pragma unroll
+                for (int a = 0; a < NG; ++a) u[a] = fmaf(vq, rv[rr][a], u[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < NG; ++a) {
+                float s = 0.f;
+#pragma unroll
+                for (int b = 0; b < NG; ++b) s = fmaf(sB[(q * NG + a) * NG + b], u[b], s);
+                w[q][a] = s;
+            }
+        }
+        // z = V w, written back to the lane's row in the element layout
+#pragma unroll
+        for (int rr = 0; rr < N; ++rr) {
+            float acc[NG];
+#pragma unroll
+            for (int a = 0; a < NG; ++a) acc[a] = 0.f;
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                const float v = sV[rr * N + q];
+#pragma unroll
+                for (int a = 0; a < NG; ++a) acc[a] = fmaf(v, w[q][a], acc[a]);
+            }
+            const int k = rr / NP, n = rr % NP;
+#pragma unroll
+            for (int a = 0; a < NG; ++a) rv[rr][a] = acc[a];
+            (void)k; (void)n;
+        }
+#pragma unroll
+        for (int j = 0; j < CPR; ++j) {
+            float e4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = 4 * j + u, k = i / (NG * NP), a = (i / NP) % NG, n = i % NP;
+                e4[u] = rv[k * NP + n][a];
+            }
+            reinterpret_cast<float4*>(row)[j] = make_float4(e4[0], e4[1], e4[2], e4[3]);
+        }
+        __syncwarp();
+        const int64_t e = gw + (t / nc) * W;
+        const int c0 = (int)(t % nc) * 32;
+        const float* rows = rbuf + (t & 1) * P::RBUF;
+#pragma unroll
+        for (int u = 0; u < CPR; ++u) {
+            const int ci = lane + 32 * u, sl = ci / CPR, j = ci % CPR;
+            if (c0 + sl < nshots)
+                *reinterpret_cast<float4*>(z0 + (int64_t)(c0 + sl) * nvec + e * NV + 4 * j) =
+                    reinterpret_cast<const float4*>(rows + sl * P::ROW)[j];
+        }
+        __syncwarp();   // the rows and the V, B blocks are free for the item after next
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename R>
 static bool pre1_apply_fast(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld,
                             cudaError_t* err, int nshots) {
     const int64_t blocks = std::min<int64_t>((c->n_elem + 3) / 4, 1 << 30);
     const int d = c->dim, np = c->Nphi, ng = c->Ng;
+    if constexpr (std::is_same<R, float>::value) {
+        if (d == 2 && np == 6 && ng == 3 && nshots >= 16 && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
+            reinterpret_cast<uintptr_t>(z) % 16 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
+            reinterpret_cast<uintptr_t>(B) % 16 == 0 && (ld * (int64_t)sizeof(R)) % 16 == 0) {
+            constexpr int wpb = 4;
+            const size_t smem = sizeof(float) * wpb * Pre1Shots::PER_WARP;
+            const int64_t nb = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, (int64_t)c->n_sm * 16);
+            cudaFuncSetAttribute(pre1_apply_shots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            pre1_apply_shots_kernel<<<(unsigned)nb, 32 * wpb, smem, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z, nshots,
+                                                                                c->nvel);
+            note_launch(c);
+            *err = cudaGetLastError();
+            return true;
+        }
+    }
 #define STDG_PRE_FAST(D_, NP_, NG_)                                                                        \
     if (d == D_ && np == NP_ && ng == NG_) {                                                              \
         pre1_apply_reg_kernel<D_, NP_, NG_, R><<<(unsigned)blocks, 128, 0, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z, nshots, c->nvel); \

@@ -500,6 +500,35 @@ def test_tensor_core_stencil_preconditioner_matches_oracle_per_shot(n_shots):
     assert out["mixed"] < 2e-3
 
 
+@pytest.mark.parametrize("n_shots", [9, 20, 64])
+def test_stacked_block_jacobi_matches_oracle_per_shot(n_shots):
+    # Pre1 (Appendix A, Eq. pre1) applied to a stacked vector of shots: 9 shots take the
+    # register kernel (shots looped per element), 20 and 64 the kernel with one lane per shot
+    # (a partial and two full groups of 32); every shot against the oracle's block-diagonal
+    # inverse.  FP32 blocks bound the mixed result; a layout mistake gives errors of order one.
+    torch = need_gpu()
+    from oracle.precond import pre1
+    w = synth.scaled("c4", ny=8, steps=1, n_shots=n_shots)
+    sim = oracle_sim(w)
+    n = sim.A.shape[0]
+    R = np.random.default_rng(17).normal(size=(n_shots, n))
+    P = pre1(sim.A, w.n_elem)
+    ref = np.array([P @ R[k] for k in range(n_shots)])
+    out = {}
+    for precision, fp32 in (("mixed", True), ("fp64", False)):
+        s = gpu_solver(w, precision=precision, with_receivers=False, preconditioner=1)
+        dt = torch.float32 if fp32 else torch.float64
+        rd = torch.tensor(R.ravel(), dtype=dt, device="cuda")
+        zd = torch.zeros_like(rd)
+        torch.cuda.synchronize()
+        s.apply_preconditioner_device(w.dt, rd.data_ptr(), zd.data_ptr(), fp32=fp32)
+        Z = zd.cpu().numpy().astype(np.float64).reshape(n_shots, n)
+        out[precision] = max(rel_l2(Z[k], ref[k]) for k in range(n_shots))
+    print("stacked Pre1, %d shots: FP32 %.3g, FP64 %.3g" % (n_shots, out["mixed"], out["fp64"]))
+    assert out["fp64"] < max(1e-9, 1e4 * oracle_rounding_spread(sim, w))
+    assert out["mixed"] < 1e-5
+
+
 def test_tensor_core_stencil_preconditioner_keeps_iteration_counts():
     # the TF32 local step must not degrade the preconditioner: a stacked mixed-precision solve
     # (tensor-core local step) takes about as many iterations as its slowest shot solved alone
