@@ -190,10 +190,12 @@ def e2e_steps(torch, s, w, steps, stream):
     return dt * 1e3, v.nbytes + sig.nbytes, v.nbytes + sig.nbytes + rec_bytes
 
 
-# DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the
-# 16,384-triangle copy of the 2D p = p_gamma = 3 construction (profiles/traffic_face_pre2_c2_16k.md),
-# scaled by the units one launch processes.  Valid for that shape only.
-TRAFFIC_PER_UNIT = {"face_fp32": (50544128 + 4608) / 24768, "pre2_local_fp32": (429949184 + 2444032) / 16384}
+# DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum), scaled
+# by the units one launch processes; valid for the 2D p = p_gamma = 3 shape only: the tiled
+# face kernel per face on the 102,400-triangle copy of the construction
+# (profiles/face_tile_c2_102k.md), the Pre2 local step per element on the 16,384-triangle copy
+# (profiles/traffic_face_pre2_c2_16k.md).
+TRAFFIC_PER_UNIT = {"face_fp32": (344876032 + 27466752) / 154080, "pre2_local_fp32": (429949184 + 2444032) / 16384}
 
 
 def _traffic(w, key, units):
