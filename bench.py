@@ -234,7 +234,10 @@ def face_kernel_roofline(s, w, fp32, n_face, pk, fp64_pk=None):
     if fp32:
         peak = float(pk.get("hbm_gbs", 6800.0))
         achieved = bytes_alg / (ms * 1e-3) / 1e9
-        return {"kernel": "face_apply_tma_kernel<float>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+        # the tiled kernels serve 2D p = 3 and 3D p = 2; other shapes, the one-face-per-warp kernel
+        tiled = (d == 2 and w.p == 3 and w.p_gamma == 3) or (d == 3 and w.p == 2 and w.p_gamma == 2)
+        name = ("face_apply_tile_kernel" if d == 2 else "face_apply_tile3_kernel") if tiled else "face_apply_tma_kernel<float>"
+        return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(w, "face_fp32", n_face),
                 "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(flops), "ms_per_launch": round(ms, 4),
                 "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
@@ -314,7 +317,6 @@ def c3_section(torch, args, stream, dist, world, pk, fp64_pk):
                     "tuning": s.tuning}
     out["face_fp32"] = face_kernel_roofline(s, w, True, n_face, pk)
     out["face_fp64"] = face_kernel_roofline(s, w, False, n_face, pk, fp64_pk)
-    out["face_fp32"]["kernel"] = "face_apply_tma_kernel<3,10,3,float>"
     out["face_fp64"]["kernel"] = "face_apply_kernel<3,10,double>"
     s.close()
     if args.c3_fp64_steps > 0:

@@ -682,6 +682,287 @@ __global__ void __maxnreg__(MAXREG) face_apply_tile_kernel(int64_t n_face, const
 }
 
 // ---------------------------------------------------------------------------------
+// Tiled single-shot FP32 kernel for 3D, p = 2 (d = 3, N_phi = 10, N_gamma = 3).  Per face the
+// gather is 9 x 30 x 20 (rows (k,b), columns (l,m), contraction (s,n)) and the scatter
+// 9 x 20 x 30.  Three faces per warp, nine lanes each (lanes 27..31 idle); lane (k, l) owns
+// the three time-node rows (k, b) and the ten columns (l, m):
+//   gather:  g[k][l][b][m] over the full (s, n) contraction, tiles (Rg, l), Rg = 0..3;
+//   E : g :  off-diagonal lanes take g[l][k] from the transposed lane, diagonal lanes the two
+//            other diagonal blocks (the trace): two shuffles per value;
+//   S t   :  in registers, slot j = time node (l + j) % 3 (the lane's own rows of S);
+//   scatter: partial sums over the lane's ten columns with the same tiles, reduced over the
+//            three l-lanes of its k in two shuffle rounds (round r reads slot 3 - r of lane
+//            l + r), so that each lane ends with time node l of every row group.
+// D~ per face: 12 tiles of 5 rows (s, n) x 10 columns m of one l, 52 floats each (two of
+// padding), rows paired as in the 2D tiled kernel; tile (Rg, l) at position 3Rg + l (13
+// 16-byte chunks apart: the three tiles a face's lanes read lie in distinct banks).  The
+// element rows (90 values, 360 bytes: not a 16-byte multiple) are copied by the lanes in
+// 8-byte cp.async pieces; the tiles by cp.async.bulk on the warp's mbarrier.
+// ---------------------------------------------------------------------------------
+struct FaceTile3 {
+    static constexpr int NP = 10, NG = 3, NVS = 3 * NG * NP;   // 90 values per element
+    static constexpr int TS = 52;                    // floats per 5 x 10 tile
+    static constexpr int DT = 12 * TS;               // 624 floats per face
+    static constexpr int XOFF = DT, XR = NVS;
+    static constexpr int FPW = 3;                    // faces per warp
+    static constexpr int FACE_SEG = 816;             // 204 x 16 bytes: faces 4 bank groups apart
+    static constexpr int STAGE = FPW * FACE_SEG;
+    static constexpr int PER_WARP = 2 * STAGE;
+    static_assert(XOFF + 2 * XR <= FACE_SEG && (DT * 4) % 16 == 0, "3D tile kernel layout");
+};
+
+__host__ __device__ inline bool tile3_slot_rc(int slot, int odd, int* r, int* c) {
+    if (slot < 20) { *c = slot >> 1; *r = (slot & 1) + (odd ? 1 : 0); return true; }
+    if (slot < 40) { *c = (slot - 20) >> 1; *r = (slot & 1) + (odd ? 3 : 2); return true; }
+    if (slot < 50) { *c = slot - 40; *r = odd ? 0 : 4; return true; }
+    return false;
+}
+
+// FP64 D~ [face][s][l][n][m] -> FP32 tiles
+__global__ void tile3_d32_kernel(int64_t n_face, const double* __restrict__ D, float* __restrict__ Dt) {
+    using F = FaceTile3;
+    const int64_t n = n_face * F::DT;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = i / F::DT;
+        const int w = (int)(i % F::DT), pos = w / F::TS, slot = w % F::TS;
+        const int Rg = pos / 3, l = pos % 3;
+        int r, c;
+        float v = 0.f;
+        if (tile3_slot_rc(slot, Rg & 1, &r, &c))
+            v = (float)D[f * (2 * 3 * F::NP * F::NP) + ((((Rg >> 1) * 3 + l) * F::NP) + 5 * (Rg & 1) + r) * F::NP + c];
+        Dt[i] = v;
+    }
+}
+
+__device__ __forceinline__ void cp_async8(float* dst, const float* src, bool on) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(on ? 8u : 0u)
+                 : "memory");
+}
+
+template <int MAXREG>
+__global__ void __maxnreg__(MAXREG) face_apply_tile3_kernel(int64_t n_face, const int32_t* __restrict__ fl,
+                                                            const int32_t* __restrict__ fr, const float* __restrict__ Dt,
+                                                            const float* __restrict__ lamf, const float* __restrict__ muf,
+                                                            const RefTables* __restrict__ rtp, const float* __restrict__ x,
+                                                            const int* __restrict__ xidx, int64_t ld, float* __restrict__ y,
+                                                            float scale, int* __restrict__ err) {
+    using F = FaceTile3;
+    constexpr int TS = F::TS, NVS = F::NVS, NG = F::NG, FPW = F::FPW;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[4][2];
+    if (xidx) x += (int64_t)(*xidx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    float* base = reinterpret_cast<float*>(smraw) + warp * F::PER_WARP;
+    for (int t = lane; t < F::PER_WARP; t += 32) base[t] = 0.f;
+    const uint32_t bar0 = smem_u32(&bars[warp][0]), bar1 = smem_u32(&bars[warp][1]);
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool active = lane < 9 * FPW;
+    const int fq = active ? lane / 9 : FPW - 1, kl = active ? lane % 9 : 0, k = kl / 3, l = kl % 3;
+    const int fb = fq * 9;                            // first lane of the face
+    const bool diag = k == l;
+    // shuffle sources: E:g (transposed lane, or the two other diagonal lanes) and the two
+    // rounds of the reduce over the l-lanes
+    const int src1 = active ? (diag ? fb + 4 * ((k + 1) % 3) : fb + 3 * l + k) : lane;
+    const int src2 = active ? (diag ? fb + 4 * ((k + 2) % 3) : lane) : lane;
+    const int srr1 = active ? fb + 3 * k + (l + 1) % 3 : lane;
+    const int srr2 = active ? fb + 3 * k + (l + 2) % 3 : lane;
+    float Sm[NG][NG];   // scale * S, slot j = time node (l + j) % 3
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+#pragma unroll
+        for (int b = 0; b < NG; ++b) Sm[j][b] = scale * (float)rtp->S[((l + j) % 3) * NG + b];
+    const int64_t n_grp = (n_face + FPW - 1) / FPW;
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    constexpr long kPollLimit = 1L << 24;
+
+    auto load_ids = [&](int64_t pp, int (&el)[FPW], int (&er)[FPW]) {
+#pragma unroll
+        for (int i = 0; i < FPW; ++i) {
+            const int64_t f = FPW * pp + i;
+            const bool ok = pp < n_grp && f < n_face;
+            el[i] = ok ? fl[f] : -1;
+            er[i] = ok ? fr[f] : -1;
+        }
+    };
+    auto issue = [&](int64_t p, int st, const int (&el)[FPW], const int (&er)[FPW]) {   // every lane
+        float* sg = base + st * F::STAGE;
+        if (lane == 0) {
+            const uint32_t bar = st ? bar1 : bar0;
+            uint32_t bytes = 0;
+#pragma unroll
+            for (int i = 0; i < FPW; ++i)
+                if (el[i] >= 0) bytes += F::DT * sizeof(float);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, bytes);
+#pragma unroll
+            for (int i = 0; i < FPW; ++i)
+                if (el[i] >= 0) bulk_g2s(smem_u32(sg + i * F::FACE_SEG), Dt + (FPW * p + i) * (int64_t)F::DT,
+                                         F::DT * sizeof(float), bar);
+        }
+        // element rows: FPW faces x 2 sides x 45 pieces of 8 bytes
+#pragma unroll
+        for (int u = 0; u < (FPW * 2 * NVS / 2 + 31) / 32; ++u) {
+            const int ci = lane + 32 * u;
+            if (ci < FPW * 2 * NVS / 2) {
+                const int i = ci / NVS, side = (ci % NVS) / (NVS / 2), j = ci % (NVS / 2);
+                static_assert(FPW == 3, "face selection below");
+                const int eli = i == 0 ? el[0] : (i == 1 ? el[1] : el[2]);   // selects, not a local array
+                const int eri = i == 0 ? er[0] : (i == 1 ? er[1] : er[2]);
+                const int e = side ? eri : eli;
+                const bool ok = eli >= 0 && e >= 0;
+                cp_async8(sg + i * F::FACE_SEG + F::XOFF + side * F::XR + 2 * j,
+                          ok ? x + (int64_t)e * NVS + 2 * j : x, ok);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto fetch = [&](int64_t pp, int& a, int& b, float& lm, float& m) {
+        const int64_t ff = FPW * pp + fq;
+        const bool ok = active && pp < n_grp && ff < n_face;
+        a = ok ? fl[ff] : -1;
+        b = ok ? fr[ff] : -1;
+        lm = ok ? lamf[ff] : 0.f;
+        m = ok ? muf[ff] : 0.f;
+    };
+
+    int64_t p = blockIdx.x * (int64_t)wpb + warp;
+    int idl[FPW], idr[FPW];
+    load_ids(p, idl, idr);
+    if (p < n_grp) issue(p, 0, idl, idr);
+    load_ids(p + stride, idl, idr);
+    int el, er;
+    float lam, mu;
+    fetch(p, el, er, lam, mu);
+    uint32_t ph0 = 0, ph1 = 0;
+    int st = 0;
+    for (; p < n_grp; p += stride) {
+        const int64_t pn = p + stride;
+        if (pn < n_grp) issue(pn, st ^ 1, idl, idr);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        int nidl[FPW], nidr[FPW];
+        load_ids(pn + stride, nidl, nidr);
+        int el_n, er_n;
+        float lam_n, mu_n;
+        fetch(pn, el_n, er_n, lam_n, mu_n);
+        if (!__all_sync(FULL, mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit))) {
+            if (lane == 0) atomicExch(err, 1);
+            bool drained = mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit);
+            if (pn < n_grp) drained = mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit) && drained;
+            if (!drained && lane == 0) atomicExch(err, 2);
+            break;
+        }
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncwarp();
+        if (st) ph1 ^= 1u; else ph0 ^= 1u;
+        const float* seg = base + st * F::STAGE + fq * F::FACE_SEG;
+        // ---- gather: rows (k, b), columns (l, m), m = 0..9
+        float2 acc[NG][10];
+#pragma unroll
+        for (int b = 0; b < NG; ++b)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) acc[b][c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int Rg = 0; Rg < 4; ++Rg) {   // one tile live at a time (rolled loop)
+            const int s = Rg >> 1, h = Rg & 1;
+            {
+                float T[TS];   // the tile, read once for the three time nodes
+                {
+                    const float4* tp = reinterpret_cast<const float4*>(seg + TS * (3 * Rg + l));
+#pragma unroll
+                    for (int j = 0; j < TS / 4; ++j) {
+                        const float4 q = tp[j];
+                        T[4 * j] = q.x; T[4 * j + 1] = q.y; T[4 * j + 2] = q.z; T[4 * j + 3] = q.w;
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < NG; ++b) {
+                    const float2* vr = reinterpret_cast<const float2*>(seg + F::XOFF + s * F::XR + (3 * k + b) * F::NP);
+                    const float2 pa = vr[h ? 3 : 0], pb = vr[h ? 4 : 1], m2 = vr[2];
+                    const float sg = h ? m2.y : m2.x;
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) {
+                        acc[b][c] = ffma2(make_float2(T[2 * c], T[2 * c + 1]), pa, acc[b][c]);
+                        acc[b][c] = ffma2(make_float2(T[20 + 2 * c], T[21 + 2 * c]), pb, acc[b][c]);
+                        acc[b][c].x = fmaf(T[40 + c], sg, acc[b][c].x);
+                    }
+                }
+            }
+        }
+        // ---- t = E_j : g (two shuffles per value), h = scale S t in the lane's slot order
+        float tv[NG][10];
+#pragma unroll
+        for (int b = 0; b < NG; ++b)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                const float gv = acc[b][c].x + acc[b][c].y;
+                const float x1 = __shfl_sync(FULL, gv, src1);
+                const float x2 = __shfl_sync(FULL, gv, src2);
+                tv[b][c] = diag ? fmaf(2.f * mu, gv, lam * (gv + x1 + x2)) : mu * (gv + x1);
+            }
+        float hv[NG][10];
+#pragma unroll
+        for (int j = 0; j < NG; ++j)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                float a = 0.f;
+#pragma unroll
+                for (int b2 = 0; b2 < NG; ++b2) a = fmaf(Sm[j][b2], tv[b2][c], a);
+                hv[j][c] = a;
+            }
+        // ---- scatter: partial sums over this lane's columns, reduced over the three l-lanes
+#pragma unroll 1
+        for (int Rg = 0; Rg < 4; ++Rg) {
+            float T[TS];
+            {
+                const float4* tp = reinterpret_cast<const float4*>(seg + TS * (3 * Rg + l));
+#pragma unroll
+                for (int j = 0; j < TS / 4; ++j) {
+                    const float4 q = tp[j];
+                    T[4 * j] = q.x; T[4 * j + 1] = q.y; T[4 * j + 2] = q.z; T[4 * j + 3] = q.w;
+                }
+            }
+            float R[NG][5];
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                float2 oA = make_float2(0.f, 0.f), oB = oA;
+                float oS = 0.f;
+#pragma unroll
+                for (int c = 0; c < 10; ++c) {
+                    const float hc = hv[j][c];
+                    oA = ffma2(make_float2(T[2 * c], T[2 * c + 1]), make_float2(hc, hc), oA);
+                    oB = ffma2(make_float2(T[20 + 2 * c], T[21 + 2 * c]), make_float2(hc, hc), oB);
+                    oS = fmaf(T[40 + c], hc, oS);
+                }
+                R[j][0] = oA.x; R[j][1] = oA.y; R[j][2] = oB.x; R[j][3] = oB.y; R[j][4] = oS;
+            }
+            float Y[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                Y[v] = R[0][v] + __shfl_sync(FULL, R[2][v], srr1) + __shfl_sync(FULL, R[1][v], srr2);
+            const int es = (Rg >> 1) == 0 ? el : er, odd = Rg & 1;
+            if (es >= 0) {
+                float* yr = y + (int64_t)es * NVS + (3 * k + l) * F::NP + 5 * odd;
+                red_add2(yr + odd, Y[0], Y[1]);
+                red_add2(yr + 2 + odd, Y[2], Y[3]);
+                red_add1(yr + (odd ? 0 : 4), Y[4]);
+            }
+        }
+        __syncwarp();   // stage st is free for the next group
+        st ^= 1;
+        el = el_n; er = er_n; lam = lam_n; mu = mu_n;
+#pragma unroll
+        for (int i = 0; i < FPW; ++i) { idl[i] = nidl[i]; idr[i] = nidr[i]; }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------
 // Multi-shot FP32 kernel for 2D, p = 2 (d = 2, N_phi = 6, N_gamma = 3): one lane per shot.
 // A warp takes a face and 32 shots of a stacked vector at a time.  Each lane keeps its shot's
 // two element rows (72 values) and its 72 outputs in registers; the face's D~ block is read
@@ -912,6 +1193,26 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
             return cudaGetLastError();
         }
     }
+    if constexpr (DIM == 3 && NP == 10 && NG == 3 && std::is_same<R, float>::value) {
+        // the 3D tiled kernel, on the tiled copy of D~ made with the FP32 copy
+        if (nshots == 1 && c->d_err && c->d_Dt32 && D == c->d_D32 && reinterpret_cast<uintptr_t>(x) % 8 == 0 &&
+            reinterpret_cast<uintptr_t>(y) % 8 == 0 && (ld * (int64_t)sizeof(R)) % 8 == 0) {
+            using TF = FaceTile3;
+            const int wpb = c->tune.face_wpb;   // <= 4: the kernel's per-warp barriers
+            const size_t smem = sizeof(float) * (size_t)wpb * TF::PER_WARP;
+            const int64_t n_grp = (c->n_face + TF::FPW - 1) / TF::FPW;
+            const int64_t blocks = std::min<int64_t>((n_grp + wpb - 1) / wpb, (int64_t)c->n_sm * c->tune.face_bpsm);
+            auto go = [&](auto kern) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kern<<<(unsigned)blocks, 32 * wpb, smem, c->stream>>>(c->n_face, c->d_face_l, c->d_face_r, c->d_Dt32, lamf,
+                                                                     muf, c->d_rt, x, xidx, ld, y, (float)scale, c->d_err);
+            };
+            if (c->tune.face_cap) go(face_apply_tile3_kernel<168>);
+            else go(face_apply_tile3_kernel<255>);
+            note_launch(c);
+            return cudaGetLastError();
+        }
+    }
     if (nshots == 1 && aligned && c->d_err) {
         const int wpb = c->tune.face_wpb;   // <= 4: the kernel's launch bounds and its per-warp barriers
         const size_t smem = sizeof(R) * (size_t)wpb * T::PER_WARP;
@@ -964,10 +1265,15 @@ static cudaError_t launch_fast(stdg_ctx* c, const R* D, const R* lamf, const R* 
 }
 
 // FP32 tiles of D~ for the tiled (2,10,4) kernel; false for other shapes
-bool face_tiled_shape(const stdg_ctx* c) { return c->dim == 2 && c->Nphi == 10 && c->Ng == 4; }
-int64_t face_tiled_floats(const stdg_ctx* c) { return face_tiled_shape(c) ? c->n_face * FaceTile::DT : 0; }
+static bool tiled2(const stdg_ctx* c) { return c->dim == 2 && c->Nphi == 10 && c->Ng == 4; }
+static bool tiled3(const stdg_ctx* c) { return c->dim == 3 && c->Nphi == 10 && c->Ng == 3; }
+bool face_tiled_shape(const stdg_ctx* c) { return tiled2(c) || tiled3(c); }
+int64_t face_tiled_floats(const stdg_ctx* c) {
+    return tiled2(c) ? c->n_face * FaceTile::DT : tiled3(c) ? c->n_face * FaceTile3::DT : 0;
+}
 cudaError_t launch_tile_d32(stdg_ctx* c) {
-    tile_d32_kernel<<<(unsigned)(c->n_sm * 8), 256, 0, c->stream>>>(c->n_face, c->d_D, c->d_Dt32);
+    if (tiled2(c)) tile_d32_kernel<<<(unsigned)(c->n_sm * 8), 256, 0, c->stream>>>(c->n_face, c->d_D, c->d_Dt32);
+    else tile3_d32_kernel<<<(unsigned)(c->n_sm * 8), 256, 0, c->stream>>>(c->n_face, c->d_D, c->d_Dt32);
     note_launch(c);
     return cudaGetLastError();
 }

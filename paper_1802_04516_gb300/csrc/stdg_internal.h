@@ -114,7 +114,7 @@ struct stdg_ctx {
     double *d_L = nullptr;      // Cholesky factors of the dual mass matrices (lower, [face][m][m'])
     double *d_Mdual = nullptr;  // dual mass matrices (set-up workspace)
     float *d_D32 = nullptr;     // FP32 copy of D~
-    float *d_Dt32 = nullptr;    // FP32 D~ in 5 x 5 tiles (2D, p = 3 only: the tiled face kernel)
+    float *d_Dt32 = nullptr;    // FP32 D~ in tiles (2D p = 3 and 3D p = 2 only: the tiled face kernels)
     double *d_lamf = nullptr, *d_muf = nullptr, *d_rhoJ = nullptr;    // per face / element
     float *d_lamf32 = nullptr, *d_muf32 = nullptr, *d_rhoJ32 = nullptr;
 
