@@ -50,6 +50,9 @@ extern "C" {
 #define STDG_ENONFINITE (-7) /* a residual norm became NaN or Inf (e.g. an input that
                                 overflows); the solve stopped, the state is advanced but
                                 holds non-finite values                                 */
+#define STDG_EENERGY  (-8)  /* the energy check (stdg_set_energy_check) found a shot whose
+                                energy grew over a source-free stdg_step; the state is
+                                advanced                                                */
 
 enum stdg_scheme { STDG_SCHEME_CN = 0, STDG_SCHEME_STDG = 1 };
 enum stdg_precision { STDG_FP64 = 0, STDG_MIXED_FP32 = 1 };
@@ -159,6 +162,18 @@ int stdg_set_time(stdg_ctx* ctx, double t);
 
 /* Total energy of each shot's carried state (Eq. SP3F): out[n_shots]. */
 int stdg_energy(stdg_ctx* ctx, double* out);
+
+/* Energy-growth sentinel (Sec. 5, Theorem 4: without sources the discrete energy of the
+ * space-time scheme never increases from one slab to the next, and Crank-Nicolson keeps it).
+ * With enable != 0, every stdg_step on a context without point sources (none set, or
+ * amplitude a1 = 0) evaluates each shot's energy before and after the call and returns
+ * STDG_EENERGY when E_after > (1 + rel_tol) E_before for some shot, or E_after is not finite;
+ * the state, time and receiver records are advanced as for STDG_OK, and a status of the solve
+ * itself (STDG_ENOTCONV, STDG_ENONFINITE, ...) takes precedence.  rel_tol > -1: 0 or a small
+ * positive value allows rounding (FP64 about 1e-12, mixed precision the inner tolerance);
+ * a negative value demands a decrease by that fraction.  Off by default (two energy
+ * evaluations per call).  Returns STDG_OK or STDG_EINVAL (rel_tol <= -1 or not finite). */
+int stdg_set_energy_check(stdg_ctx* ctx, int enable, double rel_tol);
 
 /* Receiver records since the last stdg_set_receivers / stdg_set_sources:
  * out[n_shots][n_recorded_steps][n_rec][dim]; `cap` = capacity in doubles.

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libstdg.so")
 
 STDG_OK, STDG_EINVAL, STDG_EMESH, STDG_ENOMEM, STDG_ECUDA, STDG_ENOTCONV, STDG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 STDG_ENONFINITE = -7
+STDG_EENERGY = -8
 SCHEME = {"cn": 0, "stdg": 1}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_fp32": 1}
 
@@ -63,6 +64,7 @@ SIGNATURES = {
     "stdg_get_time": (C.c_int, [_P, _D]),
     "stdg_set_time": (C.c_int, [_P, C.c_double]),
     "stdg_energy": (C.c_int, [_P, _D]),
+    "stdg_set_energy_check": (C.c_int, [_P, C.c_int, C.c_double]),
     "stdg_read_receivers": (C.c_int, [_P, _D, C.c_int64]),
     "stdg_apply_operator": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_apply_operator_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
@@ -298,12 +300,18 @@ class Solver:
         self.n_rec = xr.shape[0]
         self._chk(self.lib.stdg_set_receivers(self.h, xr.shape[0], _d(xr)))
 
-    def step(self, dt, n_steps=1, allow_notconv=False):
+    def step(self, dt, n_steps=1, allow_notconv=False, allow=()):
         st = stdg_stats()
         rc = self.lib.stdg_step(self.h, dt, n_steps, C.byref(st))
         self.last_stats = st.as_dict()
-        self._chk(rc, allow=(STDG_ENOTCONV,) if allow_notconv else ())
+        self.last_rc = rc
+        self._chk(rc, allow=tuple(allow) + ((STDG_ENOTCONV,) if allow_notconv else ()))
         return self.last_stats
+
+    def set_energy_check(self, enable=True, rel_tol=0.0):
+        """Energy-growth sentinel around step (Theorem 4): STDG_EENERGY when a shot's energy
+        grows by more than rel_tol over a source-free step (negative rel_tol: demands a decrease)."""
+        self._chk(self.lib.stdg_set_energy_check(self.h, 1 if enable else 0, float(rel_tol)))
 
     @property
     def time(self):

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/stdg.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "stdg_internal.h"
@@ -665,7 +666,34 @@ int stdg_step(stdg_ctx* c, double dt, int n_steps, stdg_stats* out) {
     if (n_steps == 0) return STDG_OK;
     int rc = ensure_records(c, n_steps);
     if (rc != STDG_OK) return rc;
-    return solver_step(c, dt, n_steps, out);
+    // Theorem 4 bounds the energy only without sources
+    const bool check = c->echeck_on && !(c->have_sources && c->src_a1 != 0.0);
+    std::vector<double> e0, e1;
+    if (check) {
+        e0.resize(c->n_shots);
+        if ((rc = stdg_energy(c, e0.data())) != STDG_OK) return rc;
+    }
+    rc = solver_step(c, dt, n_steps, out);
+    if (check && rc == STDG_OK) {
+        e1.resize(c->n_shots);
+        if ((rc = stdg_energy(c, e1.data())) != STDG_OK) return rc;
+        for (int s = 0; s < c->n_shots; ++s)
+            if (!(e1[s] <= (1.0 + c->echeck_tol) * e0[s])) {   // also catches a non-finite energy
+                char msg[160];
+                std::snprintf(msg, sizeof msg, "energy of shot %d grew over a source-free step: %.17g -> %.17g", s,
+                              e0[s], e1[s]);
+                STDG_FAIL(c, STDG_EENERGY, msg);
+            }
+    }
+    return rc;
+}
+
+int stdg_set_energy_check(stdg_ctx* c, int enable, double rel_tol) {
+    CHECK_CTX(c);
+    if (!std::isfinite(rel_tol) || rel_tol <= -1.0) STDG_FAIL(c, STDG_EINVAL, "rel_tol must be finite and > -1");
+    c->echeck_on = enable != 0;
+    c->echeck_tol = rel_tol;
+    return STDG_OK;
 }
 
 int stdg_misfit_grad(stdg_ctx* c, double dt, int n_steps, const double* data, int checkpoint_every, double* loss,

@@ -157,6 +157,8 @@ struct stdg_ctx {
     // take_device_error after every call that can launch such a kernel.
     int* d_err = nullptr;
     bool wait_gave_up = false;   // the last take_device_error found the word set
+    bool echeck_on = false;      // energy-growth sentinel around stdg_step
+    double echeck_tol = 0.0;
 
     int n_sm = 152;              // multiprocessors of the context's device (grid sizing)
     stdg::Tuning tune;

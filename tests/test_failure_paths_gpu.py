@@ -6,7 +6,11 @@
 * an input that overflows: the residual sentinel stops the solve at once with
   STDG_ENONFINITE instead of iterating to the cap;
 * the device error word of the face kernel's bounded bulk-copy waits, set from the host:
-  reported once as STDG_ECUDA by the next checking call, then cleared.
+  reported once as STDG_ECUDA by the next checking call, then cleared;
+* the energy-growth sentinel (Theorem 4): silent on source-free steps, which dissipate
+  (space-time DG) or keep (Crank-Nicolson) the energy; tripped by a tolerance that demands
+  a decrease no step gives (a host-side setting), with the state advanced; skipped when
+  sources drive the solution.
 """
 import numpy as np
 import pytest
@@ -119,3 +123,56 @@ def test_bounded_wait_error_is_reported_once_and_cleared():
     s.apply_operator_device(w.dt, x.data_ptr(), y.data_ptr(), fp32=True)
     torch.cuda.synchronize()
     assert torch.isfinite(y).all() and float(y.abs().max()) > 0
+
+
+def _periodic(scheme, precision, p):
+    from paper_1802_04516_gb300.binding import Solver
+    xyz, ev, per = synth.tri_grid(6, 6, 1.0, 1.0, periodic=True, jitter=0.2, seed=21)
+    pg = 0 if scheme == "cn" else p
+    s = Solver(2, p, pg, scheme, precision, rel_tol=1e-12 if precision == "fp64" else 1e-9, max_iters=5000,
+               gmres_restart=30, preconditioner=1)
+    s.set_mesh(xyz, ev, per)
+    s.set_material(*synth.homogeneous(ev.shape[0], 2.0, 1.0, 1.0))
+    s.set_shots(1)
+    s.set_plane_wave(0, [1.0, 0.0], amp=0.01)
+    return s
+
+
+@pytest.mark.parametrize("scheme,precision,tol", [("stdg", "fp64", 1e-12), ("stdg", "mixed", 1e-8),
+                                                  ("cn", "fp64", 1e-10)])
+def test_energy_sentinel_is_silent_on_source_free_steps(scheme, precision, tol):
+    need_gpu()
+    s = _periodic(scheme, precision, 2)
+    s.set_energy_check(True, tol)
+    e0 = s.energy()[0]
+    for _ in range(3):
+        st = s.step(0.02, 2)
+        assert st["status"] == 0
+    e1 = s.energy()[0]
+    assert 0 < e1 <= (1 + tol) * e0
+
+
+def test_energy_sentinel_trips_on_a_demanded_decrease_and_advances_the_state():
+    from paper_1802_04516_gb300.binding import STDG_EENERGY, StdgError
+    need_gpu()
+    s = _periodic("stdg", "fp64", 2)
+    e0 = s.energy()[0]
+    s.set_energy_check(True, -0.5)   # demands that each call halve the energy: no step does
+    with pytest.raises(StdgError) as ei:
+        s.step(0.02, 1)
+    assert ei.value.code == STDG_EENERGY and "grew" in str(ei.value)
+    assert abs(s.time - 0.02) < 1e-15        # the step ran and the state advanced
+    e1 = s.energy()[0]
+    assert 0.5 * e0 < e1 <= e0 * (1 + 1e-12)
+    s.set_energy_check(False)
+    assert s.step(0.02, 1)["status"] == 0
+    with pytest.raises(StdgError):
+        s.set_energy_check(True, -1.0)       # rel_tol must be > -1
+
+
+def test_energy_sentinel_is_skipped_when_sources_drive_the_solution():
+    need_gpu()
+    w = _small()
+    s = gpu_solver(w, precision="fp64", rel_tol=1e-12, max_iters=5000)
+    s.set_energy_check(True, -0.5)           # would trip on any source-free step
+    assert s.step(w.dt, 2)["status"] == 0
