@@ -113,6 +113,22 @@ int stdg_set_mesh(stdg_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_el
  * STDG_EINVAL); STDG_ESTATE before stdg_set_mesh.  Also sets up the preconditioner. */
 int stdg_set_material(stdg_ctx* ctx, const double* lambda, const double* mu, const double* rho);
 
+/* Per-element time scale alpha (n_elem values, > 0, finite), for disconnected parts of one
+ * mesh that advance with their own time steps (a ragged batch, each part at its own CFL):
+ * a stdg_step(dt) advances element i by alpha_i dt in its own time.  alpha must be the same
+ * on the two elements of every face (STDG_EINVAL otherwise: a step that changes across a
+ * face is local time stepping, not this scheme).  Implemented without a kernel change: with
+ * tau = t / alpha the elastic system of a part is the same system with density rho / alpha
+ * and Lame parameters alpha lambda, alpha mu (Eq. 5 rescaled; the slab system of Eq.
+ * velocity.sys then scales by 1/alpha on both sides, the stress update of Eq. NM26 is
+ * unchanged), and a point source in such a part has the Ricker wavelet of Sec. 6.3 at
+ * frequency alpha f0 and delay t_delay / alpha.  States, receivers and stdg_energy stay in
+ * physical units; the time of stdg_get_time is the reference time (alpha = 1).  NULL resets
+ * to 1 everywhere.  Applies to the material and sources already set and to later ones;
+ * STDG_ESTATE before stdg_set_mesh.  stdg_misfit_grad rejects a context with a time scale
+ * other than 1 (STDG_ESTATE). */
+int stdg_set_time_scale(stdg_ctx* ctx, const double* alpha);
+
 /* Number of shots (right-hand sides).  Resets states to zero.  Default 1. */
 int stdg_set_shots(stdg_ctx* ctx, int n_shots);
 

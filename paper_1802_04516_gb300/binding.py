@@ -65,6 +65,7 @@ SIGNATURES = {
     "stdg_set_time": (C.c_int, [_P, C.c_double]),
     "stdg_energy": (C.c_int, [_P, _D]),
     "stdg_set_energy_check": (C.c_int, [_P, C.c_int, C.c_double]),
+    "stdg_set_time_scale": (C.c_int, [_P, _D]),
     "stdg_read_receivers": (C.c_int, [_P, _D, C.c_int64]),
     "stdg_apply_operator": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_apply_operator_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
@@ -307,6 +308,15 @@ class Solver:
         self.last_rc = rc
         self._chk(rc, allow=tuple(allow) + ((STDG_ENOTCONV,) if allow_notconv else ()))
         return self.last_stats
+
+    def set_time_scale(self, alpha=None):
+        """Per-element time scale: step(dt) advances element i by alpha[i] dt (one value per
+        disconnected part; None resets to 1)."""
+        if alpha is None:
+            self._chk(self.lib.stdg_set_time_scale(self.h, None))
+            return
+        a = _need(_f64(alpha), self.n_elem, "alpha")
+        self._chk(self.lib.stdg_set_time_scale(self.h, _d(a)))
 
     def set_energy_check(self, enable=True, rel_tol=0.0):
         """Energy-growth sentinel around step (Theorem 4): STDG_EENERGY when a shot's energy

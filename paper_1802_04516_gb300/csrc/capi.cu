@@ -382,6 +382,9 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     c->d_D = c->d_L = c->d_Mdual = nullptr;
     c->d_D32 = c->d_Dt32 = nullptr;
     c->d_lamf = c->d_muf = c->d_rhoJ = nullptr;
+    c->d_lamf_ph = c->d_muf_ph = c->d_rhoJ_ph = nullptr;
+    c->alpha_e.clear();
+    c->src_alpha.clear();
     c->d_lamf32 = c->d_muf32 = c->d_rhoJ32 = nullptr;
     c->d_vtr = c->d_sigtr = c->d_b = c->d_x = c->d_energy = c->d_sigtmp = nullptr;
     c->d_src = nullptr;
@@ -471,6 +474,8 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     return STDG_OK;
 }
 
+static int upload_material(stdg_ctx* c);
+
 int stdg_set_material(stdg_ctx* c, const double* lambda, const double* mu, const double* rho) {
     CHECK_CTX(c);
     NEED_MESH(c);
@@ -483,16 +488,47 @@ int stdg_set_material(stdg_ctx* c, const double* lambda, const double* mu, const
     c->lam_e.assign(lambda, lambda + ne);
     c->mu_e.assign(mu, mu + ne);
     c->rho_e.assign(rho, rho + ne);
-    // E_j: sub-cell-measure-weighted mean over the dual cell (|T_{i,j}| = |T_i| / (d+1))
+    (void)nf;
+    return upload_material(c);
+}
+
+// Device material from the host copies: E_j as the sub-cell-measure-weighted mean over the
+// dual cell (|T_{i,j}| = |T_i| / (d+1)), rho_i |J_i| per element; with a time scale alpha
+// the device holds alpha lambda, alpha mu, rho / alpha (physical copies kept for the energy).
+// Sets up the preconditioner.
+static int upload_material(stdg_ctx* c) {
+    const int64_t ne = c->n_elem, nf = c->n_face;
+    const bool ts = !c->alpha_e.empty();
     int rc;
     std::vector<double> lf(nf), mf(nf), rj(ne);
     for (int64_t f = 0; f < nf; ++f) {
         const int64_t l = c->hm.face_l[f], r = c->hm.face_r[f];
         double wl = c->hm.detJ[l], wr = r >= 0 ? c->hm.detJ[r] : 0.0;
-        lf[f] = (wl * lambda[l] + (r >= 0 ? wr * lambda[r] : 0.0)) / (wl + wr);
-        mf[f] = (wl * mu[l] + (r >= 0 ? wr * mu[r] : 0.0)) / (wl + wr);
+        lf[f] = (wl * c->lam_e[l] + (r >= 0 ? wr * c->lam_e[r] : 0.0)) / (wl + wr);
+        mf[f] = (wl * c->mu_e[l] + (r >= 0 ? wr * c->mu_e[r] : 0.0)) / (wl + wr);
     }
-    for (int64_t i = 0; i < ne; ++i) rj[i] = rho[i] * c->hm.detJ[i];
+    for (int64_t i = 0; i < ne; ++i) rj[i] = c->rho_e[i] * c->hm.detJ[i];
+    if (ts) {
+        if (!c->d_lamf_ph) {
+            if ((rc = dev_alloc(c, (void**)&c->d_lamf_ph, sizeof(double) * nf)) != STDG_OK) return rc;
+            if ((rc = dev_alloc(c, (void**)&c->d_muf_ph, sizeof(double) * nf)) != STDG_OK) return rc;
+            if ((rc = dev_alloc(c, (void**)&c->d_rhoJ_ph, sizeof(double) * ne)) != STDG_OK) return rc;
+        }
+        STDG_CUDA(c, cudaMemcpy(c->d_lamf_ph, lf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+        STDG_CUDA(c, cudaMemcpy(c->d_muf_ph, mf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+        STDG_CUDA(c, cudaMemcpy(c->d_rhoJ_ph, rj.data(), sizeof(double) * ne, cudaMemcpyHostToDevice));
+        for (int64_t f = 0; f < nf; ++f) {   // both elements of a face have the same scale
+            const double a = c->alpha_e[c->hm.face_l[f]];
+            lf[f] *= a;
+            mf[f] *= a;
+        }
+        for (int64_t i = 0; i < ne; ++i) rj[i] /= c->alpha_e[i];
+    } else if (c->d_lamf_ph) {
+        dev_free(c, c->d_lamf_ph);
+        dev_free(c, c->d_muf_ph);
+        dev_free(c, c->d_rhoJ_ph);
+        c->d_lamf_ph = c->d_muf_ph = c->d_rhoJ_ph = nullptr;
+    }
     STDG_CUDA(c, cudaMemcpy(c->d_lamf, lf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
     STDG_CUDA(c, cudaMemcpy(c->d_muf, mf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
     STDG_CUDA(c, cudaMemcpy(c->d_rhoJ, rj.data(), sizeof(double) * ne, cudaMemcpyHostToDevice));
@@ -500,6 +536,41 @@ int stdg_set_material(stdg_ctx* c, const double* lambda, const double* mu, const
     rc = upload_material32(c);
     if (rc != STDG_OK) return rc;
     if (c->opt.preconditioner) return setup_pre1(c);
+    return STDG_OK;
+}
+
+// time scale of each point source: that of its element
+static void set_source_alpha(stdg_ctx* c) {
+    c->src_alpha.clear();
+    if (c->alpha_e.empty()) return;
+    c->src_alpha.resize(c->src_elem.size());
+    for (size_t q = 0; q < c->src_elem.size(); ++q) c->src_alpha[q] = c->alpha_e[c->src_elem[q]];
+}
+
+int stdg_set_time_scale(stdg_ctx* c, const double* alpha) {
+    CHECK_CTX(c);
+    NEED_MESH(c);
+    const int64_t ne = c->n_elem;
+    if (!alpha) {
+        c->alpha_e.clear();
+    } else {
+        bool ones = true;
+        for (int64_t i = 0; i < ne; ++i) {
+            if (!std::isfinite(alpha[i]) || !(alpha[i] > 0)) STDG_FAIL(c, STDG_EINVAL, "time scale must be finite and > 0");
+            ones = ones && alpha[i] == 1.0;
+        }
+        for (int64_t f = 0; f < c->n_face; ++f) {
+            const int64_t r = c->hm.face_r[f];
+            if (r >= 0 && alpha[c->hm.face_l[f]] != alpha[r])
+                STDG_FAIL(c, STDG_EINVAL, "time scale differs across a face");
+        }
+        if (ones) c->alpha_e.clear();
+        else c->alpha_e.assign(alpha, alpha + ne);
+    }
+    int rc;
+    if (c->have_material && (rc = upload_material(c)) != STDG_OK) return rc;
+    if (c->have_sources) set_source_alpha(c);
+    solver_invalidate_graph(c);   // the source wavelets are launch arguments of captured graphs
     return STDG_OK;
 }
 
@@ -597,6 +668,7 @@ int stdg_set_point_sources(stdg_ctx* c, int n_shots, int per_shot, const double*
     c->src_td = t_delay;
     c->src_a1 = a1;
     c->have_sources = 1;
+    set_source_alpha(c);
     solver_invalidate_graph(c);
     return STDG_OK;
 }
@@ -703,6 +775,7 @@ int stdg_misfit_grad(stdg_ctx* c, double dt, int n_steps, const double* data, in
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 1 || !data || !loss)
         STDG_FAIL(c, STDG_EINVAL, "bad misfit arguments");
     if (c->opt.scheme != STDG_SCHEME_STDG) STDG_FAIL(c, STDG_EINVAL, "the adjoint covers the space-time DG scheme only");
+    if (!c->alpha_e.empty()) STDG_FAIL(c, STDG_ESTATE, "the adjoint needs a time scale of 1 everywhere");
     if (c->n_rec < 1) STDG_FAIL(c, STDG_ESTATE, "the misfit needs receivers (stdg_set_receivers)");
     if (!c->d_vtr) STDG_FAIL(c, STDG_ESTATE, "no state: set sources, shots or a state first");
     const int64_t nd = (int64_t)c->n_shots * n_steps * c->n_rec * c->dim;

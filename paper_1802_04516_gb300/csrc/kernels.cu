@@ -820,9 +820,11 @@ cudaError_t launch_rhs(stdg_ctx* c, double dt, const double* dparams, int shot, 
     }));
     for (int q = 0; c->have_sources && q < c->src_per_shot; ++q) {   // sequential: sources may share an element
         const int64_t sq = (int64_t)shot * c->src_per_shot + q;
+        // a source in a part with time scale alpha sees its wavelet in that part's scaled time
+        const double al = c->src_alpha.empty() ? 1.0 : c->src_alpha[sq];
         rhs_source_kernel<<<1, 128, 0, c->stream>>>(c->dim, NP, NG, c->d_rt, dparams, (int32_t)c->src_elem[sq],
-                                                     c->d_src + sq * (c->dim + NP), c->src_f0, c->src_td, c->src_a1,
-                                                     c->d_gl8, b); note_launch(c);
+                                                     c->d_src + sq * (c->dim + NP), c->src_f0 * al, c->src_td / al,
+                                                     c->src_a1, c->d_gl8, b); note_launch(c);
     }
     return cudaGetLastError();
 }
@@ -983,12 +985,16 @@ __global__ void energy_kernel(int64_t n_elem, int64_t n_face, int NP, const RefT
 
 cudaError_t launch_energy(stdg_ctx* c, int shot, double* d_out) {
     cudaMemsetAsync(d_out, 0, sizeof(double), c->stream);
+    // physical material when a time scale is set (the operator's copies are scaled)
+    const double* rhoJ = c->d_rhoJ_ph ? c->d_rhoJ_ph : c->d_rhoJ;
+    const double* lamf = c->d_lamf_ph ? c->d_lamf_ph : c->d_lamf;
+    const double* muf = c->d_muf_ph ? c->d_muf_ph : c->d_muf;
     if (c->dim == 2) {
-        energy_kernel<2><<<c->n_sm * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
-                                                         c->d_lamf, c->d_muf, c->d_sigtr + shot * c->nsig, d_out);
+        energy_kernel<2><<<c->n_sm * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, rhoJ, c->d_vtr + shot * c->ntr,
+                                                         lamf, muf, c->d_sigtr + shot * c->nsig, d_out);
     } else {
-        energy_kernel<3><<<c->n_sm * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, c->d_rhoJ, c->d_vtr + shot * c->ntr,
-                                                         c->d_lamf, c->d_muf, c->d_sigtr + shot * c->nsig, d_out);
+        energy_kernel<3><<<c->n_sm * 4, 256, 0, c->stream>>>(c->n_elem, c->n_face, c->Nphi, c->d_rt, rhoJ, c->d_vtr + shot * c->ntr,
+                                                         lamf, muf, c->d_sigtr + shot * c->nsig, d_out);
     }
     note_launch(c);
     return cudaGetLastError();

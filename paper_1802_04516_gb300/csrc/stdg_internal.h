@@ -115,7 +115,10 @@ struct stdg_ctx {
     double *d_Mdual = nullptr;  // dual mass matrices (set-up workspace)
     float *d_D32 = nullptr;     // FP32 copy of D~
     float *d_Dt32 = nullptr;    // FP32 D~ in tiles (2D p = 3 and 3D p = 2 only: the tiled face kernels)
-    double *d_lamf = nullptr, *d_muf = nullptr, *d_rhoJ = nullptr;    // per face / element
+    double *d_lamf = nullptr, *d_muf = nullptr, *d_rhoJ = nullptr;    // per face / element (time-scaled)
+    // physical copies for the energy when a time scale other than 1 is set (else null)
+    double *d_lamf_ph = nullptr, *d_muf_ph = nullptr, *d_rhoJ_ph = nullptr;
+    std::vector<double> alpha_e;       // per-element time scale; empty: 1 everywhere
     float *d_lamf32 = nullptr, *d_muf32 = nullptr, *d_rhoJ32 = nullptr;
 
     // ---- device: state (shot-major)
@@ -131,6 +134,7 @@ struct stdg_ctx {
     double *d_src = nullptr;           // [shot][source]: [dim dir][Nphi phi(x_s)]
     int32_t *d_src_elem = nullptr;
     double src_f0 = 0, src_td = 0, src_a1 = 0;
+    std::vector<double> src_alpha;     // time scale of each source's element (empty: 1)
     std::vector<double> src_xs, src_dir;   // host copies: [shot][source of the shot][dim]
     double* d_gl8 = nullptr;           // 8-point Gauss-Legendre rule on [0,1]: nodes, weights
     std::vector<double> lam_e, mu_e, rho_e;   // host copies of the material

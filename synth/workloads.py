@@ -176,7 +176,9 @@ def scaled(name, **kw):
 def ragged_union(ks=range(16), p=2, steps=200, scale=1.0, seed=1300, gap=0.5):
     """The ragged batch as one input: meshes c4_ragged(k) placed side by side (x-shifted by
     their width plus ``gap``) as one disconnected mesh, so that one context -- and one launch
-    per kernel -- advances all of them.  All parts share the smallest part's time step.
+    per kernel -- advances all of them.  ``dt`` is the smallest part's time step; extra
+    ``part_dt`` holds each part's own (10x CFL) step and ``alpha`` the per-element ratio
+    part_dt / dt, the time scale that lets every part advance at its own step.
     Returns (Workload, list of (first element, element count) per part)."""
     parts = [c4_ragged(k, p=p, steps=steps, seed=seed, scale=scale) for k in ks]
     xyz, ev, lam, mu, rho, xs, rec, spans = [], [], [], [], [], [], [], []
@@ -193,11 +195,13 @@ def ragged_union(ks=range(16), p=2, steps=200, scale=1.0, seed=1300, gap=0.5):
         eoff += w.n_elem
         xoff += 2.0 + gap
     dt = min(w.dt for w in parts)
+    alpha = np.concatenate([np.full(w.n_elem, w.dt / dt) for w in parts])
     u = Workload("c4_ragged_union%d_p%d_%dtri" % (len(parts), p, eoff), 2, np.concatenate(xyz),
                  np.concatenate(ev).astype(np.int32), None, np.concatenate(lam), np.concatenate(mu),
                  np.concatenate(rho), p=p, p_gamma=p, scheme="stdg", dt=dt, n_steps=steps, h=parts[0].h,
                  shots_xs=None, shots_dir=None, receivers=np.concatenate(rec),
-                 extra={"part_sources": np.array(xs), "spans": spans})
+                 extra={"part_sources": np.array(xs), "spans": spans, "part_dt": [w.dt for w in parts],
+                        "alpha": alpha})
     return u, spans
 
 

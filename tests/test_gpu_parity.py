@@ -291,6 +291,44 @@ def test_ragged_union_matches_oracle_per_part(precision, tol, rel_tol):
     assert f0 == sig.shape[0]
 
 
+@pytest.mark.parametrize("precision,tol,rel_tol,pre", [("fp64", 1e-10, 1e-13, 1), ("mixed", 1e-8, 1e-12, 2)])
+def test_ragged_union_with_per_part_time_steps_matches_oracle(precision, tol, rel_tol, pre):
+    # the ragged batch with every part at its own 10x-CFL step: one context, one stacked solve
+    # per slab, a per-element time scale (part_dt / smallest dt); each part against its own
+    # oracle run at its own step (the oracle knows nothing of time scales)
+    need_gpu()
+    from paper_1802_04516_gb300.binding import StdgError
+    w, spans = synth.ragged_union(ks=[0, 5, 10], steps=3, scale=0.02)
+    part_dt = w.extra["part_dt"]
+    assert max(part_dt) > 1.2 * min(part_dt)     # the parts' own steps really differ
+    s = gpu_solver(w, precision=precision, rel_tol=rel_tol, max_iters=20000, preconditioner=pre)
+    bad = np.array(w.extra["alpha"])
+    bad[spans[1][0]] *= 1.5                       # one element off its part's scale
+    with pytest.raises(StdgError):
+        s.set_time_scale(bad)
+    s.set_time_scale(w.extra["alpha"])
+    st = s.step(w.dt, 3)
+    assert st["status"] == 0
+    v, sig = s.get_state(0)
+    energy = s.energy()[0]
+    parts = [synth.c4_ragged(k, steps=3, seed=1300, scale=0.02) for k in [0, 5, 10]]
+    f0, e_parts = 0, 0.0
+    for (e0, ne), part, dtp in zip(spans, parts, part_dt):
+        assert part.n_elem == ne and part.dt == dtp
+        sim = oracle_sim(part, dt=dtp)            # the part alone at its own step
+        sim.set_source(part.shots_xs[0], [0.0, 1.0], w.f0, w.t_delay, w.a1)
+        sim.step(3)
+        nf = sim.sig_tr.shape[0]
+        err_v = rel_l2(v[e0:e0 + ne], sim.v_tr)
+        err_s = stress_field_rel(sig[f0:f0 + nf], sim.sig_tr, sim.disc)
+        print(precision, "part of %d triangles, dt %.4g: velocity %.3g stress %.3g" % (ne, dtp, err_v, err_s))
+        assert err_v < tol and err_s < tol
+        e_parts += sim.energy()
+        f0 += nf
+    assert f0 == sig.shape[0]
+    assert abs(energy - e_parts) <= 10 * tol * e_parts   # stdg_energy stays physical
+
+
 PRE2_CASES = [OP_CASES[i] for i in (0, 2, 3, 4)]
 
 
