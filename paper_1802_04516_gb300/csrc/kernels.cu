@@ -418,41 +418,60 @@ cudaError_t launch_to_fp32(stdg_ctx* c) {
 // Operator: element mass term and face (Schur) term.
 // ---------------------------------------------------------------------------------
 // y[e][k][a][n] = rho_i |J_i| sum_b T[a][b] sum_n' Mref[n][n'] v[e][k][b][n']
-// n_elem = elements x shots of the (shot-major) vectors, n_elem_base = elements of the mesh
+// n_elem = elements x shots of the (shot-major) vectors, n_elem_base = elements of the mesh.
+// A block takes EB = blockDim / (d N_gamma) consecutive elements at a time: their values are
+// loaded into shared memory with consecutive (coalesced) reads, each thread forms one row
+// (k, a) of one element, the rows go back to the same shared buffer and out with consecutive
+// writes.
 template <int NP, typename R>
-__global__ void mass_kernel(int64_t n_elem, int64_t n_elem_base, int dim, int NG, const RefTables* __restrict__ rtp,
-                            const R* __restrict__ rhoJ, const R* __restrict__ v, const int* __restrict__ vidx,
-                            int64_t ld, R* __restrict__ y) {
+__global__ void __launch_bounds__(128) mass_kernel(int64_t n_elem, int64_t n_elem_base, int dim, int NG,
+                                                   const RefTables* __restrict__ rtp, const R* __restrict__ rhoJ,
+                                                   const R* __restrict__ v, const int* __restrict__ vidx, int64_t ld,
+                                                   R* __restrict__ y) {
     if (vidx) v += (int64_t)(*vidx) * ld;
+    extern __shared__ __align__(16) unsigned char mass_smem[];
+    R* sV = reinterpret_cast<R*>(mass_smem);
     __shared__ R sM[NP * NP];
     __shared__ R sT[kMaxNG * kMaxNG];
     for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) sM[t] = (R)rtp->Mref[t];
     for (int t = threadIdx.x; t < NG * NG; t += blockDim.x) sT[t] = (R)rtp->T[t];
-    __syncthreads();
-    const int per_e = dim * NG;          // rows of NP values per element
-    const int64_t nrow = n_elem * per_e;
-    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < nrow; row += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = row / per_e;
-        const int ka = (int)(row % per_e);
-        const int k = ka / NG, a = ka % NG;
-        const R* ve = v + (e * dim + k) * NG * NP;
-        R tv[NP];
+    const int rows_e = dim * NG, per_e = rows_e * NP;
+    const int EB = blockDim.x / rows_e;
+    const int r = threadIdx.x, le = r / rows_e, ka = r % rows_e, k = ka / NG, a = ka % NG;
+    for (int64_t e0 = blockIdx.x * (int64_t)EB; e0 < n_elem; e0 += (int64_t)gridDim.x * EB) {
+        const int ne = (int)min((int64_t)EB, n_elem - e0);
+        const int64_t base = e0 * per_e;
+        __syncthreads();   // the previous elements' values have been written out
+        for (int t = threadIdx.x; t < ne * per_e; t += blockDim.x) sV[t] = v[base + t];
+        __syncthreads();
+        const bool act = le < ne;
+        R out[NP];
+        if (act) {
+            const R* ve = sV + (le * dim + k) * NG * NP;
+            R tv[NP];
 #pragma unroll
-        for (int n = 0; n < NP; ++n) tv[n] = 0;
-        for (int b = 0; b < NG; ++b) {
-            const R tab = sT[a * NG + b];
+            for (int n = 0; n < NP; ++n) tv[n] = 0;
+            for (int b = 0; b < NG; ++b) {
+                const R tab = sT[a * NG + b];
 #pragma unroll
-            for (int n = 0; n < NP; ++n) tv[n] += tab * ve[b * NP + n];
+                for (int n = 0; n < NP; ++n) tv[n] += tab * ve[b * NP + n];
+            }
+            const R sc = rhoJ[(e0 + le) % n_elem_base];
+#pragma unroll
+            for (int n = 0; n < NP; ++n) {
+                R acc = 0;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) acc += sM[n * NP + q] * tv[q];
+                out[n] = sc * acc;
+            }
         }
-        const R s = rhoJ[e % n_elem_base];
-        R* ye = y + row * NP;
+        __syncthreads();   // every row has read the element's values
+        if (act) {
 #pragma unroll
-        for (int n = 0; n < NP; ++n) {
-            R acc = 0;
-#pragma unroll
-            for (int q = 0; q < NP; ++q) acc += sM[n * NP + q] * tv[q];
-            ye[n] = s * acc;
+            for (int n = 0; n < NP; ++n) sV[r * NP + n] = out[n];   // row (e, k, a) of y
         }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * per_e; t += blockDim.x) y[base + t] = sV[t];
     }
 }
 
@@ -617,8 +636,12 @@ static cudaError_t apply_tmpl(stdg_ctx* c, const R* D, const R* lamf, const R* m
     const int NG = c->Ng;
     if (mass) {
         const int64_t rows = c->n_elem * nshots * c->dim * NG;
-        mass_kernel<NP, R><<<(unsigned)std::min<int64_t>((rows + 127) / 128, c->n_sm * 64), 128, 0, c->stream>>>(
-            c->n_elem * nshots, c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
+        const int EB = 128 / (c->dim * NG);   // elements per block and pass (d N_gamma <= 15)
+        const int64_t ne = c->n_elem * nshots;
+        const size_t smem = sizeof(R) * (size_t)EB * c->dim * NG * NP;
+        (void)rows;
+        mass_kernel<NP, R><<<(unsigned)std::min<int64_t>((ne + EB - 1) / EB, (int64_t)c->n_sm * 16), 128, smem, c->stream>>>(
+            ne, c->n_elem, c->dim, NG, c->d_rt, rhoJ, x, xidx, ld, y); note_launch(c);
     }
     if (!face) return cudaGetLastError();
     cudaError_t fe;
