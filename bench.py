@@ -406,19 +406,24 @@ def adjoint_section(torch, args, stream, dist, world):
 
 
 def pre2_local_roofline(s, w, pk):
-    """Element-local step of the stencil preconditioner, z = S^{-1} (2 r - w) in FP32: one
-    dense (d N_phi N_gamma)^2 FP32 block per element (padded to 16 bytes) streamed from HBM,
-    plus r, w read and z written."""
+    """Element-local step of the stencil preconditioner, z = S^{-1} (2 r - w) in FP32 arithmetic:
+    one dense (d N_phi N_gamma)^2 block per element streamed from HBM -- FP16 balanced (H plus
+    2N FP32 scales) by default, or FP32 padded to 16 bytes -- plus r, w read and z written."""
     from math import comb
     nphi = comb(w.p + w.dim, w.dim)
     N = w.dim * nphi * (w.p_gamma + 1)
     nvel = w.n_elem * N
-    bytes_alg = w.n_elem * ((N * N + 3) // 4 * 4) * 4 + 3 * nvel * 4
+    bits = s.pre2_bits
+    if bits == 16:
+        block, name, tkey = N * N * 2 + 2 * N * 4, "pre2_local_half_kernel", "pre2_local_fp16"
+    else:
+        block, name, tkey = ((N * N + 3) // 4 * 4) * 4, "pre2_local_kernel<float,float,1>", "pre2_local_fp32"
+    bytes_alg = w.n_elem * block + 3 * nvel * 4
     ms = s.time_kernel(w.dt, 2, fp32=True, n=20)
     peak = float(pk.get("hbm_gbs", 6800.0))
     achieved = bytes_alg / (ms * 1e-3) / 1e9
-    return {"kernel": "pre2_local_kernel<float,float,1>", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(w, "pre2_local_fp32", w.n_elem),
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": _traffic(w, tkey, w.n_elem),
             "alg_bytes_per_launch": int(bytes_alg), "alg_flops_per_launch": int(2 * w.n_elem * N * N),
             "ms_per_launch": round(ms, 4), "peak_source": "measured hbm_gbs" if "hbm_gbs" in pk else "fallback"}
 

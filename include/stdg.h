@@ -77,7 +77,8 @@ typedef struct {
                            GMRES instead of CG.  Needs d N_phi N_gamma <= 128 (else STDG_EINVAL at
                            stdg_set_material); costs (d N_phi N_gamma)^2 values per element, FP64
                            in FP64 contexts and FP32 in mixed-precision ones (which keep no FP64
-                           copy: the FP64 stencil apply calls are then STDG_ESTATE).            */
+                           copy: the FP64 stencil apply calls are then STDG_ESTATE) plus a
+                           balanced FP16 copy for one shot (stdg_set_pre2_storage).             */
 } stdg_options;
 
 typedef struct {
@@ -209,8 +210,20 @@ int stdg_apply_operator_device(stdg_ctx* ctx, double dt, const void* x_dev, void
 /* Sizes: what = 0 n_elem, 1 n_face, 2 N_phi, 3 N_psi, 4 N_gamma, 5 stress comps s,
  * 6 n_shots, 7 velocity values per shot and slab, 8 n_rec, 9 n_boundary_faces,
  * 10 device bytes held, 11 kernel executions of the library during the last stdg_step
- * call (counted on the device, including every iteration of the device-side loops). */
+ * call (counted on the device, including every iteration of the device-side loops),
+ * 12 bits per stored entry of the stencil preconditioner's local blocks in the FP32 inner
+ * solve of one shot (16 or 32; 0 without such blocks). */
 int stdg_query(stdg_ctx* ctx, int what, int64_t* out);
+
+/* Storage of the stencil preconditioner's local blocks S_e^{-1} (Appendix A, Eq. APPRE2)
+ * applied by the FP32 inner solve of a single shot: bits = 16 (default for mixed precision)
+ * keeps each block balanced, S^{-1} = diag(r) H diag(c) with r_i = max_j |S_ij|,
+ * c_j = max_i |S_ij| / r_i, and H in FP16 (11-bit significand, as the TF32 rounding of the
+ * multi-shot tensor-core path), FP32 arithmetic: half the bytes of the slab's dominant
+ * stream; bits = 32 applies the FP32 blocks.  The preconditioner only steers the Krylov
+ * iteration, so the solution meets the same residual bar either way.  Shapes with an odd
+ * d N_phi N_gamma or above 128 keep FP32.  Returns STDG_OK or STDG_EINVAL (bits not 16/32). */
+int stdg_set_pre2_storage(stdg_ctx* ctx, int bits);
 
 /* Face table as built by stdg_set_mesh: l(j), r(j) (-1 on the boundary). */
 int stdg_get_faces(stdg_ctx* ctx, int32_t* face_l, int32_t* face_r);

@@ -66,6 +66,7 @@ SIGNATURES = {
     "stdg_energy": (C.c_int, [_P, _D]),
     "stdg_set_energy_check": (C.c_int, [_P, C.c_int, C.c_double]),
     "stdg_set_time_scale": (C.c_int, [_P, _D]),
+    "stdg_set_pre2_storage": (C.c_int, [_P, C.c_int]),
     "stdg_read_receivers": (C.c_int, [_P, _D, C.c_int64]),
     "stdg_apply_operator": (C.c_int, [_P, C.c_double, _D, _D]),
     "stdg_apply_operator_device": (C.c_int, [_P, C.c_double, _P, _P, C.c_int]),
@@ -317,6 +318,13 @@ class Solver:
             return
         a = _need(_f64(alpha), self.n_elem, "alpha")
         self._chk(self.lib.stdg_set_time_scale(self.h, _d(a)))
+
+    def set_pre2_storage(self, bits):
+        """Stencil-preconditioner blocks of the single-shot FP32 inner solve: 16 (balanced FP16,
+        default) or 32 bits."""
+        self._chk(self.lib.stdg_set_pre2_storage(self.h, int(bits)))
+
+    pre2_bits = property(lambda s: s.query(12))
 
     def set_energy_check(self, enable=True, rel_tol=0.0):
         """Energy-growth sentinel around step (Theorem 4): STDG_EENERGY when a shot's energy

@@ -214,6 +214,11 @@ static int setup_pre1(stdg_ctx* c) {
             // tensor-core image of the FP32 blocks for batches of shots
             if (c->opt.precision != STDG_FP64 && pre2_mma_supported(c) &&
                 (rc = dev_alloc(c, (void**)&c->d_pre2_mma, sizeof(float) * pre2_mma_image_floats(c))) != STDG_OK) return rc;
+            // FP16 balanced copy for one shot (the dominant stream at half the bytes)
+            if (c->opt.precision != STDG_FP64 && pre2_half_supported(c)) {
+                if ((rc = dev_alloc(c, &c->d_pre2_16, 2 * (size_t)ne * N * N)) != STDG_OK) return rc;
+                if ((rc = dev_alloc(c, (void**)&c->d_pre2_scl, sizeof(float) * 2 * (size_t)ne * N)) != STDG_OK) return rc;
+            }
             if ((rc = dev_alloc(c, (void**)&c->d_p2status, sizeof(int))) != STDG_OK) return rc;
         }
     }
@@ -231,6 +236,7 @@ int precond_for_dt(stdg_ctx* c, double dt) {
         STDG_CUDA(c, cudaMemsetAsync(c->d_p2status, 0, sizeof(int), c->stream));
         STDG_CUDA(c, launch_pre2_setup(c, dt, c->d_p2status));
         if (c->d_pre2_mma) STDG_CUDA(c, launch_pre2_mma_image(c));
+        if (c->d_pre2_16) STDG_CUDA(c, launch_pre2_half(c));
         int status = 0;
         STDG_CUDA(c, cudaMemcpyAsync(&status, c->d_p2status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         STDG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -372,6 +378,8 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     c->d_pre2 = nullptr;
     c->d_pre2_32 = nullptr;
     c->d_pre2_mma = nullptr;
+    c->d_pre2_16 = nullptr;
+    c->d_pre2_scl = nullptr;
     c->d_p2y = c->d_p2t = nullptr;
     c->d_p2status = nullptr;
     c->pre_dt = -1.0;
@@ -876,8 +884,17 @@ int stdg_query(stdg_ctx* c, int what, int64_t* out) {
         case 9: *out = c->hm.n_bnd; break;
         case 10: *out = (int64_t)c->bytes; break;
         case 11: *out = c->last_launches; break;
+        case 12: *out = c->d_pre2_32 ? (c->d_pre2_16 && c->pre2_bits == 16 ? 16 : 32) : 0; break;
         default: STDG_FAIL(c, STDG_EINVAL, "unknown query");
     }
+    return STDG_OK;
+}
+
+int stdg_set_pre2_storage(stdg_ctx* c, int bits) {
+    CHECK_CTX(c);
+    if (bits != 16 && bits != 32) STDG_FAIL(c, STDG_EINVAL, "bits must be 16 or 32");
+    c->pre2_bits = bits;
+    solver_invalidate_graph(c);   // graphs keep the kernel they were captured with
     return STDG_OK;
 }
 

@@ -27,6 +27,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 
 #include "stdg_internal.h"
 
@@ -250,6 +252,118 @@ __global__ void __launch_bounds__(128) pre2_local_kernel(int64_t n_elem, int N, 
     }
 }
 
+// FP16 storage of the FP32 path's blocks.  Each block is balanced, S^{-1} = diag(r) H diag(c)
+// with r_i = max_j |S_ij| and c_j = max_i |S_ij| / r_i, so that every row and column of H
+// has its largest entry at magnitude 1 and H is stored in FP16 (11-bit significand, as the
+// TF32 rounding of the tensor-core batch path).  One warp per element; lane holds rows
+// lane + 32 i of the column-major FP32 block.
+__global__ void __launch_bounds__(128) pre2_half_kernel(int64_t n_elem, int N, int64_t es, const float* __restrict__ S32,
+                                                        __half* __restrict__ H, float* __restrict__ scl) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
+        const float* Se = S32 + e * es;
+        __half* He = H + e * (int64_t)N * N;
+        float* se = scl + e * 2 * (int64_t)N;
+        float rmax[kP2MaxRows];
+#pragma unroll
+        for (int i = 0; i < kP2MaxRows; ++i) rmax[i] = 0.f;
+        for (int c = 0; c < N; ++c)
+#pragma unroll
+            for (int i = 0; i < kP2MaxRows; ++i) {
+                const int rr = lane + 32 * i;
+                if (rr < N) rmax[i] = fmaxf(rmax[i], fabsf(Se[(int64_t)c * N + rr]));
+            }
+        float rinv[kP2MaxRows];
+#pragma unroll
+        for (int i = 0; i < kP2MaxRows; ++i) {
+            const int rr = lane + 32 * i;
+            const float rs = rmax[i] > 0.f ? rmax[i] : 1.f;
+            rinv[i] = 1.f / rs;
+            if (rr < N) se[rr] = rs;
+        }
+        for (int c = 0; c < N; ++c) {
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < kP2MaxRows; ++i) {
+                const int rr = lane + 32 * i;
+                if (rr < N) m = fmaxf(m, fabsf(Se[(int64_t)c * N + rr]) * rinv[i]);
+            }
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const float cs = m > 0.f ? m : 1.f;
+            if (lane == 0) se[N + c] = cs;
+            const float cinv = 1.f / cs;
+#pragma unroll
+            for (int i = 0; i < kP2MaxRows; ++i) {
+                const int rr = lane + 32 * i;
+                if (rr < N) He[(int64_t)c * N + rr] = __float2half_rn(Se[(int64_t)c * N + rr] * rinv[i] * cinv);
+            }
+        }
+    }
+}
+
+bool pre2_half_supported(const stdg_ctx* c) {
+    const int N = c->dim * c->Nphi * c->Ng;
+    return N % 2 == 0 && N <= 64 * kP2MaxRows / 2 && N <= 32 * kP2MaxRows;
+}
+
+cudaError_t launch_pre2_half(stdg_ctx* c) {
+    const int N = c->dim * c->Nphi * c->Ng;
+    const int64_t blocks = std::min<int64_t>((c->n_elem + 3) / 4, (int64_t)c->n_sm * 16);
+    pre2_half_kernel<<<(unsigned)blocks, 128, 0, c->stream>>>(c->n_elem, N, pre2_stride32(c), c->d_pre2_32,
+                                                             reinterpret_cast<__half*>(c->d_pre2_16), c->d_pre2_scl);
+    note_launch(c);
+    return cudaGetLastError();
+}
+
+// z_e = diag(r) H diag(c) (2 r_e - w_e) with FP16 H, one shot: one warp per element, lane
+// holds row pairs 2(lane + 32 i), +1 (one 4-byte load of two FP16 values per column); the
+// column scales multiply the staged vector, the row scales the accumulated rows.
+__global__ void __launch_bounds__(128) pre2_local_half_kernel(int64_t n_elem, int N, const __half* __restrict__ H,
+                                                              const float* __restrict__ scl, const float* __restrict__ r,
+                                                              const int* __restrict__ ridx, int64_t ld,
+                                                              const float* __restrict__ w, float* __restrict__ z) {
+    constexpr int PAIRS = kP2MaxRows / 2;   // row pairs per lane: N <= 128
+    extern __shared__ unsigned char smraw[];
+    if (ridx) r += (int64_t)(*ridx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    float* st = reinterpret_cast<float*>(smraw) + (size_t)warp * N;
+    for (int64_t e = blockIdx.x * (int64_t)wpb + warp; e < n_elem; e += (int64_t)gridDim.x * wpb) {
+        const __half2* He = reinterpret_cast<const __half2*>(H + e * (int64_t)N * N);
+        const float* se = scl + e * 2 * (int64_t)N;
+        for (int q = lane; q < N; q += 32) {
+            const int64_t i = e * N + q;
+            st[q] = (2.f * r[i] - w[i]) * se[N + q];
+        }
+        __syncwarp();
+        float2 acc[PAIRS];
+#pragma unroll
+        for (int i = 0; i < PAIRS; ++i) acc[i] = make_float2(0.f, 0.f);
+        const int NH = N / 2;
+        for (int c = 0; c < N; ++c) {
+            const float x = st[c];
+            const __half2* col = He + (int64_t)c * NH;
+#pragma unroll
+            for (int i = 0; i < PAIRS; ++i) {
+                const int pr = lane + 32 * i;
+                if (pr < NH) {
+                    const float2 a = __half22float2(col[pr]);
+                    acc[i].x = fmaf(a.x, x, acc[i].x);
+                    acc[i].y = fmaf(a.y, x, acc[i].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PAIRS; ++i) {
+            const int pr = lane + 32 * i;
+            if (pr < NH) {
+                const float2 rs = *reinterpret_cast<const float2*>(se + 2 * pr);
+                *reinterpret_cast<float2*>(z + e * N + 2 * pr) = make_float2(acc[i].x * rs.x, acc[i].y * rs.y);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 static size_t pre2_setup_smem(int dim, int NP, int NG) {
     const int n = dim * NP, N = n * NG;
     return sizeof(double) * ((size_t)N * 2 * N + 2 * (size_t)n * n + (size_t)n * NG * NG + 2 * (size_t)dim * NP * NP + N);
@@ -283,6 +397,15 @@ static cudaError_t pre2_local_t(stdg_ctx* c, const S* Sinv, int64_t es, const R*
     }
     const int wpb = c->tune.pre2_wpb;
     const int64_t blocks = std::min<int64_t>((c->n_elem + wpb - 1) / wpb, 1 << 30);
+    if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+        // one shot with the FP16 copy of the blocks (half the bytes of the dominant stream)
+        if (nshots == 1 && c->d_pre2_16 && c->pre2_bits == 16 && Sinv == c->d_pre2_32) {
+            pre2_local_half_kernel<<<(unsigned)blocks, 32 * wpb, sizeof(float) * wpb * N, c->stream>>>(
+                c->n_elem, N, reinterpret_cast<const __half*>(c->d_pre2_16), c->d_pre2_scl, r, ridx, ld, w, z);
+            note_launch(c);
+            return cudaGetLastError();
+        }
+    }
     if (nshots == 1) {
         pre2_local_kernel<R, S, 1><<<(unsigned)blocks, 32 * wpb, sizeof(R) * wpb * N, c->stream>>>(
             c->n_elem, N, es, Sinv, r, ridx, ld, w, z, nshots, c->nvel);

@@ -153,6 +153,9 @@ struct stdg_ctx {
     double* d_pre2 = nullptr;
     float* d_pre2_32 = nullptr;                // FP32 copy for the FP32 solver, pre2_stride32 apart
     float* d_pre2_mma = nullptr;               // TF32-rounded tensor-core operand image (multi-shot, pre2_mma.cu)
+    void* d_pre2_16 = nullptr;                 // FP16 balanced blocks H (S^-1 = diag(r) H diag(c)), single shot
+    float* d_pre2_scl = nullptr;               // per element: row scales r then column scales c
+    int pre2_bits = 16;                        // storage of the FP32 path's local blocks: 16 or 32
     void *d_p2y = nullptr, *d_p2t = nullptr;   // P_1 r and A P_1 r, stacked over shots (FP64-sized)
     int* d_p2status = nullptr;
 
@@ -244,6 +247,8 @@ inline int64_t pre2_stride32(const stdg_ctx* c) {
     return (N * N + 3) / 4 * 4;
 }
 cudaError_t launch_pre2_setup(stdg_ctx* c, double dt, int* d_status);
+bool pre2_half_supported(const stdg_ctx* c);
+cudaError_t launch_pre2_half(stdg_ctx* c);
 cudaError_t launch_pre2_apply(stdg_ctx* c, const double* r, double* z, const int* ridx, int64_t ld, int nshots = 1);
 cudaError_t launch_pre2_apply32(stdg_ctx* c, const float* r, float* z, const int* ridx, int64_t ld, int nshots = 1);
 cudaError_t launch_pre2_local(stdg_ctx* c, int fp32, const void* r, const void* w, void* z);

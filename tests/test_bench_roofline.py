@@ -16,8 +16,8 @@ N_ELEM, N_FACE = 200704, 301728
 
 
 class _Timed:
-    def __init__(self, ms_op, ms_kernel):
-        self.ms_op, self.ms_kernel = ms_op, ms_kernel
+    def __init__(self, ms_op, ms_kernel, pre2_bits=32):
+        self.ms_op, self.ms_kernel, self.pre2_bits = ms_op, ms_kernel, pre2_bits
 
     def time_operator(self, dt, fp32, n):
         return self.ms_op
@@ -56,6 +56,15 @@ def test_pre2_local_bytes_and_fraction():
     assert r["traffic"] == int((429949184 + 2444032) / 16384 * N_ELEM)
     # the ncu per-unit figures belong to the p = 3 shape only
     assert bench.pre2_local_roofline(_Timed(None, 0.8), _w(2, 2), {"hbm_gbs": 7000.0})["traffic"] is None
+
+
+def test_pre2_local_bytes_with_fp16_blocks():
+    # balanced FP16 storage: N^2 FP16 entries and 2N FP32 scales per element, same vectors
+    N = 80
+    alg = N_ELEM * (N * N * 2 + 2 * N * 4) + 3 * 4 * N_ELEM * N
+    r = bench.pre2_local_roofline(_Timed(None, 0.45, pre2_bits=16), _w(), {"hbm_gbs": 7000.0})
+    assert r["alg_bytes_per_launch"] == alg and r["kernel"] == "pre2_local_half_kernel"
+    assert abs(r["achieved"] - alg / 0.45e-3 / 1e9) < 0.1
 
 
 def test_dominant_kernel_by_time_per_iteration():

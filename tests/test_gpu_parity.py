@@ -567,6 +567,50 @@ def test_stacked_block_jacobi_matches_oracle_per_shot(n_shots):
     assert out["mixed"] < 1e-5
 
 
+@pytest.mark.parametrize("name,make", PRE2_CASES, ids=[c[0] for c in PRE2_CASES])
+def test_fp16_stencil_blocks_match_oracle(name, make):
+    # the single-shot FP32 inner solve applies the Pre2 blocks balanced, diag(r) H diag(c),
+    # with H in FP16 (2^-11 per entry, as the TF32 rounding of the batch path); against the
+    # oracle's literal Pre2 (FP64), and the 32-bit setting at FP32 accuracy
+    torch = need_gpu()
+    from oracle.precond import pre2
+    w = make()
+    sim = oracle_sim(w)
+    r = np.random.default_rng(11).normal(size=sim.A.shape[0])
+    zo = pre2(sim.A, w.n_elem, sim.mesh.elem_nbr) @ r
+    s = gpu_solver(w, precision="mixed", with_sources=False, with_receivers=False, preconditioner=2)
+    s.set_shots(1)
+    out = {}
+    for bits in (16, 32):
+        s.set_pre2_storage(bits)
+        rd = torch.tensor(r, dtype=torch.float32, device="cuda")
+        zd = torch.zeros_like(rd)
+        torch.cuda.synchronize()
+        s.apply_preconditioner_device(w.dt, rd.data_ptr(), zd.data_ptr(), fp32=True)
+        out[bits] = rel_l2(zd.cpu().numpy().astype(np.float64), zo)
+        N = w.dim * s.query(2) * s.query(4)
+        assert s.pre2_bits == (bits if N % 2 == 0 and N <= 128 else 32)
+    print(name, "Pre2 single shot: FP16 blocks %.3g, FP32 blocks %.3g" % (out[16], out[32]))
+    assert out[32] < 1e-4
+    assert out[16] < 2e-3
+
+
+def test_fp16_stencil_blocks_keep_iteration_counts():
+    # the FP16 blocks must not degrade the preconditioner: a mixed-precision solve on a scaled
+    # copy of the benchmark construction takes about as many iterations as with FP32 blocks
+    need_gpu()
+    w = synth.scaled("c2", ny=10, steps=3)
+    its = {}
+    for bits in (32, 16):
+        s = gpu_solver(w, precision="mixed", rel_tol=1e-10, max_iters=20000, preconditioner=2)
+        s.set_pre2_storage(bits)
+        st = s.step(w.dt, 3)
+        assert st["status"] == 0 and st["final_rel_res"] <= 1e-10
+        its[bits] = st["iters_total"]
+    print("Pre2 inner iterations over 3 slabs: FP32 blocks %d, FP16 blocks %d" % (its[32], its[16]))
+    assert its[16] <= 1.1 * its[32] + 5
+
+
 def test_tensor_core_stencil_preconditioner_keeps_iteration_counts():
     # the TF32 local step must not degrade the preconditioner: a stacked mixed-precision solve
     # (tensor-core local step) takes about as many iterations as its slowest shot solved alone
