@@ -398,14 +398,18 @@ def test_stencil_preconditioned_multishot_matches_oracle():
         assert stress_field_rel(sig, sim.sig_tr, sim.disc) < 1e-8
 
 
-def test_stencil_preconditioned_mixed_solves_converge_on_the_inversion_medium():
-    # 30 slabs of the 60,024-triangle heterogeneous medium, 8 shots, mixed precision with
-    # Pre2: every slab converges in a bounded number of inner iterations (reduced-precision
-    # preconditioner blocks once made these solves stagnate after 16 slabs)
+@pytest.mark.parametrize("n_shots", [8, 1])
+def test_stencil_preconditioned_mixed_solves_converge_on_the_inversion_medium(n_shots):
+    # 30 slabs of the 60,024-triangle heterogeneous medium, mixed precision with Pre2: every
+    # slab converges in a bounded number of inner iterations (BF16 preconditioner blocks once
+    # made these solves stagnate after 16 slabs).  8 shots: the tensor-core batch path (TF32
+    # blocks); 1 shot: the balanced FP16 blocks
     need_gpu()
-    w = synth.c5_adjoint(steps=30, true_model=True)
+    w = synth.c5_adjoint(steps=30, true_model=True, n_shots=n_shots)
     s = gpu_solver(w, precision="mixed", rel_tol=1e-8, max_iters=1500, preconditioner=2, gmres_restart=10,
                    inner_tol=1e-2)
+    if n_shots == 1:
+        assert s.pre2_bits == 16
     worst = 0
     for _ in range(w.n_steps):
         st = s.step(w.dt, 1)
