@@ -521,12 +521,178 @@ __global__ void __launch_bounds__(128) pre1_apply_shots_kernel(int64_t n_elem, c
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+// Single-shot FP32 block-Jacobi apply for 2D, p = 3 (N = d N_phi = 20, N_gamma = 4).  Per
+// element u = V^T r, w_q = B_q u_q, z = V w are 20 x 20 x 4 products.  Six consecutive
+// elements per warp, five lanes each: lane g holds columns 4g..4g+3 for u and w (16
+// accumulators: every V value read feeds four products, every r value four) and rows
+// 4g..4g+3 for z.  The six elements' V, B and r are three contiguous ranges, copied by
+// cp.async.bulk one group ahead (per-warp double buffer, bounded mbarrier waits); w goes to
+// the element's r slot, z to its B slot, and z leaves with consecutive 16-byte stores.
+struct Pre1Tile {
+    static constexpr int NP = 10, NG = 4, N = 20, NV = N * NG;     // 80 values per element
+    static constexpr int EPW = 6;                                  // elements per warp and group
+    static constexpr int VE = N * N, BE = N * NG * NG;             // 400, 320 floats
+    static constexpr int SB = EPW * VE, SR = SB + EPW * BE;        // stage: V | B | r
+    static constexpr int STAGE = SR + EPW * NV;                    // 4,800 floats
+    static constexpr int PER_WARP = 2 * STAGE;
+    static_assert((VE * 4) % 16 == 0 && (BE * 4) % 16 == 0 && (NV * 4) % 16 == 0, "bulk copies need 16-byte sizes");
+};
+
+__global__ void __launch_bounds__(64) pre1_apply_tile_kernel(int64_t n_elem, const float* __restrict__ V,
+                                                             const float* __restrict__ B, const float* __restrict__ r,
+                                                             const int* __restrict__ ridx, int64_t ld,
+                                                             float* __restrict__ z, int* __restrict__ err) {
+    using P = Pre1Tile;
+    constexpr int N = P::N, NG = P::NG, NP = P::NP, NV = P::NV, EPW = P::EPW, VE = P::VE, BE = P::BE;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[2][2];
+    if (ridx) r += (int64_t)(*ridx) * ld;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    float* base = reinterpret_cast<float*>(smraw) + warp * P::PER_WARP;
+    const uint32_t bar0 = smem_u32(&bars[warp][0]), bar1 = smem_u32(&bars[warp][1]);
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int el = lane / 5, g = lane % 5;    // lanes 30, 31: el = 6, idle
+    const int64_t n_grp = (n_elem + EPW - 1) / EPW;
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    constexpr long kPollLimit = 1L << 24;
+    auto issue = [&](int64_t p, int st) {   // lane 0 only
+        const int64_t e0 = p * EPW;
+        const int ne = (int)min((int64_t)EPW, n_elem - e0);
+        float* sg = base + st * P::STAGE;
+        const uint32_t bar = st ? bar1 : bar0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (uint32_t)(ne * (VE + BE + NV) * sizeof(float)));
+        bulk_g2s(smem_u32(sg), V + e0 * VE, ne * VE * sizeof(float), bar);
+        bulk_g2s(smem_u32(sg + P::SB), B + e0 * BE, ne * BE * sizeof(float), bar);
+        bulk_g2s(smem_u32(sg + P::SR), r + e0 * NV, ne * NV * sizeof(float), bar);
+    };
+    int64_t p = blockIdx.x * (int64_t)wpb + warp;
+    if (p < n_grp && lane == 0) issue(p, 0);
+    uint32_t ph0 = 0, ph1 = 0;
+    int st = 0;
+    for (; p < n_grp; p += stride) {
+        const int64_t pn = p + stride;
+        if (pn < n_grp && lane == 0) issue(pn, st ^ 1);
+        if (!__all_sync(0xffffffffu, mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit))) {
+            if (lane == 0) atomicExch(err, 1);
+            bool drained = mbar_wait(st ? bar1 : bar0, st ? ph1 : ph0, kPollLimit);
+            if (pn < n_grp) drained = mbar_wait(st ? bar0 : bar1, st ? ph0 : ph1, kPollLimit) && drained;
+            if (!drained && lane == 0) atomicExch(err, 2);
+            break;
+        }
+        if (st) ph1 ^= 1u; else ph0 ^= 1u;
+        float* sg = base + st * P::STAGE;
+        const int64_t e0 = p * EPW;
+        const int ne = (int)min((int64_t)EPW, n_elem - e0);
+        const bool act = el < ne;
+        const float* sV = sg + (act ? el : 0) * VE;
+        float* sB = sg + P::SB + (act ? el : 0) * BE;
+        float* sR = sg + P::SR + (act ? el : 0) * NV;
+        // ---- u = V^T r for columns 4g..4g+3, then w_q = B_q u_q
+        float wq[4][NG];
+        if (act) {
+            float u[4][NG];
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi)
+#pragma unroll
+                for (int a = 0; a < NG; ++a) u[qi][a] = 0.f;
+#pragma unroll
+            for (int row = 0; row < N; ++row) {
+                const float4 v4 = *reinterpret_cast<const float4*>(sV + row * N + 4 * g);
+                const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                const int k = row / NP, n = row % NP;
+                float ra[NG];
+#pragma unroll
+                for (int a = 0; a < NG; ++a) ra[a] = sR[(k * NG + a) * NP + n];
+#pragma unroll
+                for (int qi = 0; qi < 4; ++qi)
+#pragma unroll
+                    for (int a = 0; a < NG; ++a) u[qi][a] = fmaf(vv[qi], ra[a], u[qi][a]);
+            }
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi) {
+                const float4* bq = reinterpret_cast<const float4*>(sB + (4 * g + qi) * NG * NG);
+#pragma unroll
+                for (int a = 0; a < NG; ++a) {
+                    const float4 b4 = bq[a];
+                    wq[qi][a] = fmaf(b4.x, u[qi][0], fmaf(b4.y, u[qi][1], fmaf(b4.z, u[qi][2], b4.w * u[qi][3])));
+                }
+            }
+        }
+        __syncwarp();   // the element's r and B have been read
+        if (act) {
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi)
+                *reinterpret_cast<float4*>(sR + (4 * g + qi) * NG) = make_float4(wq[qi][0], wq[qi][1], wq[qi][2], wq[qi][3]);
+        }
+        __syncwarp();
+        // ---- z = V w for rows 4g..4g+3, into the element's B slot in the element layout
+        if (act) {
+            float zz[4][NG];
+#pragma unroll
+            for (int ri = 0; ri < 4; ++ri)
+#pragma unroll
+                for (int a = 0; a < NG; ++a) zz[ri][a] = 0.f;
+#pragma unroll
+            for (int qc = 0; qc < N / 4; ++qc) {
+                float4 wv[4];
+#pragma unroll
+                for (int qi = 0; qi < 4; ++qi) wv[qi] = *reinterpret_cast<const float4*>(sR + (4 * qc + qi) * NG);
+#pragma unroll
+                for (int ri = 0; ri < 4; ++ri) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(sV + (4 * g + ri) * N + 4 * qc);
+                    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                    for (int qi = 0; qi < 4; ++qi) {
+                        zz[ri][0] = fmaf(vv[qi], wv[qi].x, zz[ri][0]);
+                        zz[ri][1] = fmaf(vv[qi], wv[qi].y, zz[ri][1]);
+                        zz[ri][2] = fmaf(vv[qi], wv[qi].z, zz[ri][2]);
+                        zz[ri][3] = fmaf(vv[qi], wv[qi].w, zz[ri][3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int ri = 0; ri < 4; ++ri) {
+                const int row = 4 * g + ri, k = row / NP, n = row % NP;
+#pragma unroll
+                for (int a = 0; a < NG; ++a) sB[(k * NG + a) * NP + n] = zz[ri][a];
+            }
+        }
+        __syncwarp();
+        for (int t = lane; t < ne * (NV / 4); t += 32) {
+            const int e2 = t / (NV / 4), j = t % (NV / 4);
+            *reinterpret_cast<float4*>(z + (e0 + e2) * NV + 4 * j) =
+                *reinterpret_cast<const float4*>(sg + P::SB + e2 * BE + 4 * j);
+        }
+        __syncwarp();   // stage st is free for the next group
+        st ^= 1;
+    }
+}
+
 template <typename R>
 static bool pre1_apply_fast(stdg_ctx* c, const R* V, const R* B, const R* r, R* z, const int* ridx, int64_t ld,
                             cudaError_t* err, int nshots) {
     const int64_t blocks = std::min<int64_t>((c->n_elem + 3) / 4, 1 << 30);
     const int d = c->dim, np = c->Nphi, ng = c->Ng;
     if constexpr (std::is_same<R, float>::value) {
+        if (d == 2 && np == 10 && ng == 4 && nshots == 1 && c->d_err && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
+            reinterpret_cast<uintptr_t>(z) % 16 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
+            reinterpret_cast<uintptr_t>(B) % 16 == 0 && (ld * (int64_t)sizeof(R)) % 16 == 0) {
+            constexpr int wpb = 1;   // 38.4 KB of stages per warp
+            const size_t smem = sizeof(float) * wpb * Pre1Tile::PER_WARP;
+            const int64_t n_grp = (c->n_elem + Pre1Tile::EPW - 1) / Pre1Tile::EPW;
+            const int64_t nb = std::min<int64_t>((n_grp + wpb - 1) / wpb, (int64_t)c->n_sm * 16);
+            cudaFuncSetAttribute(pre1_apply_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            pre1_apply_tile_kernel<<<(unsigned)nb, 32 * wpb, smem, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z, c->d_err);
+            note_launch(c);
+            *err = cudaGetLastError();
+            return true;
+        }
         if (d == 2 && np == 6 && ng == 3 && nshots >= 16 && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(z) % 16 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(B) % 16 == 0 && (ld * (int64_t)sizeof(R)) % 16 == 0) {

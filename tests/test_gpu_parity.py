@@ -615,6 +615,28 @@ def test_fp16_stencil_blocks_keep_iteration_counts():
     assert its[16] <= 1.1 * its[32] + 5
 
 
+def test_fp32_block_jacobi_single_shot_p3_matches_oracle():
+    # the single-shot FP32 block-Jacobi apply at p = 3 in 2D (six elements per warp, staged by
+    # bulk copies): 196 elements = 32 full groups and a ragged tail of four; against the
+    # oracle's block-diagonal inverse
+    torch = need_gpu()
+    from oracle.precond import pre1
+    w = synth.scaled("c2", ny=7, p=3, steps=1)
+    assert w.n_elem % 6 == 4
+    sim = oracle_sim(w)
+    r = np.random.default_rng(19).normal(size=sim.A.shape[0])
+    zo = pre1(sim.A, w.n_elem) @ r
+    s = gpu_solver(w, precision="mixed", with_sources=False, with_receivers=False, preconditioner=1)
+    s.set_shots(1)
+    rd = torch.tensor(r, dtype=torch.float32, device="cuda")
+    zd = torch.zeros_like(rd)
+    torch.cuda.synchronize()
+    s.apply_preconditioner_device(w.dt, rd.data_ptr(), zd.data_ptr(), fp32=True)
+    err = rel_l2(zd.cpu().numpy().astype(np.float64), zo)
+    print("Pre1 FP32 single shot, p = 3: %.3g" % err)
+    assert err < 1e-5
+
+
 def test_tensor_core_stencil_preconditioner_keeps_iteration_counts():
     # the TF32 local step must not degrade the preconditioner: a stacked mixed-precision solve
     # (tensor-core local step) takes about as many iterations as its slowest shot solved alone
