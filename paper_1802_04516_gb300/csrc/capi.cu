@@ -178,6 +178,8 @@ static int setup_pre1(stdg_ctx* c) {
         if (c->opt.precision != STDG_FP64) {
             if ((rc = dev_alloc(c, (void**)&c->d_preV32, sizeof(float) * ne * n * n)) != STDG_OK) return rc;
             if ((rc = dev_alloc(c, (void**)&c->d_preB32, sizeof(float) * ne * n * c->Ng * c->Ng)) != STDG_OK) return rc;
+            if (c->dim == 2 && c->Nphi == 10 && c->Ng == 4 &&   // the single-shot apply's lane order
+                (rc = dev_alloc(c, (void**)&c->d_preB32t, sizeof(float) * ne * n * c->Ng * c->Ng)) != STDG_OK) return rc;
         }
     }
     double* d_Rinv = nullptr;
@@ -375,6 +377,7 @@ int stdg_set_mesh(stdg_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem
     c->d_elem_face = nullptr;
     c->d_preV = c->d_preLam = c->d_preB = nullptr;
     c->d_preV32 = c->d_preB32 = nullptr;
+    c->d_preB32t = nullptr;
     c->d_pre2 = nullptr;
     c->d_pre2_32 = nullptr;
     c->d_pre2_mma = nullptr;

@@ -524,8 +524,9 @@ __global__ void __launch_bounds__(128) pre1_apply_shots_kernel(int64_t n_elem, c
 // Single-shot FP32 block-Jacobi apply for 2D, p = 3 (N = d N_phi = 20, N_gamma = 4).  Per
 // element u = V^T r, w_q = B_q u_q, z = V w are 20 x 20 x 4 products.  Six consecutive
 // elements per warp, five lanes each: lane g holds columns 4g..4g+3 for u and w (16
-// accumulators: every V value read feeds four products, every r value four) and rows
-// 4g..4g+3 for z.  The six elements' V, B and r are three contiguous ranges, copied by
+// accumulators: every V value read feeds four products, every r value four; B comes in the
+// lane order [qi][a][g][b]) and rows g, g+5, g+10, g+15 for z (their V rows are 20 floats
+// apart across lanes: distinct banks).  The six elements' V, B and r are three contiguous ranges, copied by
 // cp.async.bulk one group ahead (per-warp double buffer, bounded mbarrier waits); w goes to
 // the element's r slot, z to its B slot, and z leaves with consecutive 16-byte stores.
 struct Pre1Tile {
@@ -537,6 +538,19 @@ struct Pre1Tile {
     static constexpr int PER_WARP = 2 * STAGE;
     static_assert((VE * 4) % 16 == 0 && (BE * 4) % 16 == 0 && (NV * 4) % 16 == 0, "bulk copies need 16-byte sizes");
 };
+
+// B of every element from [q][a][b] to the lane order of the apply below, [qi][a][g][b] with
+// q = 4g + qi: the five lanes of an element then read consecutive 16-byte pieces
+__global__ void pre1_b_lane_order_kernel(int64_t n_elem, const float* __restrict__ B, float* __restrict__ Bt) {
+    using P = Pre1Tile;
+    const int64_t n = n_elem * P::BE;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / P::BE;
+        const int t = (int)(i % P::BE);                   // destination index in [qi][a][g][b]
+        const int b = t % P::NG, g = (t / P::NG) % 5, a = (t / (5 * P::NG)) % P::NG, qi = t / (5 * P::NG * P::NG);
+        Bt[i] = B[e * P::BE + ((4 * g + qi) * P::NG + a) * P::NG + b];
+    }
+}
 
 __global__ void __launch_bounds__(64) pre1_apply_tile_kernel(int64_t n_elem, const float* __restrict__ V,
                                                              const float* __restrict__ B, const float* __restrict__ r,
@@ -616,10 +630,9 @@ __global__ void __launch_bounds__(64) pre1_apply_tile_kernel(int64_t n_elem, con
             }
 #pragma unroll
             for (int qi = 0; qi < 4; ++qi) {
-                const float4* bq = reinterpret_cast<const float4*>(sB + (4 * g + qi) * NG * NG);
 #pragma unroll
-                for (int a = 0; a < NG; ++a) {
-                    const float4 b4 = bq[a];
+                for (int a = 0; a < NG; ++a) {   // B in the lane order [qi][a][g][b]
+                    const float4 b4 = *reinterpret_cast<const float4*>(sB + ((qi * NG + a) * 5 + g) * NG);
                     wq[qi][a] = fmaf(b4.x, u[qi][0], fmaf(b4.y, u[qi][1], fmaf(b4.z, u[qi][2], b4.w * u[qi][3])));
                 }
             }
@@ -631,7 +644,7 @@ __global__ void __launch_bounds__(64) pre1_apply_tile_kernel(int64_t n_elem, con
                 *reinterpret_cast<float4*>(sR + (4 * g + qi) * NG) = make_float4(wq[qi][0], wq[qi][1], wq[qi][2], wq[qi][3]);
         }
         __syncwarp();
-        // ---- z = V w for rows 4g..4g+3, into the element's B slot in the element layout
+        // ---- z = V w for rows g + 5 ri, into the element's B slot in the element layout
         if (act) {
             float zz[4][NG];
 #pragma unroll
@@ -644,8 +657,8 @@ __global__ void __launch_bounds__(64) pre1_apply_tile_kernel(int64_t n_elem, con
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) wv[qi] = *reinterpret_cast<const float4*>(sR + (4 * qc + qi) * NG);
 #pragma unroll
-                for (int ri = 0; ri < 4; ++ri) {
-                    const float4 v4 = *reinterpret_cast<const float4*>(sV + (4 * g + ri) * N + 4 * qc);
+                for (int ri = 0; ri < 4; ++ri) {   // rows g + 5 ri: 20 floats apart across lanes, no conflict
+                    const float4 v4 = *reinterpret_cast<const float4*>(sV + (g + 5 * ri) * N + 4 * qc);
                     const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                     for (int qi = 0; qi < 4; ++qi) {
@@ -658,7 +671,7 @@ __global__ void __launch_bounds__(64) pre1_apply_tile_kernel(int64_t n_elem, con
             }
 #pragma unroll
             for (int ri = 0; ri < 4; ++ri) {
-                const int row = 4 * g + ri, k = row / NP, n = row % NP;
+                const int row = g + 5 * ri, k = row / NP, n = row % NP;
 #pragma unroll
                 for (int a = 0; a < NG; ++a) sB[(k * NG + a) * NP + n] = zz[ri][a];
             }
@@ -680,7 +693,8 @@ static bool pre1_apply_fast(stdg_ctx* c, const R* V, const R* B, const R* r, R* 
     const int64_t blocks = std::min<int64_t>((c->n_elem + 3) / 4, 1 << 30);
     const int d = c->dim, np = c->Nphi, ng = c->Ng;
     if constexpr (std::is_same<R, float>::value) {
-        if (d == 2 && np == 10 && ng == 4 && nshots == 1 && c->d_err && reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
+        if (d == 2 && np == 10 && ng == 4 && nshots == 1 && c->d_err && c->d_preB32t && B == c->d_preB32 &&
+            reinterpret_cast<uintptr_t>(r) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(z) % 16 == 0 && reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(B) % 16 == 0 && (ld * (int64_t)sizeof(R)) % 16 == 0) {
             constexpr int wpb = 1;   // 38.4 KB of stages per warp
@@ -688,7 +702,8 @@ static bool pre1_apply_fast(stdg_ctx* c, const R* V, const R* B, const R* r, R* 
             const int64_t n_grp = (c->n_elem + Pre1Tile::EPW - 1) / Pre1Tile::EPW;
             const int64_t nb = std::min<int64_t>((n_grp + wpb - 1) / wpb, (int64_t)c->n_sm * 16);
             cudaFuncSetAttribute(pre1_apply_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            pre1_apply_tile_kernel<<<(unsigned)nb, 32 * wpb, smem, c->stream>>>(c->n_elem, V, B, r, ridx, ld, z, c->d_err);
+            pre1_apply_tile_kernel<<<(unsigned)nb, 32 * wpb, smem, c->stream>>>(c->n_elem, V, c->d_preB32t, r, ridx, ld, z,
+                                                                              c->d_err);
             note_launch(c);
             *err = cudaGetLastError();
             return true;
@@ -743,6 +758,11 @@ cudaError_t launch_pre1_time(stdg_ctx* c, double dt) {
     if (c->d_preB32) {
         pre1_time_kernel<float><<<(unsigned)((nq + 127) / 128), 128, 0, c->stream>>>(nq, c->Ng, c->d_rt, c->d_preLam,
                                                                                   cfac * dt * dt, c->d_preB32); note_launch(c);
+    }
+    if (c->d_preB32t) {
+        const int64_t nb = c->n_elem * Pre1Tile::BE;
+        pre1_b_lane_order_kernel<<<(unsigned)std::min<int64_t>((nb + 255) / 256, (int64_t)c->n_sm * 32), 256, 0, c->stream>>>(
+            c->n_elem, c->d_preB32, c->d_preB32t); note_launch(c);
     }
     return cudaGetLastError();
 }

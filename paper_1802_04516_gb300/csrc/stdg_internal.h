@@ -147,6 +147,7 @@ struct stdg_ctx {
     // ---- block-Jacobi preconditioner (precond.cu)
     double *d_preV = nullptr, *d_preLam = nullptr, *d_preB = nullptr;
     float *d_preV32 = nullptr, *d_preB32 = nullptr;
+    float *d_preB32t = nullptr;   // B in the lane order of the single-shot 2D p = 3 apply ([qi][a][g][b])
     int32_t* d_elem_face = nullptr;
     double pre_dt = -1.0;    // slab size the time blocks d_preB were built for
     // ---- stencil preconditioner (precond2.cu): S_i^{-1} per element, column-major
