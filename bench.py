@@ -194,8 +194,10 @@ def e2e_steps(torch, s, w, steps, stream):
 # by the units one launch processes; valid for the 2D p = p_gamma = 3 shape only: the tiled
 # face kernel per face on the 102,400-triangle copy of the construction
 # (profiles/face_tile_c2_102k.md), the Pre2 local step per element on the 16,384-triangle copy
-# (profiles/traffic_face_pre2_c2_16k.md).
-TRAFFIC_PER_UNIT = {"face_fp32": (344876032 + 27466752) / 154080, "pre2_local_fp32": (429949184 + 2444032) / 16384}
+# (FP32 blocks, profiles/traffic_face_pre2_c2_16k.md) and on the 102,400-triangle copy (FP16
+# blocks, profiles/pre1_pre2_single_shot_c2_102k.md).
+TRAFFIC_PER_UNIT = {"face_fp32": (344876032 + 27466752) / 154080, "pre2_local_fp32": (429949184 + 2444032) / 16384,
+                    "pre2_local_fp16": (1450097000 + 32895744) / 102400}
 
 
 def _traffic(w, key, units):

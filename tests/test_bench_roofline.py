@@ -65,6 +65,8 @@ def test_pre2_local_bytes_with_fp16_blocks():
     r = bench.pre2_local_roofline(_Timed(None, 0.45, pre2_bits=16), _w(), {"hbm_gbs": 7000.0})
     assert r["alg_bytes_per_launch"] == alg and r["kernel"] == "pre2_local_half_kernel"
     assert abs(r["achieved"] - alg / 0.45e-3 / 1e9) < 0.1
+    # ncu's DRAM bytes per element of the FP16 kernel on the 102,400-triangle copy, scaled
+    assert r["traffic"] == int((1450097000 + 32895744) / 102400 * N_ELEM)
 
 
 def test_dominant_kernel_by_time_per_iteration():
