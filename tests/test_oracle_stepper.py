@@ -185,3 +185,31 @@ def test_source_vector_is_the_slab_integral_of_the_wavelet():
             for k in range(dz.dim):
                 got = sv[e_s, k, a].sum()
                 assert abs(got - w.shots_dir[0][k] * ref) <= 1e-11 * sim.dt * w.a1, (t0, a, k, got, ref)
+
+
+@pytest.mark.parametrize("scheme,p,pg", [("stdg", 2, 2), ("cn", 1, 0)])
+def test_time_scaling_identity(scheme, p, pg):
+    # A mesh part advancing with step alpha dt is the same discrete scheme as the part with
+    # density rho / alpha, Lame parameters alpha lambda, alpha mu and the Ricker wavelet at
+    # frequency alpha f0, delay t_D / alpha, advanced with step dt (Eq. 5 in the time
+    # tau = t / alpha; the basis of per-part time steps in a ragged batch): states equal to
+    # rounding, energy scaled by 1 / alpha
+    w = synth.c4_ragged(0, steps=3, scale=0.02)
+    alpha, dt = 1.7, w.dt
+    direc = [0.3, 1.0]
+
+    def run(lam, mu, rho, step, f0, td):
+        sim = Simulation(w.xyz, w.elem_vert, w.period, lam, mu, rho, p, pg, scheme, step)
+        sim.set_source(w.shots_xs[0], direc, f0, td, w.a1)
+        sim.step(3)
+        return sim
+
+    a = run(w.lam, w.mu, w.rho, alpha * dt, w.f0, w.t_delay)
+    b = run(alpha * w.lam, alpha * w.mu, w.rho / alpha, dt, alpha * w.f0, w.t_delay / alpha)
+    assert np.abs(a.v_tr).max() > 0
+    assert np.abs(b.v_tr - a.v_tr).max() <= 1e-10 * np.abs(a.v_tr).max()
+    assert np.abs(b.sig_tr - a.sig_tr).max() <= 1e-10 * np.abs(a.sig_tr).max()
+    assert abs(b.energy() - a.energy() / alpha) <= 1e-10 * a.energy()
+    # a different step without the rescaling is a different solution
+    c = run(w.lam, w.mu, w.rho, dt, w.f0, w.t_delay)
+    assert np.abs(c.v_tr - a.v_tr).max() > 1e-3 * np.abs(a.v_tr).max()
