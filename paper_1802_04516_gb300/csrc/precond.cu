@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kPreThreads) pre1_setup_kernel(
             __syncthreads();
             if (s_off <= 1e-30 * s_diag || s_diag == 0.0) break;
             for (int round = 0; round < slots - 1; ++round) {
-                // rotation angles for the pairs of this round
+                // rotation angles for the pairs of this step of the pair schedule
                 if (tid < m2) {
                     int p = top[tid], q = bot[tid];
                     if (p > q) { int t = p; p = q; q = t; }
